@@ -1,0 +1,320 @@
+"""Seeded synthetic inputs and neuron-model tables for the HH hot path.
+
+This module is shared by the CUDA path, the FP64 oracle's tests and the
+benchmark.  It holds parameters and random draws only -- none of the method's
+arithmetic (no rate function, no integrator, no routing).  Every array that is
+handed to both sides is produced here once, in the precision the library
+consumes (float32 / int32), and the oracle reads the very same values.
+
+Neuron models are plain data: a list of channels, each with a reversal
+potential E_X, a maximal conductance gbar_X and a list of gates with an
+exponent, following the general form I = C_m dV/dt + sum_X gbar_X eta_X(p)(V-E_X)
+with dp/dt = alpha_p(V)(1-p) - beta_p(V) p (Methods, Eq. hh_eq_full), where
+eta_X is the product of the gates raised to their exponents.
+
+A rate function is a tuple (form, a, vh, k[, vh2, k2, c]) evaluated as
+c + form(V):
+  const   : a
+  exp     : a * exp((V - vh)/k)
+  sigmoid : a / (1 + exp((V - vh)/k))
+  linoid  : a * (V - vh) / (1 - exp(-(V - vh)/k))      (removable point at V = vh)
+  bell    : a / (exp((V - vh)/k) + exp((V - vh2)/k2))
+Gate kinds:
+  ab      : f1 = alpha(V), f2 = beta(V)                       [1/ms]
+  inftau  : f1 = p_inf(V), f2 = tau(V)                        [-, ms]
+  ca      : p_inf = Ca / (Ca + f1.a), tau = f2(V)              (Ca in uM)
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Model tables
+# ---------------------------------------------------------------------------
+
+
+def fn(form, a, vh=0.0, k=1.0, vh2=0.0, k2=1.0, c=0.0):
+    return (form, float(a), float(vh), float(k), float(vh2), float(k2), float(c))
+
+
+# Classic squid-axon HH (Hodgkin & Huxley 1952, Methods "HH point neuron"),
+# modern convention with rest near -65 mV.  Rate constants are the textbook
+# set; reversal potentials and maximal conductances are the ones the
+# single-neuron workload names (ENa=50, EK=-77, EL=-54.4 mV; 120/36/0.3 mS/cm^2).
+CLASSIC_HH = {
+    "name": "hh1952",
+    "C_m": 1.0,  # uF/cm^2
+    "channels": [
+        {"name": "Na", "E": 50.0, "gbar": 120.0, "gates": [
+            {"kind": "ab", "power": 3, "f1": fn("linoid", 0.1, -40.0, 10.0),
+             "f2": fn("exp", 4.0, -65.0, -18.0)},                  # m
+            {"kind": "ab", "power": 1, "f1": fn("exp", 0.07, -65.0, -20.0),
+             "f2": fn("sigmoid", 1.0, -35.0, -10.0)},              # h
+        ]},
+        {"name": "K", "E": -77.0, "gbar": 36.0, "gates": [
+            {"kind": "ab", "power": 4, "f1": fn("linoid", 0.01, -55.0, 10.0),
+             "f2": fn("exp", 0.125, -65.0, -80.0)},                # n
+        ]},
+        {"name": "L", "E": -54.4, "gbar": 0.3, "gates": []},
+    ],
+    "calcium": None,
+}
+
+# Multi-channel point neuron: Na, Kdr (the HH pair above), a fast transient
+# K current KA (a^3 b), a high-voltage-activated L-type Ca current (s^2,
+# ohmic, E_Ca = 120 mV), a Ca-dependent K current KCa and a hyperpolarisation
+# activated cation current Ih, with a first-order Ca pool
+#   d[Ca]/dt = -k_Ca * I_Ca - ([Ca] - Ca_rest)/tau_Ca.
+# The kinetic forms follow the shapes used for these currents in the
+# thalamic / cortical models of Huguenard & McCormick (1992; I_A, I_h) and
+# Traub et al. (1991; I_Ca); the maximal conductances are chosen so that the
+# neuron stays excitable and fires repetitively over 0-15 uA/cm^2.  The table
+# is a workload definition: both the oracle and the CUDA path consume it.
+MULTI_CHANNEL = {
+    "name": "multi6",
+    "C_m": 1.0,
+    "channels": [
+        {"name": "Na", "E": 50.0, "gbar": 120.0, "gates": [
+            {"kind": "ab", "power": 3, "f1": fn("linoid", 0.1, -40.0, 10.0),
+             "f2": fn("exp", 4.0, -65.0, -18.0)},
+            {"kind": "ab", "power": 1, "f1": fn("exp", 0.07, -65.0, -20.0),
+             "f2": fn("sigmoid", 1.0, -35.0, -10.0)},
+        ]},
+        {"name": "Kdr", "E": -77.0, "gbar": 36.0, "gates": [
+            {"kind": "ab", "power": 4, "f1": fn("linoid", 0.01, -55.0, 10.0),
+             "f2": fn("exp", 0.125, -65.0, -80.0)},
+        ]},
+        {"name": "KA", "E": -77.0, "gbar": 2.0, "gates": [
+            {"kind": "inftau", "power": 3, "f1": fn("sigmoid", 1.0, -60.0, -8.5),
+             "f2": fn("bell", 1.0, -35.8, 19.7, -79.7, -12.7, c=0.37)},
+            {"kind": "inftau", "power": 1, "f1": fn("sigmoid", 1.0, -78.0, 6.0),
+             "f2": fn("bell", 1.0, -46.0, 5.0, -238.0, -37.5, c=19.0)},
+        ]},
+        {"name": "CaL", "E": 120.0, "gbar": 0.2, "gates": [
+            {"kind": "ab", "power": 2, "f1": fn("sigmoid", 1.6, 5.0, -13.888889),
+             "f2": fn("linoid", -0.02, -8.9, -5.0)},
+        ]},
+        {"name": "KCa", "E": -77.0, "gbar": 0.1, "gates": [
+            {"kind": "ca", "power": 1, "f1": fn("const", 3.0),
+             "f2": fn("const", 10.0)},
+        ]},
+        {"name": "Ih", "E": -43.0, "gbar": 0.2, "gates": [
+            {"kind": "inftau", "power": 1, "f1": fn("sigmoid", 1.0, -75.0, 5.5),
+             "f2": fn("bell", 1.0, -169.65, -11.628, 26.676, 14.265)},
+        ]},
+        {"name": "L", "E": -54.4, "gbar": 0.3, "gates": []},
+    ],
+    # Ca pool fed by the channel named "CaL"; Ca in uM, k_Ca in uM/ms per uA/cm^2
+    "calcium": {"channel": "CaL", "tau": 20.0, "k": 0.05, "rest": 0.05},
+}
+
+MODELS = {"hh1952": CLASSIC_HH, "multi6": MULTI_CHANNEL}
+
+
+def model_gbar(model) -> np.ndarray:
+    return np.array([c["gbar"] for c in model["channels"]], dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Seeded workload generators (numpy PCG64; seed 0 by default)
+# ---------------------------------------------------------------------------
+
+
+def single_neurons(n=1024, seed=0, i_max=20.0):
+    """Independent classic HH neurons with constant injected current.
+
+    I ~ U(0, i_max) uA/cm^2, V0 = -65 mV, gates at steady state at V0.
+    Returns float32 arrays (the library's precision); the oracle reads the
+    same float32 values widened to float64.
+    """
+    rng = np.random.default_rng(seed)
+    I = rng.uniform(0.0, i_max, n).astype(np.float32)
+    V0 = np.full(n, -65.0, dtype=np.float32)
+    return {"I": I, "V0": V0}
+
+
+def multi_channel_neurons(n=1_000_000, seed=0, sigma=0.3, i_max=15.0,
+                          model=MULTI_CHANNEL):
+    """Independent multi-channel neurons with per-neuron maximal conductances.
+
+    gbar[c][i] = gbar_std[c] * LogNormal(0, sigma); I ~ U(0, i_max).
+    Returns gbar as float32 [n_channels][n].
+    """
+    rng = np.random.default_rng(seed)
+    g0 = model_gbar(model)
+    gbar = (g0[:, None] * rng.lognormal(0.0, sigma, (len(g0), n))).astype(np.float32)
+    I = rng.uniform(0.0, i_max, n).astype(np.float32)
+    V0 = np.full(n, -65.0, dtype=np.float32)
+    return {"I": I, "V0": V0, "gbar": gbar}
+
+
+def random_in_csr(n, k_in, seed, mu=-1.0, sigma=0.5, n_pre=None, allow_self=False):
+    """Fixed in-degree random graph as an in-CSR (rows = postsynaptic neuron).
+
+    Each row draws k_in distinct presynaptic sources uniformly from the other
+    n-1 neurons (no self-loops), sorted ascending; weights ~ LogNormal(mu, sigma)
+    in nS, float32.  Returns row_ptr (int64 [n+1]), col_idx (int32), weight
+    (float32).
+    """
+    rng = np.random.default_rng(seed)
+    n_pre = n if n_pre is None else n_pre
+    k_in = int(k_in)
+    pool = n_pre - (0 if allow_self else 1)
+    if k_in > pool:
+        raise ValueError("in-degree larger than the number of possible sources")
+    cols = np.empty((n, k_in), dtype=np.int32)
+    for i in range(n):
+        c = rng.choice(pool, size=k_in, replace=False)
+        if not allow_self:
+            c = c + (c >= i)
+        c.sort()
+        cols[i] = c
+    w = rng.lognormal(mu, sigma, n * k_in).astype(np.float32)
+    row_ptr = np.arange(0, (n + 1) * k_in, k_in, dtype=np.int64)
+    return row_ptr, cols.reshape(-1), w
+
+
+def random_in_csr_fast(n, k_in, seed, mu=-1.0, sigma=0.5):
+    """Same distribution as random_in_csr (k_in distinct non-self sources per
+    row, sorted) generated block-wise with sort-based rejection of duplicates;
+    used for the 1e8-synapse network where a per-row loop is too slow.  The two
+    generators draw different random streams."""
+    rng = np.random.default_rng(seed)
+    k_in = int(k_in)
+    cols = np.empty((n, k_in), dtype=np.int32)
+    block = max(1, min(n, (1 << 24) // max(k_in, 1)))
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        rows = r1 - r0
+        extra = max(8, int(k_in * k_in / max(n - 1, 1) * 3) + 8)
+        done = np.zeros(rows, dtype=bool)
+        out = cols[r0:r1]
+        while not done.all():
+            idx = np.nonzero(~done)[0]
+            cand = rng.integers(0, n - 1, size=(idx.size, k_in + extra), dtype=np.int64)
+            cand = cand + (cand >= (r0 + idx)[:, None])
+            cand.sort(axis=1)
+            dup = np.zeros_like(cand, dtype=bool)
+            dup[:, 1:] = cand[:, 1:] == cand[:, :-1]
+            n_unique = (~dup).sum(axis=1)
+            ok = n_unique >= k_in
+            for j in np.nonzero(ok)[0]:
+                u = cand[j][~dup[j]]
+                # keep a uniformly random subset of the distinct candidates
+                sel = rng.choice(u.size, size=k_in, replace=False)
+                sel.sort()
+                out[idx[j]] = u[sel]
+            done[idx[ok]] = True
+    w = rng.lognormal(mu, sigma, n * k_in).astype(np.float32)
+    row_ptr = np.arange(0, (n + 1) * k_in, k_in, dtype=np.int64)
+    return row_ptr, cols.reshape(-1), w
+
+
+def network(n=38_000, k_in=2_632, exc_frac=0.8, seed=0, mu=-1.0, sigma=0.5,
+            fast=None):
+    """Sparse conductance-based HH network (in-CSR by postsynaptic neuron).
+
+    Neurons 0 .. exc_frac*n-1 are excitatory, the rest inhibitory; V0 ~ U(-70,-60).
+    """
+    if fast is None:
+        fast = n * k_in > 2_000_000
+    gen = random_in_csr_fast if fast else random_in_csr
+    row_ptr, col, w = gen(n, k_in, seed, mu, sigma)
+    rng = np.random.default_rng(seed + 1_000_003)
+    n_exc = int(round(exc_frac * n))
+    inh = np.zeros(n, dtype=np.uint8)
+    inh[n_exc:] = 1
+    V0 = rng.uniform(-70.0, -60.0, n).astype(np.float32)
+    return {"row_ptr": row_ptr, "col": col, "w": w, "inh": inh, "V0": V0,
+            "n": n, "k_in": k_in}
+
+
+def spike_raster(n, n_steps, per_step, seed):
+    """A synthetic spike raster for open-loop routing: `per_step` distinct
+    presynaptic neurons drawn uniformly at every step.  Returns (step, idx)
+    int32 arrays sorted by (step, idx)."""
+    rng = np.random.default_rng(seed)
+    steps, idx = [], []
+    for t in range(n_steps):
+        j = np.sort(rng.choice(n, size=per_step, replace=False)).astype(np.int32)
+        steps.append(np.full(per_step, t, dtype=np.int32))
+        idx.append(j)
+    if not steps:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    return np.concatenate(steps), np.concatenate(idx)
+
+
+def recurrent_layer(B=128, n_in=700, n_hid=1024, n_out=20, T=250, seed=0,
+                    dt_outer_ms=0.1, rate_max_hz=50.0, w_in_scale=None,
+                    w_rec_scale=None, i_bias=4.0):
+    """Differentiable recurrent HH layer workload (shape of a spoken-digit task).
+
+    X[t, b, c] ~ Bernoulli(rate_c * dt_outer) with rate_c ~ U(0, rate_max) Hz;
+    weights in uA/cm^2 per input spike, rounded to bfloat16-representable
+    float32 values (the tensor-core path stores them in bf16 exactly);
+    labels ~ U{0..n_out-1}.
+    """
+    rng = np.random.default_rng(seed)
+    rate = rng.uniform(0.0, rate_max_hz, n_in)
+    p = rate * dt_outer_ms * 1e-3
+    X = (rng.random((T, B, n_in)) < p[None, None, :]).astype(np.float32)
+    if w_in_scale is None:
+        w_in_scale = 40.0
+    if w_rec_scale is None:
+        w_rec_scale = 2.0
+    W_in = to_bf16_exact(rng.normal(0.0, w_in_scale / math.sqrt(n_in), (n_in, n_hid)))
+    W_rec = to_bf16_exact(rng.normal(0.0, w_rec_scale / math.sqrt(n_hid), (n_hid, n_hid)))
+    W_out = (rng.normal(0.0, 1.0 / math.sqrt(n_hid), (n_out, n_hid))).astype(np.float32)
+    bias = np.full(n_hid, i_bias, dtype=np.float32)
+    labels = rng.integers(0, n_out, B).astype(np.int32)
+    return {"X": X, "W_in": W_in, "W_rec": W_rec, "W_out": W_out, "bias": bias,
+            "labels": labels}
+
+
+def to_bf16_exact(a) -> np.ndarray:
+    """Round float64 values to the nearest bfloat16 (ties to even) and return
+    them as float32, so that a bf16 copy holds exactly the same numbers."""
+    a32 = np.asarray(a, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def batched_networks(n_nets=64, n_min=1_000, n_max=50_000, k_min=100, k_max=1_000,
+                     seed=0, exc_frac=0.8, mu=-1.0, sigma=0.5):
+    """Many independent networks concatenated block-diagonally.
+
+    Sizes ~ LogUniform(n_min, n_max), in-degree ~ U{k_min..k_max} (clipped to
+    n-1), half of the networks use the classic HH model and half the
+    multi-channel model (model id per neuron).  Returns a single in-CSR over the
+    concatenated neuron index, net offsets and per-neuron model ids.
+    """
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_nets)).astype(np.int64)
+    kin = rng.integers(k_min, k_max + 1, n_nets)
+    kin = np.minimum(kin, sizes - 1)
+    model_of_net = rng.integers(0, 2, n_nets).astype(np.uint8)
+    offsets = np.zeros(n_nets + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(sizes)
+    rows, cols, ws = [np.zeros(1, np.int64)], [], []
+    inh = np.zeros(int(offsets[-1]), np.uint8)
+    model_id = np.zeros(int(offsets[-1]), np.uint8)
+    nnz = 0
+    for k in range(n_nets):
+        n, ki = int(sizes[k]), int(kin[k])
+        gen = random_in_csr_fast if n * ki > 2_000_000 else random_in_csr
+        rp, c, w = gen(n, ki, int(rng.integers(0, 2**31)), mu, sigma)
+        rows.append(rp[1:] + nnz)
+        cols.append(c + int(offsets[k]))
+        ws.append(w)
+        nnz += c.size
+        n_exc = int(round(exc_frac * n))
+        inh[offsets[k] + n_exc: offsets[k + 1]] = 1
+        model_id[offsets[k]: offsets[k + 1]] = model_of_net[k]
+    V0 = rng.uniform(-70.0, -60.0, int(offsets[-1])).astype(np.float32)
+    return {"row_ptr": np.concatenate(rows), "col": np.concatenate(cols).astype(np.int32),
+            "w": np.concatenate(ws).astype(np.float32), "inh": inh, "V0": V0,
+            "offsets": offsets, "sizes": sizes, "k_in": kin, "model_id": model_id,
+            "model_of_net": model_of_net}
