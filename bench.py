@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the HH hot path on the sparse conductance-based network.
+
+Workload (synthetic, seeded): 38,000 classic HH neurons (80% excitatory),
+fixed in-degree 2,632 with uniformly random sources (1.0e8 synapses, CSR),
+lognormal weights (mu=-1, sigma=0.5 nS), exponential synapses (tau_E 5 ms,
+tau_I 10 ms, E_E 0, E_I -80 mV), 1 ms delay, Poisson background, dt 0.025 ms,
+1,000 ms of simulated time per step (40,000 time steps).
+
+One bench step = reset the network state and simulate the full 1,000 ms:
+every time step runs delivery from the delay line, the background draw, the
+rates/gates/V update, threshold detection, spike compaction, routing over the
+CSR graph and synaptic decay.  value = neuron-steps/s over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_21407_gb300 import inputs as inp  # noqa: E402
+
+W = dict(n=38_000, k_in=2_632, exc_frac=0.8, mu=-1.0, sigma=0.5, tau_E=5.0, tau_I=10.0,
+         E_E=0.0, E_I=-80.0, area_cm2=2.0e-4, delay_ms=1.0, dt=0.025, T_ms=1000.0,
+         bg_rate_hz=5.0, bg_K=2_106, bg_w_nS=0.368, seed=0)
+STEPS_PER_SIM = int(round(W["T_ms"] / W["dt"]))
+DELAY = int(round(W["delay_ms"] / W["dt"]))
+SYN = {"tau_E": W["tau_E"], "tau_I": W["tau_I"], "E_E": W["E_E"], "E_I": W["E_I"],
+       "area_cm2": W["area_cm2"]}
+BG = {"rate_hz": W["bg_rate_hz"], "K": W["bg_K"], "w": W["bg_w_nS"]}
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# SFU (MUFU) issue rate per SM per clock for ex2/rcp on this architecture and
+# the SM count / maximum clock of the part.
+SM_COUNT, MUFU_PER_SM_CLK, FP32_PER_SM_CLK = 152, 16, 128
+
+
+def workload_config():
+    return {"workload": "hh_sparse_network_38k",
+            "neurons": W["n"], "in_degree": W["k_in"], "synapses": W["n"] * W["k_in"],
+            "exc_frac": W["exc_frac"], "weights": "lognormal(mu=-1,sigma=0.5) nS",
+            "tau_E_ms": W["tau_E"], "tau_I_ms": W["tau_I"], "delay_ms": W["delay_ms"],
+            "dt_ms": W["dt"], "sim_ms_per_step": W["T_ms"],
+            "time_steps_per_step": STEPS_PER_SIM,
+            "background": f"{W['bg_K']} Poisson sources x {W['bg_rate_hz']} Hz x {W['bg_w_nS']} nS",
+            "model": "classic squid-axon HH (Na, K, leak)", "precision_mode": "fast",
+            "l2": "inputs larger than L2 (CSR 800 MB vs 129 MB L2)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(MEASURED_PEAKS)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def mufu_ops_per_neuron_step(model):
+    """Algorithmic transcendental work of one exponential-Euler neuron step:
+    one exponential per exp/sigmoid/linoid rate (two for bell), one division
+    per sigmoid/linoid rate, per gate one division (p_inf) and one
+    exponential (the relaxation factor), and for V one division (V_inf) and
+    one exponential."""
+    n = 0
+    for ch in model["channels"]:
+        for g in ch["gates"]:
+            for f in (g["f1"], g["f2"]):
+                n += {"const": 0, "exp": 1, "sigmoid": 2, "linoid": 2, "bell": 3}[f[0]]
+            n += 2
+    return n + 2
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_21407_gb300 import hh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    # every rank simulates its own replica (independent networks: no data-path collective)
+    g = inp.network(n=W["n"], k_in=W["k_in"], exc_frac=W["exc_frac"], seed=W["seed"] + rank,
+                    mu=W["mu"], sigma=W["sigma"])
+    net = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
+                     delay_steps=DELAY, bg=BG, seed=W["seed"] + rank, precision=hh.HH_PREC_FAST,
+                     stream=stream.cuda_stream)
+    net.set_channels(0, inp.CLASSIC_HH)
+    out_deg = np.diff(net.readout(hh.HH_READ_N_OUT))
+    out_deg_t = torch.as_tensor(out_deg, device=dev)
+    V0_dev = torch.as_tensor(g["V0"], device=dev)
+    cap = 8_000_000
+    rec, buf = hh.make_record(W["n"], STEPS_PER_SIM, spike_cap=cap, device=dev)
+
+    def step():
+        with torch.cuda.stream(stream):
+            buf["counts"].zero_()
+            buf["n_spikes"].zero_()
+        net.reset(V0_dev)
+        net.step(STEPS_PER_SIM, rec=rec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    spikes_total = 0
+    events_total = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    # activity of the last step (every step simulates the same network from the same state)
+    counts = buf["counts"]
+    spikes_total = int(counts.sum().item()) * args.steps
+    events_total = int((counts.to(torch.int64) * out_deg_t).sum().item()) * args.steps
+    status = int(net.readout(hh.HH_READ_STATUS)[0])
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    tot = torch.tensor([spikes_total, events_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    neuron_steps = float(W["n"]) * STEPS_PER_SIM * args.steps * world
+    value = neuron_steps / (ms_max * 1e-3)
+    events_per_s = float(tot[1].item()) / (ms_max * 1e-3)
+    mean_rate = float(tot[0].item()) / (W["n"] * world * args.steps * W["T_ms"] * 1e-3)
+
+    # kernel timing pass (hh_profile brackets each launch with CUDA events on
+    # the network's stream); not part of the timed region above
+    net.profile(True)
+    step()
+    torch.cuda.synchronize()
+    kt = net.kernel_times()
+    net.profile(False)
+
+    # end-to-end through the public API with host buffers: H2D of the step's
+    # initial state from pinned memory, D2H of the spike counts and raster
+    V0_host = torch.as_tensor(g["V0"]).pin_memory()
+    counts_host = torch.empty(W["n"], dtype=torch.int32).pin_memory()
+    spikes_host = torch.empty((cap, 3), dtype=torch.int32).pin_memory()
+    nsp_host = torch.empty(1, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    d2h = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            buf["counts"].zero_()
+            buf["n_spikes"].zero_()
+        net.reset(V0_host)
+        net.step(STEPS_PER_SIM, rec=rec)
+        with torch.cuda.stream(stream):
+            counts_host.copy_(buf["counts"], non_blocking=True)
+            nsp_host.copy_(buf["n_spikes"], non_blocking=True)
+        stream.synchronize()
+        nsp = min(int(nsp_host.item()), cap)
+        with torch.cuda.stream(stream):
+            spikes_host[:nsp].copy_(buf["spikes"][:nsp], non_blocking=True)
+        stream.synchronize()
+        d2h = counts_host.numel() * 4 + 8 + nsp * 12
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = float(W["n"]) * STEPS_PER_SIM * e2e_steps * world / float(te.item())
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        n_launch_neuron, neuron_ms = kt["neuron"]
+        n_launch_route, route_ms = kt["route"]
+        avg_neuron_ms = neuron_ms / max(1, n_launch_neuron)
+        steps_per_launch = DELAY
+        mufu = mufu_ops_per_neuron_step(inp.CLASSIC_HH)
+        achieved_gops = mufu * W["n"] * steps_per_launch / (avg_neuron_ms * 1e-3) / 1e9
+        peak_gops = SM_COUNT * MUFU_PER_SM_CLK * sm_max * 1e6 / 1e9
+        cpu = cpu_baseline_sample(cores=os.cpu_count()) if not args.no_cpu_baseline else None
+        windows = STEPS_PER_SIM // DELAY
+        line = {
+            "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
+            "value": value, "unit": "neuron-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(),
+            "synaptic_events_per_s": events_per_s, "mean_rate_hz": mean_rate,
+            "status_bits": status,
+            "e2e": {"value": e2e_value, "unit": "neuron-steps/s",
+                    "h2d_bytes_per_step": W["n"] * 4, "d2h_bytes_per_step": d2h},
+            "gpu_launches": (1 + 2 * windows) * args.steps * world,
+            "kernels": {"neuron_window": {"launches_per_step": n_launch_neuron,
+                                          "avg_us": avg_neuron_ms * 1e3,
+                                          "share_of_step": neuron_ms / max(1e-9, neuron_ms + route_ms)},
+                        "route": {"launches_per_step": n_launch_route,
+                                  "avg_us": route_ms / max(1, n_launch_route) * 1e3}},
+            "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops,
+                         "unit": "Gop/s (SFU-class: exp + div)",
+                         "frac": achieved_gops / peak_gops, "traffic": None,
+                         "peak_source": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} SFU ops/clk x "
+                                        f"{sm_max:.0f} MHz ({pk_kind} sm_max)",
+                         "ops_per_neuron_step": mufu, "kernel": "k_net_window"},
+            "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    net.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_sample(cores, sim_steps=None):
+    """The FP64 oracle on the host cores: the full 38,000-neuron network for a
+    bounded number of time steps (default 2,000 = 50 ms), timed as the
+    difference of a run with and without the steps (graph transposition and
+    allocation excluded)."""
+    import oracle
+    sim_steps = sim_steps or int(os.environ.get("HH_CPU_SAMPLE_STEPS", "2000"))
+    g = inp.network(n=W["n"], k_in=W["k_in"], exc_frac=W["exc_frac"], seed=W["seed"],
+                    mu=W["mu"], sigma=W["sigma"])
+    t0 = time.perf_counter()
+    oracle.simulate_network(inp.CLASSIC_HH, g, 1, W["dt"], DELAY, SYN, bg=BG, seed=W["seed"],
+                            spk_cap=4, n_threads=cores)
+    base = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = oracle.simulate_network(inp.CLASSIC_HH, g, sim_steps + 1, W["dt"], DELAY, SYN, bg=BG,
+                                seed=W["seed"], spk_cap=4, n_threads=cores)
+    full = time.perf_counter() - t0
+    dt_s = max(1e-9, full - base)
+    return {"value": W["n"] * sim_steps / dt_s, "unit": "neuron-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sim_steps} time steps ({sim_steps * W['dt']:.0f} ms) of the full "
+                      f"38,000-neuron network, FP64, OpenMP over neurons; "
+                      f"{int(r['counts'].sum())} spikes"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    sample_steps = int(os.environ.get("HH_REF_SAMPLE_STEPS", "400"))
+    import oracle
+    g = inp.network(n=W["n"], k_in=W["k_in"], exc_frac=W["exc_frac"], seed=W["seed"],
+                    mu=W["mu"], sigma=W["sigma"])
+
+    def one():
+        t0 = time.perf_counter()
+        oracle.simulate_network(inp.CLASSIC_HH, g, sample_steps, W["dt"], DELAY, SYN, bg=BG,
+                                seed=W["seed"], spk_cap=4, n_threads=cores)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one()
+    times = [one() for _ in range(args.steps)]
+    tot = sum(times)
+    value = W["n"] * sample_steps * args.steps / tot
+    line = {"impl": "reference", "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
+            "value": value, "unit": "neuron-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": "neuron-steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"each step: {sample_steps} time steps of the full 38,000-neuron "
+                                       f"network (graph transposition included), FP64"},
+            "e2e": {"value": value, "unit": "neuron-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ncu_case():
+    """Small fixed case for ncu captures: the benchmark network, 120 time steps
+    (three delay windows), then one open-loop routing launch of a 40-step
+    raster with 1% of the neurons spiking per step."""
+    import torch
+
+    from paper_2601_21407_gb300 import hh
+    torch.cuda.set_device(0)
+    g = inp.network(n=W["n"], k_in=W["k_in"], exc_frac=W["exc_frac"], seed=W["seed"],
+                    mu=W["mu"], sigma=W["sigma"])
+    net = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
+                     delay_steps=DELAY, bg=BG, seed=W["seed"], precision=hh.HH_PREC_FAST)
+    net.set_channels(0, inp.CLASSIC_HH)
+    rec, b = hh.make_record(W["n"], 3 * DELAY, spike_cap=100_000)
+    net.step(3 * DELAY, rec=rec)
+    st, ix = inp.spike_raster(W["n"], DELAY, W["n"] // 100, 1)
+    sE = torch.zeros((2 * DELAY, W["n"]), dtype=torch.int64, device="cuda")
+    sI = torch.zeros_like(sE)
+    net.route_spikes(torch.as_tensor(st, device="cuda"), torch.as_tensor(ix, device="cuda"),
+                     2 * DELAY, sE, sI)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "network38k", "spikes": int(b["n_spikes"].item()),
+                      "raster_events": int(len(st)) * W["k_in"]}))
+    net.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run the small fixed case used for ncu captures and exit")
+    args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case()
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

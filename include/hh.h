@@ -1,0 +1,313 @@
+/*
+ * hh.h -- C ABI of libhh, the GB300 (sm_103a) Hodgkin-Huxley hot path.
+ *
+ * The library advances populations and networks of conductance-based
+ * Hodgkin-Huxley point neurons with hand-written CUDA kernels:
+ *   - voltage-dependent alpha/beta (or p_inf/tau) rate functions and the
+ *     exponential-Euler gate update of every channel gate
+ *     (Methods, Eq. hh_eq_full, second line; "Simplified discretization");
+ *   - membrane integration C_m dV/dt = I - sum_X gbar_X eta_X(p)(V - E_X)
+ *     - g_E (V - E_E) - g_I (V - E_I) with the conductances frozen over the
+ *     step (exponential Euler), or explicit Euler (Eq. hh_dyn_simplified);
+ *   - upward threshold crossing (spike) detection with linear interpolation
+ *     of the crossing time;
+ *   - exponential synaptic conductances (E/IPSP filters) fed through a
+ *     fixed synaptic delay by spike propagation over a CSR graph, plus a
+ *     Poisson background drive (Methods, "Cerebral cortex network").
+ *
+ * Conventions shared by every call
+ *   Units: V and E in mV, time in ms, currents in uA/cm^2, membrane
+ *   conductances in mS/cm^2, capacitance in uF/cm^2, synaptic weights and
+ *   g_E/g_I in nS (1 nS = 1e-6 mS / area_cm2), Ca in uM.
+ *   Memory: pointers marked "any memory" may be host (pageable or pinned) or
+ *   device pointers; the library copies them during the call (CUDA unified
+ *   addressing decides the direction).  Pointers marked "device" must be
+ *   device memory that the caller owns and keeps alive until the work queued
+ *   on the network's stream has finished.  The library owns all network
+ *   state; nothing it allocates is visible to the caller except through
+ *   hh_readout.
+ *   Streams: every call that launches work enqueues it on the stream given
+ *   at creation and returns without waiting, unless stated otherwise.
+ *   Errors: every call returns an hh_status; no exception or signal crosses
+ *   the ABI.  hh_last_error() gives a thread-local message for the last
+ *   failure of the calling thread.  Asynchronous CUDA errors and device-side
+ *   status bits (spike-buffer overflow, non-finite V) are reported by the
+ *   next call that synchronises, and by hh_readout(HH_READ_STATUS).
+ *   Determinism: results depend only on the inputs and the seed.  Synaptic
+ *   input is accumulated in 64-bit fixed point (units of 2^-32 nS), so the
+ *   order in which spikes are delivered does not change any bit.
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hh_net hh_net; /* opaque; created by hh_create_network */
+
+typedef enum {
+    HH_OK = 0,
+    HH_EINVAL = 1,       /* an argument is out of range or inconsistent */
+    HH_ENOMEM = 2,       /* a device or host allocation failed */
+    HH_ECUDA = 3,        /* a CUDA call failed (message in hh_last_error) */
+    HH_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+    HH_ESTATE = 5,       /* the call is not valid in the network's state */
+    HH_EUNSUPPORTED = 6, /* the request is valid but not implemented */
+    HH_EOVERFLOW = 7     /* a caller buffer was too small (data truncated) */
+} hh_status;
+
+/* ------------------------------------------------------------------ */
+/* Neuron models (user-defined ion channels)                            */
+/* ------------------------------------------------------------------ */
+
+/* Closed forms of a rate function r(V) = c + form(V)   (Methods, Eq.
+ * hh_eq_full: "the specific form of eta_X, alpha_p and beta_p depends on
+ * the ion X and sub-unit p"):
+ *   HH_FN_CONST   a
+ *   HH_FN_EXP     a * exp((V - vh)/k)
+ *   HH_FN_SIGMOID a / (1 + exp((V - vh)/k))
+ *   HH_FN_LINOID  a (V - vh) / (1 - exp(-(V - vh)/k)), equal to a k at V = vh
+ *   HH_FN_BELL    a / (exp((V - vh)/k) + exp((V - vh2)/k2))            */
+enum { HH_FN_CONST = 0, HH_FN_EXP = 1, HH_FN_SIGMOID = 2, HH_FN_LINOID = 3, HH_FN_BELL = 4 };
+
+/* Gate kinds:
+ *   HH_GATE_AB     f1 = alpha(V), f2 = beta(V) in 1/ms;
+ *                  p_inf = alpha/(alpha+beta), tau = 1/(alpha+beta)
+ *   HH_GATE_INFTAU f1 = p_inf(V), f2 = tau(V) in ms
+ *   HH_GATE_CA     p_inf = Ca/(Ca + f1.a), tau = f2(V)  (Ca-dependent) */
+enum { HH_GATE_AB = 0, HH_GATE_INFTAU = 1, HH_GATE_CA = 2 };
+
+#define HH_MAX_CHANNELS 8        /* channels per model (leak counts)      */
+#define HH_MAX_GATES_PER_CHANNEL 3
+#define HH_MAX_GATES 8           /* gates per model, all channels          */
+#define HH_MAX_MODELS 4          /* models per network                     */
+
+typedef struct {
+    int32_t form; /* HH_FN_* */
+    float a, vh, k, vh2, k2, c;
+} hh_fn;
+
+typedef struct {
+    int32_t kind;  /* HH_GATE_* */
+    int32_t power; /* exponent of the gate in eta_X, 1..4 */
+    hh_fn f1, f2;
+} hh_gate;
+
+typedef struct {
+    float E_rev;   /* reversal potential E_X (mV) */
+    float gbar;    /* default maximal conductance (mS/cm^2) */
+    int32_t n_gates;
+    hh_gate gates[HH_MAX_GATES_PER_CHANNEL];
+} hh_channel;
+
+/* A point-neuron model: eta_X = prod_g p_g^power_g for each channel, and an
+ * optional first-order calcium pool fed by one channel:
+ *   d[Ca]/dt = -ca_k I_Ca - ([Ca] - ca_rest)/ca_tau,
+ * advanced by exponential Euler with I_Ca evaluated at V_t and the updated
+ * gates.  ca_channel = -1 disables the pool. */
+typedef struct {
+    float C_m; /* uF/cm^2 */
+    int32_t n_channels;
+    hh_channel channels[HH_MAX_CHANNELS];
+    int32_t ca_channel;
+    float ca_tau, ca_k, ca_rest;
+} hh_model_desc;
+
+/* ------------------------------------------------------------------ */
+/* Network creation                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Arithmetic of the neuron update.  Every mode forms each update as an
+ * increment, p += (p_inf - p)(1 - e^{-z}) and V += (I - I_ion)/G (1 -
+ * e^{-dt G/C_m}) with I_ion = sum_X g_X (V - E_X), which is the exponential-
+ * Euler map itself; the modes differ in how 1 - e^{-z}, the rates and the
+ * divisions are evaluated:
+ *   HH_PREC_FAST        FP32 on the SFU: ex2.approx for the exponentials of
+ *                       the rate functions, rcp.approx for divisions, and a
+ *                       degree-8 Taylor polynomial of 1 - e^{-z} for z < 0.5;
+ *   HH_PREC_ACCURATE    FP32 with IEEE division, expf and expm1f;
+ *   HH_PREC_COMPENSATED as ACCURATE, on a two-float (hi + lo) state: each
+ *                       increment is added by an error-free two-sum, so the
+ *                       state keeps the low bits of small increments over
+ *                       many steps.                                        */
+enum { HH_PREC_FAST = 0, HH_PREC_ACCURATE = 1, HH_PREC_COMPENSATED = 2 };
+enum { HH_V_EXP_EULER = 0, HH_V_FWD_EULER = 1 };
+
+typedef struct {
+    int64_t n_neurons;          /* N >= 1 (all networks together)            */
+    int32_t n_nets;             /* >= 1 independent networks, concatenated     */
+    const int64_t* net_offsets; /* host [n_nets+1] neuron offsets, or NULL
+                                   when n_nets == 1 (informational: networks
+                                   are independent because the CSR graph is
+                                   block-diagonal)                            */
+    double dt_ms;               /* time step (> 0)                            */
+    float v_threshold;          /* spike threshold theta (mV)                 */
+    int32_t v_update;           /* HH_V_*                                     */
+    int32_t precision;          /* HH_PREC_*                                  */
+    const float* V0;            /* [N] initial V, any memory (copied)        */
+    const float* I_const;       /* [N] constant injected current, any memory,
+                                   or NULL for none                            */
+    const uint8_t* model_id;    /* [N] model index per neuron (< n models),
+                                   any memory, or NULL for model 0             */
+    /* synapses: in-CSR by postsynaptic neuron (n_synapses = 0: none) */
+    int64_t n_synapses;
+    const int64_t* row_ptr;     /* [N+1], any memory; row_ptr[0] = 0,
+                                   nondecreasing, row_ptr[N] = n_synapses     */
+    const int32_t* col_idx;     /* [n_synapses] presynaptic index in [0, N)   */
+    const float* weight;        /* [n_synapses] nS, finite, 0 <= w < 65536    */
+    const uint8_t* is_inhibitory; /* [N] presynaptic type (selects tau_I and
+                                   E_I), any memory, or NULL: all excitatory  */
+    float tau_E, tau_I;         /* ms (> 0)                                   */
+    float E_E, E_I;             /* mV                                         */
+    int32_t delay_steps;        /* synaptic delay D in steps, 1..1024         */
+    float area_cm2;             /* membrane area converting nS to mS/cm^2     */
+    /* Poisson background: bg_sources independent sources per neuron, each at
+     * bg_rate_hz, every event adding bg_weight_nS to g_E */
+    float bg_rate_hz;
+    int32_t bg_sources;
+    float bg_weight_nS;
+    uint64_t seed;              /* Philox key for the background counts       */
+    void* stream;               /* cudaStream_t for all work, NULL = legacy   */
+} hh_net_desc;
+
+/* Create a network (Methods, Eq. hh_eq_full; "Cerebral cortex network").
+ * Copies every array of *d into library-owned device memory, transposes the
+ * in-CSR into an out-CSR (rows = presynaptic neuron) on the GPU, and sets
+ * V = V0, g_E = g_I = 0, t = 0.  No neuron model is installed yet:
+ * hh_set_channels must install every model index that model_id uses (it
+ * also sets those neurons' gates to p_inf(V) and Ca to ca_rest) before
+ * hh_step_n runs.
+ * Synchronous.  Errors: HH_EINVAL for a NULL/out-of-range argument or an
+ * invalid CSR (checked on the device for col_idx and weight), HH_ENOMEM,
+ * HH_ECUDA.  On error *out is NULL and nothing is leaked. */
+hh_status hh_create_network(const hh_net_desc* d, hh_net** out);
+
+/* Install neuron model `model_index` (Methods, "Flexibility and
+ * extensibility": users define the ion-channel dynamics; Eq. hh_eq_full).
+ *   m     : the model, host memory (copied).
+ *   gbar  : [m->n_channels][N] per-neuron maximal conductances (mS/cm^2),
+ *           any memory, or NULL to use m->channels[c].gbar for every neuron.
+ *           Only the entries of neurons whose model_id equals model_index
+ *           are used.
+ * Re-initialises the gates (and Ca) of every neuron of this model to their
+ * steady state at its current V.  Synchronous.
+ * Errors: HH_EINVAL (index >= HH_MAX_MODELS, a count above the HH_MAX_*
+ * limits, a power outside 1..4, an unknown form or kind, C_m <= 0),
+ * HH_ECUDA. */
+hh_status hh_set_channels(hh_net* net, int32_t model_index, const hh_model_desc* m,
+                          const float* gbar);
+
+/* ------------------------------------------------------------------ */
+/* Stepping                                                             */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t step;   /* absolute step index: V crossed theta between t = step*dt
+                       and (step+1)*dt */
+    int32_t neuron; /* neuron index */
+    float frac;     /* (theta - V_t)/(V_{t+1} - V_t) in [0, 1): the crossing
+                       time is (step + frac)*dt */
+} hh_spike;
+
+/* Caller-owned device buffers that hh_step_n fills.  Any field may be NULL
+ * (or zero) to skip that output. */
+typedef struct {
+    float* V_trace;           /* device [n_steps][n_trace]: V after each step */
+    const int32_t* trace_idx; /* device [n_trace] neuron indices, or NULL for
+                                 neurons 0..n_trace-1                         */
+    int32_t n_trace;
+    hh_spike* spikes;         /* device [spike_cap], unordered                */
+    int64_t spike_cap;
+    int64_t* n_spikes;        /* device counter the library adds the number of
+                                 spikes to (caller initialises it); spikes
+                                 beyond spike_cap are counted but not stored
+                                 and set HH_STATUS_SPIKE_OVERFLOW             */
+    int32_t* counts;          /* device [N] per-neuron spike counts, added to */
+} hh_record;
+
+/* Advance the network by n_steps time steps (Methods, Eq. hh_eq_full with
+ * the exponential-Euler discretisation; order per step: synaptic delivery
+ * and background into g_E/g_I, rates at V_t, gates, conductances, V, Ca,
+ * threshold test, spike propagation into the delay line, decay of g_E/g_I).
+ *   I_steps: device [n_steps][N] extra injected current per step, or NULL.
+ *   rec    : outputs, or NULL.
+ * Asynchronous on the network's stream.  Errors: HH_EINVAL (n_steps < 0,
+ * trace_idx out of range is not checked: the caller guarantees it),
+ * HH_ESTATE (a model index used by model_id was never installed), HH_ECUDA. */
+hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps,
+                    const hh_record* rec);
+
+/* Reset time to 0, V to V0 (any memory, [N]; NULL = the V0 given at
+ * creation), gates and Ca to steady state, g_E = g_I = 0, and clear the
+ * delay line and the status word.  Asynchronous. */
+hh_status hh_reset(hh_net* net, const float* V0);
+
+/* Open-loop spike routing (Methods, "Cerebral cortex network": synaptic
+ * delays and E/IPSP filters; the spike-delivery step of the network):
+ * for every spike (step s, neuron j) of the given list and every synapse
+ * j -> i of weight w, add round(w * 2^32) to
+ *   sum_E[s + D][i]  (j excitatory)  or  sum_I[s + D][i]  (j inhibitory),
+ * dropping arrivals at or after n_window.  This is the same routing kernel
+ * hh_step_n uses, run on a caller-given raster without neuron dynamics.
+ *   spk_step, spk_idx: device [n_spk]; spk_step >= 0, spk_idx in [0, N)
+ *                      (entries outside are skipped).
+ *   sum_E, sum_I     : device int64 [n_window][N], accumulated into (the
+ *                      caller zeroes them).
+ * Asynchronous.  Errors: HH_EINVAL, HH_ESTATE (network has no synapses). */
+hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* spk_idx,
+                          int64_t n_spk, int32_t n_window, int64_t* sum_E, int64_t* sum_I);
+
+/* ------------------------------------------------------------------ */
+/* Readout                                                              */
+/* ------------------------------------------------------------------ */
+
+enum {
+    HH_READ_V = 0,       /* float [N] membrane potential (hi part)         */
+    HH_READ_GATES = 1,   /* float [HH_MAX_GATES][N] gate values            */
+    HH_READ_CA = 2,      /* float [N]                                       */
+    HH_READ_G_SYN = 3,   /* float [2][N] g_E then g_I (nS)                  */
+    HH_READ_STATUS = 4,  /* int32: OR of HH_STATUS_* bits since the last reset */
+    HH_READ_TIME = 5,    /* int64: steps advanced since creation / reset    */
+    HH_READ_N_OUT = 6,   /* int64 [N+1] out-CSR row pointer (rows = pre)    */
+    HH_READ_PROFILE = 7  /* hh_kernel_time [HH_KERNEL_COUNT] since hh_profile(net, 1) */
+};
+enum { HH_STATUS_SPIKE_OVERFLOW = 1, HH_STATUS_NONFINITE = 2 };
+
+/* Copy a quantity into dst (any memory) of cap_bytes bytes; *n_bytes (if
+ * not NULL) receives the bytes written.  Synchronous: waits for the work
+ * queued on the network's stream.  Errors: HH_EINVAL (unknown `what`),
+ * HH_EOVERFLOW (cap_bytes too small: nothing is written), HH_ECUDA (also for
+ * an asynchronous error of earlier queued work). */
+hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap_bytes, size_t* n_bytes);
+
+/* Kernel timing (a tracing aid for benchmarks).  While enabled, hh_step_n
+ * brackets every neuron-update launch and every routing launch with CUDA
+ * events on the network's stream; HH_READ_PROFILE returns, per kernel class,
+ * the number of launches and the summed event-to-event time.  Enabling
+ * clears the totals; disabling keeps them for readout.  Timing adds a few
+ * microseconds of event records per launch, so time throughput with it off.
+ * Errors: HH_EINVAL, HH_ECUDA. */
+typedef struct {
+    int64_t launches;
+    double total_ms;
+} hh_kernel_time;
+enum { HH_KERNEL_NEURON = 0, HH_KERNEL_ROUTE = 1, HH_KERNEL_COUNT = 2 };
+hh_status hh_profile(hh_net* net, int32_t enable);
+
+/* Release everything the network owns (waits for its queued work). NULL ok. */
+void hh_destroy(hh_net* net);
+
+/* Thread-local description of the last error of the calling thread. */
+const char* hh_last_error(void);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+int32_t hh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HH_H */

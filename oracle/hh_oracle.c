@@ -264,14 +264,17 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The uniform word used for the background count of neuron i at step t. */
+/* The uniform word used for the background count of neuron i at step t:
+ * one Philox block serves four consecutive steps.  Counter = (q, i, 1, q>>32)
+ * with q = t / 4, key = (seed, seed >> 32); the word is output[t mod 4]. */
 uint32_t or_background_word(uint64_t seed, int64_t t, int64_t i)
 {
-    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)i, 1u, (uint32_t)((uint64_t)t >> 32)};
+    uint64_t q = (uint64_t)t >> 2;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t out[4];
     or_philox4x32_10(ctr, key, out);
-    return out[0];
+    return out[(uint64_t)t & 3u];
 }
 
 /* Poisson CDF thresholds on the 2^32 grid: thr[j] = min(2^32, floor(F(j) 2^32))

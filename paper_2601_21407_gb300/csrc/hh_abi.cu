@@ -1,0 +1,844 @@
+// C ABI of libhh (see include/hh.h): argument validation, ownership of the
+// network's device memory, model preparation and the launch schedule.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hh_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+hh_status fail(hh_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define HH_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? HH_ENOMEM : HH_ECUDA,          \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+}  // namespace
+
+struct hh_net {
+    int64_t N = 0;
+    int32_t n_nets = 1;
+    double dt = 0.0;
+    float theta = 0.0f;
+    int32_t v_update = 0, precision = 0;
+    cudaStream_t st = nullptr;
+    int64_t t = 0;
+    int64_t window_index = 0;
+
+    hh::DevModels models{};
+    bool installed[HH_MAX_MODELS] = {false, false, false, false};
+    int32_t max_model_used = 0;
+
+    // state and per-neuron inputs (device)
+    float *V = nullptr, *Vlo = nullptr, *P = nullptr, *Plo = nullptr, *Ca = nullptr;
+    float *gE = nullptr, *gI = nullptr, *V0 = nullptr, *I_const = nullptr, *gbar = nullptr;
+    uint8_t *model_id = nullptr, *inh = nullptr;
+    int32_t *trace_slot = nullptr, *status = nullptr;
+
+    // synapses
+    bool has_syn = false;
+    int64_t S = 0;
+    int64_t* out_ptr = nullptr;
+    int32_t* out_post = nullptr;
+    float* out_w = nullptr;
+    int64_t *ringE = nullptr, *ringI = nullptr;
+    int32_t D = 1, R = 1;
+    float tau_E = 1.0f, tau_I = 1.0f, E_E = 0.0f, E_I = 0.0f, area = 1.0f;
+
+    // background
+    bool has_bg = false;
+    float bg_w = 0.0f;
+    uint64_t seed = 0;
+    int32_t n_thr = 0;
+    unsigned long long thr[hh::kMaxPoisson] = {};
+
+    hh::SpikeList list{};
+
+    // kernel timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    hh_kernel_time ktime[HH_KERNEL_COUNT] = {};
+
+    cudaEvent_t take_event()
+    {
+        cudaEvent_t e = nullptr;
+        if (!ev_pool.empty()) {
+            e = ev_pool.back();
+            ev_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        return e;
+    }
+
+    cudaError_t harvest()
+    {
+        for (auto& u : ev_used) {
+            float ms = 0.0f;
+            cudaError_t e = cudaEventElapsedTime(&ms, u.second.first, u.second.second);
+            if (e != cudaSuccess)
+                return e;
+            ktime[u.first].launches += 1;
+            ktime[u.first].total_ms += ms;
+            ev_pool.push_back(u.second.first);
+            ev_pool.push_back(u.second.second);
+        }
+        ev_used.clear();
+        return cudaSuccess;
+    }
+
+    std::vector<void*> allocs;
+
+    template <class T>
+    cudaError_t alloc(T** p, size_t count)
+    {
+        *p = nullptr;
+        if (count == 0)
+            count = 1;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+        if (e == cudaSuccess)
+            allocs.push_back(*p);
+        return e;
+    }
+
+    void release()
+    {
+        if (st)
+            cudaStreamSynchronize(st);
+        else
+            cudaDeviceSynchronize();
+        for (void* p : allocs)
+            cudaFree(p);
+        allocs.clear();
+        for (auto& u : ev_used) {
+            cudaEventDestroy(u.second.first);
+            cudaEventDestroy(u.second.second);
+        }
+        ev_used.clear();
+        for (cudaEvent_t e : ev_pool)
+            cudaEventDestroy(e);
+        ev_pool.clear();
+    }
+
+    hh::NeuronParams neuron_params() const
+    {
+        hh::NeuronParams p{};
+        p.N = N;
+        p.dt = (float)dt;
+        p.theta = theta;
+        p.v_update = v_update;
+        p.V = V;
+        p.Vlo = Vlo;
+        p.P = P;
+        p.Plo = Plo;
+        p.Ca = Ca;
+        p.gE = gE;
+        p.gI = gI;
+        p.model_id = model_id;
+        p.gbar = gbar;
+        p.I_const = I_const;
+        p.trace_slot = nullptr;
+        p.status = status;
+        p.ringE = ringE;
+        p.ringI = ringI;
+        p.R = R;
+        p.E_E = E_E;
+        p.E_I = E_I;
+        p.decE = (float)std::exp(-dt / (double)tau_E);
+        p.decI = (float)std::exp(-dt / (double)tau_I);
+        p.to_mS = (float)(1e-6 / (double)area);
+        p.bg_n = has_bg ? n_thr : 0;
+        p.bg_w = bg_w;
+        p.seed = seed;
+        for (int j = 0; j < hh::kMaxPoisson; ++j)
+            p.bg_thr[j] = thr[j];
+        return p;
+    }
+
+    hh::RouteParams route_params() const
+    {
+        hh::RouteParams r{};
+        r.N = N;
+        r.out_ptr = out_ptr;
+        r.out_post = out_post;
+        r.out_w = out_w;
+        r.inh = inh;
+        r.ringE = ringE;
+        r.ringI = ringI;
+        r.R = R;
+        r.D = D;
+        r.open_loop = 0;
+        r.n_window = 0;
+        return r;
+    }
+};
+
+namespace {
+
+// Poisson CDF thresholds on the 2^32 grid (inversion sampling of the
+// background count): thr[j] = min(2^32, floor(F(j) 2^32)), F accumulated as
+// pmf_0 = e^-lambda, pmf_j = (pmf_{j-1} lambda)/j; the last entry is 2^32.
+int32_t poisson_thresholds(double lambda, unsigned long long* thr, int32_t cap)
+{
+    const double two32 = 4294967296.0;
+    double pmf = std::exp(-lambda), F = pmf;
+    for (int32_t j = 0; j < cap; ++j) {
+        if (j > 0) {
+            pmf = (pmf * lambda) / (double)j;
+            F = F + pmf;
+        }
+        const double x = std::floor(F * two32);
+        unsigned long long v = x >= two32 ? (1ull << 32) : (unsigned long long)x;
+        if (j == cap - 1)
+            v = 1ull << 32;
+        thr[j] = v;
+        if (v == (1ull << 32))
+            return j + 1;
+    }
+    return cap;
+}
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+hh_status check_fn(const hh_fn& f, const char* where)
+{
+    if (f.form < HH_FN_CONST || f.form > HH_FN_BELL)
+        return fail(HH_EINVAL, "%s: unknown rate form %d", where, f.form);
+    if (!finite_f(f.a) || !finite_f(f.c) || !finite_f(f.vh) || !finite_f(f.k) || !finite_f(f.vh2) ||
+        !finite_f(f.k2))
+        return fail(HH_EINVAL, "%s: non-finite rate parameter", where);
+    if (f.form != HH_FN_CONST && f.k == 0.0f)
+        return fail(HH_EINVAL, "%s: k must be non-zero", where);
+    if (f.form == HH_FN_BELL && f.k2 == 0.0f)
+        return fail(HH_EINVAL, "%s: k2 must be non-zero", where);
+    return HH_OK;
+}
+
+hh::DevFn prep_fn(const hh_fn& f)
+{
+    hh::DevFn d{};
+    d.form = f.form;
+    d.a = f.a;
+    d.c = f.c;
+    d.vh = f.vh;
+    d.k = f.k;
+    const double k = f.k != 0.0f ? (double)f.k : 1.0;
+    const double k2 = f.k2 != 0.0f ? (double)f.k2 : 1.0;
+    d.ik = (float)(1.0 / k);
+    d.s = (float)(1.4426950408889634 / k);
+    d.b = (float)(-(double)f.vh * 1.4426950408889634 / k);
+    d.vh2 = f.vh2;
+    d.ik2 = (float)(1.0 / k2);
+    d.s2 = (float)(1.4426950408889634 / k2);
+    d.b2 = (float)(-(double)f.vh2 * 1.4426950408889634 / k2);
+    return d;
+}
+
+hh_status prep_model(const hh_model_desc* m, double dt, hh::DevModel* out)
+{
+    if (!(m->C_m > 0.0f) || !finite_f(m->C_m))
+        return fail(HH_EINVAL, "model: C_m must be > 0");
+    if (m->n_channels < 1 || m->n_channels > HH_MAX_CHANNELS)
+        return fail(HH_EINVAL, "model: n_channels %d outside 1..%d", m->n_channels, HH_MAX_CHANNELS);
+    hh::DevModel d{};
+    d.C_m = m->C_m;
+    d.inv_C = (float)(1.0 / (double)m->C_m);
+    d.n_ch = m->n_channels;
+    d.ca_ch = -1;
+    int q = 0;
+    for (int c = 0; c < m->n_channels; ++c) {
+        const hh_channel& ch = m->channels[c];
+        if (ch.n_gates < 0 || ch.n_gates > HH_MAX_GATES_PER_CHANNEL)
+            return fail(HH_EINVAL, "channel %d: n_gates %d outside 0..%d", c, ch.n_gates,
+                        HH_MAX_GATES_PER_CHANNEL);
+        if (!finite_f(ch.E_rev) || !finite_f(ch.gbar) || ch.gbar < 0.0f)
+            return fail(HH_EINVAL, "channel %d: E_rev and gbar must be finite, gbar >= 0", c);
+        d.E[c] = ch.E_rev;
+        d.gbar[c] = ch.gbar;
+        d.ch_first[c] = q;
+        d.ch_ng[c] = ch.n_gates;
+        for (int g = 0; g < ch.n_gates; ++g) {
+            if (q >= HH_MAX_GATES)
+                return fail(HH_EINVAL, "model: more than %d gates", HH_MAX_GATES);
+            const hh_gate& gt = ch.gates[g];
+            if (gt.kind < HH_GATE_AB || gt.kind > HH_GATE_CA)
+                return fail(HH_EINVAL, "channel %d gate %d: unknown kind %d", c, g, gt.kind);
+            if (gt.power < 1 || gt.power > 4)
+                return fail(HH_EINVAL, "channel %d gate %d: power %d outside 1..4", c, g, gt.power);
+            hh_status s = check_fn(gt.f1, "f1");
+            if (s != HH_OK)
+                return s;
+            if ((s = check_fn(gt.f2, "f2")) != HH_OK)
+                return s;
+            if (gt.kind == HH_GATE_CA && !(gt.f1.a > 0.0f))
+                return fail(HH_EINVAL, "channel %d gate %d: Ca half-activation must be > 0", c, g);
+            d.g[q].kind = gt.kind;
+            d.g[q].power = gt.power;
+            d.g[q].f1 = prep_fn(gt.f1);
+            d.g[q].f2 = prep_fn(gt.f2);
+            d.gate_ch[q] = c;
+            d.gate_last[q] = (g == ch.n_gates - 1);
+            d.gate_E[q] = ch.E_rev;
+            d.gate_ca[q] = 0;
+            ++q;
+        }
+    }
+    d.n_gates = q;
+    if (m->ca_channel >= 0) {
+        if (m->ca_channel >= m->n_channels)
+            return fail(HH_EINVAL, "model: ca_channel %d out of range", m->ca_channel);
+        if (m->channels[m->ca_channel].n_gates < 1)
+            return fail(HH_EINVAL, "model: the calcium channel needs at least one gate");
+        if (!(m->ca_tau > 0.0f) || !finite_f(m->ca_k) || !finite_f(m->ca_rest) || m->ca_rest < 0.0f)
+            return fail(HH_EINVAL, "model: calcium pool needs ca_tau > 0, finite ca_k, ca_rest >= 0");
+        d.ca_ch = m->ca_channel;
+        d.ca_tau = m->ca_tau;
+        d.ca_k = m->ca_k;
+        d.ca_rest = m->ca_rest;
+        d.ca_decay = (float)std::exp(-dt / (double)m->ca_tau);
+        const int last = d.ch_first[m->ca_channel] + d.ch_ng[m->ca_channel] - 1;
+        d.gate_ca[last] = 1;
+    } else if (m->ca_channel != -1) {
+        return fail(HH_EINVAL, "model: ca_channel must be -1 or a channel index");
+    }
+    for (int g = 0; g < d.n_gates; ++g)
+        if (d.g[g].kind == HH_GATE_CA && d.ca_ch < 0)
+            return fail(HH_EINVAL, "model: a Ca-dependent gate needs a calcium pool");
+    *out = d;
+    return HH_OK;
+}
+
+template <class T>
+cudaError_t copy_in(T* dst, const T* src, size_t count, cudaStream_t st)
+{
+    if (count == 0)
+        return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDefault, st);
+    if (e != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(st);
+}
+
+hh_status build_network(const hh_net_desc* d, hh_net* n)
+{
+    const int64_t N = d->n_neurons;
+    n->N = N;
+    n->n_nets = d->n_nets;
+    n->dt = d->dt_ms;
+    n->theta = d->v_threshold;
+    n->v_update = d->v_update;
+    n->precision = d->precision;
+    n->st = (cudaStream_t)d->stream;
+    cudaStream_t st = n->st;
+
+    HH_CUDA(n->alloc(&n->V, N));
+    HH_CUDA(n->alloc(&n->V0, N));
+    HH_CUDA(n->alloc(&n->Ca, N));
+    HH_CUDA(n->alloc(&n->gE, N));
+    HH_CUDA(n->alloc(&n->gI, N));
+    HH_CUDA(n->alloc(&n->P, (size_t)N * hh::kMaxGates));
+    HH_CUDA(n->alloc(&n->status, 1));
+    HH_CUDA(n->alloc(&n->trace_slot, N));
+    if (n->precision == HH_PREC_COMPENSATED) {
+        HH_CUDA(n->alloc(&n->Vlo, N));
+        HH_CUDA(n->alloc(&n->Plo, (size_t)N * hh::kMaxGates));
+    }
+    HH_CUDA(copy_in(n->V0, d->V0, (size_t)N, st));
+    HH_CUDA(cudaMemcpyAsync(n->V, n->V0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    HH_CUDA(cudaMemsetAsync(n->P, 0, (size_t)N * hh::kMaxGates * sizeof(float), st));
+    HH_CUDA(cudaMemsetAsync(n->Ca, 0, N * sizeof(float), st));
+    HH_CUDA(cudaMemsetAsync(n->gE, 0, N * sizeof(float), st));
+    HH_CUDA(cudaMemsetAsync(n->gI, 0, N * sizeof(float), st));
+    HH_CUDA(cudaMemsetAsync(n->status, 0, sizeof(int32_t), st));
+    if (n->Vlo) {
+        HH_CUDA(cudaMemsetAsync(n->Vlo, 0, N * sizeof(float), st));
+        HH_CUDA(cudaMemsetAsync(n->Plo, 0, (size_t)N * hh::kMaxGates * sizeof(float), st));
+    }
+    if (d->I_const) {
+        HH_CUDA(n->alloc(&n->I_const, N));
+        HH_CUDA(copy_in(n->I_const, d->I_const, (size_t)N, st));
+    }
+    if (d->model_id) {
+        std::vector<uint8_t> h(N);
+        HH_CUDA(cudaMemcpy(h.data(), d->model_id, N, cudaMemcpyDefault));
+        int32_t mx = 0;
+        for (int64_t i = 0; i < N; ++i)
+            mx = h[i] > mx ? h[i] : mx;
+        if (mx >= HH_MAX_MODELS)
+            return fail(HH_EINVAL, "model_id %d >= HH_MAX_MODELS", mx);
+        n->max_model_used = mx;
+        HH_CUDA(n->alloc(&n->model_id, N));
+        HH_CUDA(copy_in(n->model_id, h.data(), (size_t)N, st));
+    }
+
+    // synapses: in-CSR -> out-CSR on the device
+    n->has_syn = d->n_synapses > 0;
+    if (d->n_synapses < 0)
+        return fail(HH_EINVAL, "n_synapses < 0");
+    n->tau_E = d->tau_E;
+    n->tau_I = d->tau_I;
+    n->E_E = d->E_E;
+    n->E_I = d->E_I;
+    n->area = d->area_cm2;
+    n->D = d->delay_steps;
+    if (n->has_syn || d->bg_sources > 0) {
+        if (!(d->tau_E > 0.0f) || !(d->tau_I > 0.0f) || !(d->area_cm2 > 0.0f) ||
+            !finite_f(d->E_E) || !finite_f(d->E_I))
+            return fail(HH_EINVAL, "synapses need tau_E, tau_I, area_cm2 > 0 and finite E_E, E_I");
+    }
+    if (n->has_syn) {
+        if (d->delay_steps < 1 || d->delay_steps > 1024)
+            return fail(HH_EINVAL, "delay_steps %d outside 1..1024", d->delay_steps);
+        if (!d->row_ptr || !d->col_idx || !d->weight)
+            return fail(HH_EINVAL, "row_ptr, col_idx and weight are required when n_synapses > 0");
+        const int64_t S = d->n_synapses;
+        n->S = S;
+        std::vector<int64_t> rp(N + 1);
+        HH_CUDA(cudaMemcpy(rp.data(), d->row_ptr, (N + 1) * sizeof(int64_t), cudaMemcpyDefault));
+        if (rp[0] != 0 || rp[N] != S)
+            return fail(HH_EINVAL, "row_ptr[0] must be 0 and row_ptr[N] = n_synapses");
+        for (int64_t i = 0; i < N; ++i) {
+            if (rp[i + 1] < rp[i])
+                return fail(HH_EINVAL, "row_ptr decreases at row %lld", (long long)i);
+            if (rp[i + 1] - rp[i] > 32767)
+                return fail(HH_EINVAL, "in-degree of neuron %lld exceeds 32767", (long long)i);
+        }
+        int32_t* col = nullptr;
+        float* w = nullptr;
+        int64_t* drp = nullptr;
+        int32_t* cnt = nullptr;
+        unsigned long long* cursor = nullptr;
+        hh_status rc = HH_OK;
+        auto cleanup = [&]() {
+            cudaStreamSynchronize(st);
+            for (void* p : {(void*)col, (void*)w, (void*)drp, (void*)cnt, (void*)cursor})
+                if (p)
+                    cudaFree(p);
+        };
+        do {
+            cudaError_t e;
+            if ((e = cudaMalloc(&col, S * sizeof(int32_t))) != cudaSuccess ||
+                (e = cudaMalloc(&w, S * sizeof(float))) != cudaSuccess ||
+                (e = cudaMalloc(&drp, (N + 1) * sizeof(int64_t))) != cudaSuccess ||
+                (e = cudaMalloc(&cnt, (N + 1) * sizeof(int32_t))) != cudaSuccess ||
+                (e = cudaMalloc(&cursor, (N + 1) * sizeof(unsigned long long))) != cudaSuccess) {
+                rc = fail(HH_ENOMEM, "allocating the CSR staging buffers: %s", cudaGetErrorString(e));
+                break;
+            }
+            if ((e = copy_in(col, d->col_idx, (size_t)S, st)) != cudaSuccess ||
+                (e = copy_in(w, d->weight, (size_t)S, st)) != cudaSuccess ||
+                (e = copy_in(drp, rp.data(), (size_t)N + 1, st)) != cudaSuccess ||
+                (e = cudaMemsetAsync(cnt, 0, (N + 1) * sizeof(int32_t), st)) != cudaSuccess ||
+                (e = hh::launch_csr_check(col, w, S, N, cnt + N, st)) != cudaSuccess) {
+                rc = fail(HH_ECUDA, "copying the CSR: %s", cudaGetErrorString(e));
+                break;
+            }
+            int32_t flag = 0;
+            if ((e = cudaMemcpyAsync(&flag, cnt + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                rc = fail(HH_ECUDA, "checking the CSR: %s", cudaGetErrorString(e));
+                break;
+            }
+            if (flag & 1) {
+                rc = fail(HH_EINVAL, "col_idx holds an index outside [0, N)");
+                break;
+            }
+            if (flag & 2) {
+                rc = fail(HH_EINVAL, "weight holds a value that is not finite or outside [0, 65536) nS");
+                break;
+            }
+            std::vector<int32_t> hc(N);
+            std::vector<int64_t> op(N + 1);
+            if ((e = hh::launch_count_pre(col, S, cnt, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(hc.data(), cnt, N * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                rc = fail(HH_ECUDA, "counting out-degrees: %s", cudaGetErrorString(e));
+                break;
+            }
+            op[0] = 0;
+            for (int64_t j = 0; j < N; ++j)
+                op[j + 1] = op[j] + hc[j];
+            if ((e = n->alloc(&n->out_ptr, N + 1)) != cudaSuccess ||
+                (e = n->alloc(&n->out_post, S)) != cudaSuccess ||
+                (e = n->alloc(&n->out_w, S)) != cudaSuccess) {
+                rc = fail(HH_ENOMEM, "allocating the out-CSR: %s", cudaGetErrorString(e));
+                break;
+            }
+            if ((e = copy_in(n->out_ptr, op.data(), (size_t)N + 1, st)) != cudaSuccess ||
+                (e = copy_in(reinterpret_cast<int64_t*>(cursor), op.data(), (size_t)N, st)) != cudaSuccess ||
+                (e = hh::launch_fill_out(drp, col, w, N, cursor, n->out_post, n->out_w, st)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                rc = fail(HH_ECUDA, "filling the out-CSR: %s", cudaGetErrorString(e));
+                break;
+            }
+        } while (0);
+        cleanup();
+        if (rc != HH_OK)
+            return rc;
+        if (d->is_inhibitory) {
+            HH_CUDA(n->alloc(&n->inh, N));
+            HH_CUDA(copy_in(n->inh, d->is_inhibitory, (size_t)N, st));
+        }
+    }
+    // background
+    if (d->bg_sources < 0 || !(d->bg_rate_hz >= 0.0f) || !(d->bg_weight_nS >= 0.0f) ||
+        !finite_f(d->bg_rate_hz) || !finite_f(d->bg_weight_nS))
+        return fail(HH_EINVAL, "background needs bg_sources >= 0, finite bg_rate_hz >= 0, bg_weight_nS >= 0");
+    n->has_bg = d->bg_sources > 0 && d->bg_rate_hz > 0.0f;
+    n->seed = d->seed;
+    n->bg_w = d->bg_weight_nS;
+    if (n->has_bg) {
+        const double lambda = (((double)d->bg_sources * (double)d->bg_rate_hz) * d->dt_ms) / 1000.0;
+        n->n_thr = poisson_thresholds(lambda, n->thr, hh::kMaxPoisson);
+    }
+    // delay ring and window spike lists
+    if (n->has_syn || n->has_bg) {
+        n->R = n->has_syn ? n->D : 1;
+        HH_CUDA(n->alloc(&n->ringE, (size_t)n->R * N));
+        HH_CUDA(n->alloc(&n->ringI, (size_t)n->R * N));
+        HH_CUDA(cudaMemsetAsync(n->ringE, 0, (size_t)n->R * N * sizeof(int64_t), st));
+        HH_CUDA(cudaMemsetAsync(n->ringI, 0, (size_t)n->R * N * sizeof(int64_t), st));
+        const int64_t W = n->has_syn ? n->D : 1;
+        n->list.cap = N * ((W + 1) / 2) + 32;
+        HH_CUDA(n->alloc(&n->list.step, n->list.cap));
+        HH_CUDA(n->alloc(&n->list.idx, n->list.cap));
+        HH_CUDA(n->alloc(&n->list.counter, 2));
+        HH_CUDA(cudaMemsetAsync(n->list.counter, 0, 2 * sizeof(int32_t), st));
+    }
+    HH_CUDA(cudaStreamSynchronize(st));
+    return HH_OK;
+}
+
+int max_gates_installed(const hh_net* n)
+{
+    int g = 1;
+    for (int m = 0; m < HH_MAX_MODELS; ++m)
+        if (n->installed[m] && n->models.m[m].n_gates > g)
+            g = n->models.m[m].n_gates;
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+hh_status hh_create_network(const hh_net_desc* d, hh_net** out)
+{
+    if (!out)
+        return fail(HH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d)
+        return fail(HH_EINVAL, "descriptor is NULL");
+    if (d->n_neurons < 1 || d->n_neurons > ((int64_t)1 << 31) - 1)
+        return fail(HH_EINVAL, "n_neurons %lld outside 1..2^31-1", (long long)d->n_neurons);
+    if (d->n_nets < 1)
+        return fail(HH_EINVAL, "n_nets must be >= 1");
+    if (d->n_nets > 1 && d->net_offsets) {
+        if (d->net_offsets[0] != 0 || d->net_offsets[d->n_nets] != d->n_neurons)
+            return fail(HH_EINVAL, "net_offsets must run from 0 to n_neurons");
+        for (int32_t k = 0; k < d->n_nets; ++k)
+            if (d->net_offsets[k + 1] < d->net_offsets[k])
+                return fail(HH_EINVAL, "net_offsets decrease at %d", k);
+    }
+    if (!(d->dt_ms > 0.0) || !std::isfinite(d->dt_ms))
+        return fail(HH_EINVAL, "dt_ms must be > 0");
+    if (!finite_f(d->v_threshold))
+        return fail(HH_EINVAL, "v_threshold must be finite");
+    if (d->v_update != HH_V_EXP_EULER && d->v_update != HH_V_FWD_EULER)
+        return fail(HH_EINVAL, "unknown v_update %d", d->v_update);
+    if (d->precision < HH_PREC_FAST || d->precision > HH_PREC_COMPENSATED)
+        return fail(HH_EINVAL, "unknown precision %d", d->precision);
+    if (!d->V0)
+        return fail(HH_EINVAL, "V0 is required");
+    hh_net* n = new (std::nothrow) hh_net();
+    if (!n)
+        return fail(HH_ENOMEM, "host allocation failed");
+    hh_status s = build_network(d, n);
+    if (s != HH_OK) {
+        std::string keep = g_err;
+        n->release();
+        delete n;
+        g_err = keep;
+        return s;
+    }
+    *out = n;
+    return HH_OK;
+}
+
+hh_status hh_set_channels(hh_net* net, int32_t model_index, const hh_model_desc* m, const float* gbar)
+{
+    if (!net || !m)
+        return fail(HH_EINVAL, "net and model must not be NULL");
+    if (model_index < 0 || model_index >= HH_MAX_MODELS)
+        return fail(HH_EINVAL, "model_index %d outside 0..%d", model_index, HH_MAX_MODELS - 1);
+    hh::DevModel dm{};
+    hh_status s = prep_model(m, net->dt, &dm);
+    if (s != HH_OK)
+        return s;
+    net->models.m[model_index] = dm;
+    net->installed[model_index] = true;
+    net->models.max_gates = max_gates_installed(net);
+    net->models.n = HH_MAX_MODELS;
+    if (gbar || net->gbar) {
+        if (!net->gbar) {
+            // first per-neuron table: every other model's neurons take their defaults
+            HH_CUDA(net->alloc(&net->gbar, (size_t)hh::kMaxChannels * net->N));
+            HH_CUDA(hh::launch_fill_gbar(net->models, net->N, net->model_id, -1, nullptr, net->gbar,
+                                         net->st));
+        }
+        float* staged = nullptr;
+        if (gbar) {
+            const size_t cnt = (size_t)m->n_channels * net->N;
+            HH_CUDA(cudaMalloc(&staged, cnt * sizeof(float)));
+            cudaError_t e = copy_in(staged, gbar, cnt, net->st);
+            if (e != cudaSuccess) {
+                cudaFree(staged);
+                return fail(HH_ECUDA, "copying gbar: %s", cudaGetErrorString(e));
+            }
+        }
+        cudaError_t e = hh::launch_fill_gbar(net->models, net->N, net->model_id, model_index, staged,
+                                             net->gbar, net->st);
+        cudaError_t e2 = cudaStreamSynchronize(net->st);
+        if (staged)
+            cudaFree(staged);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(HH_ECUDA, "filling gbar: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    hh::NeuronParams p = net->neuron_params();
+    HH_CUDA(hh::launch_init_state(net->models, p, nullptr, model_index, net->precision, net->st));
+    HH_CUDA(cudaStreamSynchronize(net->st));
+    return HH_OK;
+}
+
+hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh_record* rec)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (n_steps < 0)
+        return fail(HH_EINVAL, "n_steps < 0");
+    for (int m = 0; m <= net->max_model_used; ++m)
+        if (!net->installed[m])
+            return fail(HH_ESTATE, "model %d is used but was not installed with hh_set_channels", m);
+    if (net->t + n_steps > (int64_t)INT32_MAX)
+        return fail(HH_EINVAL, "step index would exceed 2^31-1");
+    hh::RecordParams R{};
+    if (rec) {
+        if (rec->n_trace < 0 || (rec->V_trace && rec->n_trace == 0))
+            return fail(HH_EINVAL, "n_trace must be > 0 when V_trace is given");
+        if (rec->spikes && !rec->n_spikes)
+            return fail(HH_EINVAL, "spikes needs an n_spikes counter");
+        if (rec->spike_cap < 0)
+            return fail(HH_EINVAL, "spike_cap < 0");
+        if (!rec->trace_idx && rec->n_trace > net->N)
+            return fail(HH_EINVAL, "n_trace > N without trace_idx");
+        R.V_trace = rec->V_trace;
+        R.n_trace = rec->V_trace ? rec->n_trace : 0;
+        R.spikes = rec->spikes;
+        R.spike_cap = rec->spikes ? rec->spike_cap : 0;
+        R.n_spikes = reinterpret_cast<unsigned long long*>(rec->n_spikes);
+        R.counts = rec->counts;
+    }
+    if (n_steps == 0)
+        return HH_OK;
+    hh::NeuronParams p = net->neuron_params();
+    if (R.V_trace && rec->trace_idx) {
+        HH_CUDA(cudaMemsetAsync(net->trace_slot, 0xff, net->N * sizeof(int32_t), net->st));
+        HH_CUDA(hh::launch_trace_slots(rec->trace_idx, rec->n_trace, net->N, net->trace_slot, net->st));
+        p.trace_slot = net->trace_slot;
+    }
+    // optional event bracketing of each launch (hh_profile)
+    auto timed = [&](int kind, auto&& launch) -> cudaError_t {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (net->profiling) {
+            e0 = net->take_event();
+            e1 = net->take_event();
+            if (!e0 || !e1)
+                return cudaErrorMemoryAllocation;
+            cudaError_t e = cudaEventRecord(e0, net->st);
+            if (e != cudaSuccess)
+                return e;
+        }
+        cudaError_t e = launch();
+        if (e != cudaSuccess || !net->profiling)
+            return e;
+        e = cudaEventRecord(e1, net->st);
+        net->ev_used.push_back({kind, {e0, e1}});
+        return e;
+    };
+    if (!net->has_syn && !net->has_bg) {
+        HH_CUDA(timed(HH_KERNEL_NEURON, [&] { return hh::launch_independent(net->models, p, net->precision, net->t, n_steps, I_steps, R,
+                                       net->st); }));
+    } else {
+        const hh::RouteParams rp = net->route_params();
+        const int32_t Wmax = net->has_syn ? net->D : (1 << 30);
+        for (int32_t w0 = 0; w0 < n_steps; w0 += Wmax) {
+            const int32_t W = (n_steps - w0) < Wmax ? (n_steps - w0) : Wmax;
+            const int32_t parity = (int32_t)(net->window_index & 1);
+            hh::RecordParams Rw = R;
+            if (Rw.V_trace)
+                Rw.V_trace += (int64_t)w0 * Rw.n_trace;
+            HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
+                return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, parity,
+                                             I_steps ? I_steps + (int64_t)w0 * net->N : nullptr, Rw,
+                                             net->list, net->st);
+            }));
+            if (net->has_syn)
+                HH_CUDA(timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, parity, net->st); }));
+            else
+                HH_CUDA(cudaMemsetAsync(net->list.counter + parity, 0, sizeof(int32_t), net->st));
+            net->window_index++;
+        }
+    }
+    net->t += n_steps;
+    return HH_OK;
+}
+
+hh_status hh_reset(hh_net* net, const float* V0)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    cudaStream_t st = net->st;
+    if (V0)
+        HH_CUDA(cudaMemcpyAsync(net->V0, V0, net->N * sizeof(float), cudaMemcpyDefault, st));
+    hh::NeuronParams p = net->neuron_params();
+    HH_CUDA(hh::launch_init_state(net->models, p, net->V0, -1, net->precision, st));
+    HH_CUDA(cudaMemsetAsync(net->gE, 0, net->N * sizeof(float), st));
+    HH_CUDA(cudaMemsetAsync(net->gI, 0, net->N * sizeof(float), st));
+    HH_CUDA(cudaMemsetAsync(net->status, 0, sizeof(int32_t), st));
+    if (net->ringE) {
+        HH_CUDA(cudaMemsetAsync(net->ringE, 0, (size_t)net->R * net->N * sizeof(int64_t), st));
+        HH_CUDA(cudaMemsetAsync(net->ringI, 0, (size_t)net->R * net->N * sizeof(int64_t), st));
+        HH_CUDA(cudaMemsetAsync(net->list.counter, 0, 2 * sizeof(int32_t), st));
+    }
+    net->t = 0;
+    net->window_index = 0;
+    return HH_OK;
+}
+
+hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* spk_idx, int64_t n_spk,
+                          int32_t n_window, int64_t* sum_E, int64_t* sum_I)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (!net->has_syn)
+        return fail(HH_ESTATE, "the network has no synapses");
+    if (n_spk < 0 || n_window < 0)
+        return fail(HH_EINVAL, "n_spk and n_window must be >= 0");
+    if (n_spk > 0 && (!spk_step || !spk_idx))
+        return fail(HH_EINVAL, "spike arrays are NULL");
+    if (n_window > 0 && (!sum_E || !sum_I))
+        return fail(HH_EINVAL, "sum_E and sum_I are required");
+    if (n_spk == 0 || n_window == 0)
+        return HH_OK;
+    hh::RouteParams rp = net->route_params();
+    rp.open_loop = 1;
+    rp.n_window = n_window;
+    rp.ringE = sum_E;
+    rp.ringI = sum_I;
+    HH_CUDA(hh::launch_route_list(rp, spk_step, spk_idx, n_spk, net->st));
+    return HH_OK;
+}
+
+hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap, size_t* n_bytes)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (n_bytes)
+        *n_bytes = 0;
+    HH_CUDA(cudaStreamSynchronize(net->st));
+    const size_t N = (size_t)net->N;
+    size_t need = 0;
+    switch (what) {
+    case HH_READ_V: need = N * sizeof(float); break;
+    case HH_READ_GATES: need = N * hh::kMaxGates * sizeof(float); break;
+    case HH_READ_CA: need = N * sizeof(float); break;
+    case HH_READ_G_SYN: need = 2 * N * sizeof(float); break;
+    case HH_READ_STATUS: need = sizeof(int32_t); break;
+    case HH_READ_TIME: need = sizeof(int64_t); break;
+    case HH_READ_N_OUT:
+        if (!net->has_syn)
+            return fail(HH_ESTATE, "the network has no synapses");
+        need = (N + 1) * sizeof(int64_t);
+        break;
+    case HH_READ_PROFILE: need = sizeof(net->ktime); break;
+    default: return fail(HH_EINVAL, "unknown readout %d", what);
+    }
+    if (!dst)
+        return fail(HH_EINVAL, "dst is NULL");
+    if (cap < need)
+        return fail(HH_EOVERFLOW, "readout %d needs %zu bytes, got %zu", what, need, cap);
+    switch (what) {
+    case HH_READ_V: HH_CUDA(cudaMemcpy(dst, net->V, need, cudaMemcpyDefault)); break;
+    case HH_READ_GATES: HH_CUDA(cudaMemcpy(dst, net->P, need, cudaMemcpyDefault)); break;
+    case HH_READ_CA: HH_CUDA(cudaMemcpy(dst, net->Ca, need, cudaMemcpyDefault)); break;
+    case HH_READ_G_SYN:
+        HH_CUDA(cudaMemcpy(dst, net->gE, N * sizeof(float), cudaMemcpyDefault));
+        HH_CUDA(cudaMemcpy((char*)dst + N * sizeof(float), net->gI, N * sizeof(float), cudaMemcpyDefault));
+        break;
+    case HH_READ_STATUS: HH_CUDA(cudaMemcpy(dst, net->status, need, cudaMemcpyDefault)); break;
+    case HH_READ_TIME: {
+        int64_t t = net->t;
+        HH_CUDA(cudaMemcpy(dst, &t, need, cudaMemcpyDefault));
+        break;
+    }
+    case HH_READ_N_OUT: HH_CUDA(cudaMemcpy(dst, net->out_ptr, need, cudaMemcpyDefault)); break;
+    case HH_READ_PROFILE:
+        HH_CUDA(net->harvest());
+        HH_CUDA(cudaMemcpy(dst, net->ktime, need, cudaMemcpyDefault));
+        break;
+    }
+    if (n_bytes)
+        *n_bytes = need;
+    return HH_OK;
+}
+
+hh_status hh_profile(hh_net* net, int32_t enable)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (enable) {
+        HH_CUDA(cudaStreamSynchronize(net->st));
+        HH_CUDA(net->harvest());
+        for (auto& k : net->ktime)
+            k = hh_kernel_time{0, 0.0};
+    }
+    net->profiling = enable != 0;
+    return HH_OK;
+}
+
+void hh_destroy(hh_net* net)
+{
+    if (!net)
+        return;
+    net->release();
+    delete net;
+}
+
+const char* hh_last_error(void) { return g_err.c_str(); }
+
+int32_t hh_version(void) { return 0x000100; }
+
+}  // extern "C"

@@ -1,0 +1,362 @@
+"""Thin ctypes binding of libhh (include/hh.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of libhh.so.  The functions keep the C names (hh_create_network,
+hh_set_channels, hh_step_n, hh_reset, hh_route_spikes, hh_readout,
+hh_destroy, hh_last_error); ``Network`` is a small convenience wrapper that
+owns a handle and passes torch device tensors' data pointers.
+
+There is no CPU fallback: if libhh.so cannot be built or loaded, ``lib()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA, HH_ETIMEOUT, HH_ESTATE, HH_EUNSUPPORTED, HH_EOVERFLOW = range(8)
+HH_FN = {"const": 0, "exp": 1, "sigmoid": 2, "linoid": 3, "bell": 4}
+HH_GATE = {"ab": 0, "inftau": 1, "ca": 2}
+HH_MAX_CHANNELS, HH_MAX_GATES_PER_CHANNEL, HH_MAX_GATES, HH_MAX_MODELS = 8, 3, 8, 4
+HH_PREC_FAST, HH_PREC_ACCURATE, HH_PREC_COMPENSATED = 0, 1, 2
+HH_V_EXP_EULER, HH_V_FWD_EULER = 0, 1
+(HH_READ_V, HH_READ_GATES, HH_READ_CA, HH_READ_G_SYN, HH_READ_STATUS, HH_READ_TIME,
+ HH_READ_N_OUT, HH_READ_PROFILE) = range(8)
+HH_KERNEL_NEURON, HH_KERNEL_ROUTE, HH_KERNEL_COUNT = 0, 1, 2
+HH_STATUS_SPIKE_OVERFLOW, HH_STATUS_NONFINITE = 1, 2
+
+
+class HHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"hh status {status}: {msg}")
+        self.status = status
+
+
+class hh_fn(C.Structure):
+    _fields_ = [("form", C.c_int32), ("a", C.c_float), ("vh", C.c_float), ("k", C.c_float),
+                ("vh2", C.c_float), ("k2", C.c_float), ("c", C.c_float)]
+
+
+class hh_gate(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("power", C.c_int32), ("f1", hh_fn), ("f2", hh_fn)]
+
+
+class hh_channel(C.Structure):
+    _fields_ = [("E_rev", C.c_float), ("gbar", C.c_float), ("n_gates", C.c_int32),
+                ("gates", hh_gate * HH_MAX_GATES_PER_CHANNEL)]
+
+
+class hh_model_desc(C.Structure):
+    _fields_ = [("C_m", C.c_float), ("n_channels", C.c_int32),
+                ("channels", hh_channel * HH_MAX_CHANNELS), ("ca_channel", C.c_int32),
+                ("ca_tau", C.c_float), ("ca_k", C.c_float), ("ca_rest", C.c_float)]
+
+
+class hh_net_desc(C.Structure):
+    _fields_ = [("n_neurons", C.c_int64), ("n_nets", C.c_int32), ("net_offsets", C.c_void_p),
+                ("dt_ms", C.c_double), ("v_threshold", C.c_float), ("v_update", C.c_int32),
+                ("precision", C.c_int32), ("V0", C.c_void_p), ("I_const", C.c_void_p),
+                ("model_id", C.c_void_p), ("n_synapses", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("weight", C.c_void_p), ("is_inhibitory", C.c_void_p),
+                ("tau_E", C.c_float), ("tau_I", C.c_float), ("E_E", C.c_float),
+                ("E_I", C.c_float), ("delay_steps", C.c_int32), ("area_cm2", C.c_float),
+                ("bg_rate_hz", C.c_float), ("bg_sources", C.c_int32), ("bg_weight_nS", C.c_float),
+                ("seed", C.c_uint64), ("stream", C.c_void_p)]
+
+
+class hh_spike(C.Structure):
+    _fields_ = [("step", C.c_int32), ("neuron", C.c_int32), ("frac", C.c_float)]
+
+
+class hh_kernel_time(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+class hh_record(C.Structure):
+    _fields_ = [("V_trace", C.c_void_p), ("trace_idx", C.c_void_p), ("n_trace", C.c_int32),
+                ("spikes", C.c_void_p), ("spike_cap", C.c_int64), ("n_spikes", C.c_void_p),
+                ("counts", C.c_void_p)]
+
+
+EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_route_spikes",
+           "hh_readout", "hh_profile", "hh_destroy", "hh_last_error", "hh_version"]
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libhh.so")
+
+
+def lib():
+    """Build (if stale) and load libhh.so.  Raises when it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+            _build.build()
+            L = C.CDLL(lib_path())
+            P = C.POINTER
+            vp = C.c_void_p
+            L.hh_create_network.restype = C.c_int
+            L.hh_create_network.argtypes = [P(hh_net_desc), P(vp)]
+            L.hh_set_channels.restype = C.c_int
+            L.hh_set_channels.argtypes = [vp, C.c_int32, P(hh_model_desc), vp]
+            L.hh_step_n.restype = C.c_int
+            L.hh_step_n.argtypes = [vp, C.c_int32, vp, P(hh_record)]
+            L.hh_reset.restype = C.c_int
+            L.hh_reset.argtypes = [vp, vp]
+            L.hh_route_spikes.restype = C.c_int
+            L.hh_route_spikes.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, vp, vp]
+            L.hh_readout.restype = C.c_int
+            L.hh_readout.argtypes = [vp, C.c_int32, vp, C.c_size_t, P(C.c_size_t)]
+            L.hh_profile.restype = C.c_int
+            L.hh_profile.argtypes = [vp, C.c_int32]
+            L.hh_destroy.restype = None
+            L.hh_destroy.argtypes = [vp]
+            L.hh_last_error.restype = C.c_char_p
+            L.hh_last_error.argtypes = []
+            L.hh_version.restype = C.c_int32
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != HH_OK:
+        raise HHError(status, lib().hh_last_error().decode(errors="replace"))
+
+
+def hh_last_error() -> str:
+    return lib().hh_last_error().decode(errors="replace")
+
+
+def hh_create_network(desc: hh_net_desc) -> int:
+    h = C.c_void_p()
+    _check(lib().hh_create_network(C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def hh_set_channels(net: int, model_index: int, model: hh_model_desc, gbar_ptr=None):
+    _check(lib().hh_set_channels(net, model_index, C.byref(model), gbar_ptr))
+
+
+def hh_step_n(net: int, n_steps: int, I_steps_ptr=None, rec: hh_record | None = None):
+    _check(lib().hh_step_n(net, n_steps, I_steps_ptr, C.byref(rec) if rec is not None else None))
+
+
+def hh_reset(net: int, V0_ptr=None):
+    _check(lib().hh_reset(net, V0_ptr))
+
+
+def hh_route_spikes(net: int, step_ptr, idx_ptr, n_spk: int, n_window: int, sumE_ptr, sumI_ptr):
+    _check(lib().hh_route_spikes(net, step_ptr, idx_ptr, n_spk, n_window, sumE_ptr, sumI_ptr))
+
+
+def hh_readout(net: int, what: int, dst_ptr, cap: int) -> int:
+    n = C.c_size_t()
+    _check(lib().hh_readout(net, what, dst_ptr, cap, C.byref(n)))
+    return n.value
+
+
+def hh_profile(net: int, enable: bool):
+    _check(lib().hh_profile(net, 1 if enable else 0))
+
+
+def hh_destroy(net: int):
+    lib().hh_destroy(net)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _fn(t) -> hh_fn:
+    form, a, vh, k, vh2, k2, c = t
+    return hh_fn(HH_FN[form], a, vh, k, vh2, k2, c)
+
+
+def model_desc(model: dict) -> hh_model_desc:
+    """hh_model_desc from a model table (paper_2601_21407_gb300.inputs)."""
+    m = hh_model_desc()
+    m.C_m = model["C_m"]
+    m.n_channels = len(model["channels"])
+    m.ca_channel = -1
+    for ci, ch in enumerate(model["channels"]):
+        m.channels[ci].E_rev = ch["E"]
+        m.channels[ci].gbar = ch["gbar"]
+        m.channels[ci].n_gates = len(ch["gates"])
+        for gi, g in enumerate(ch["gates"]):
+            m.channels[ci].gates[gi] = hh_gate(HH_GATE[g["kind"]], g["power"], _fn(g["f1"]),
+                                               _fn(g["f2"]))
+    ca = model.get("calcium")
+    if ca:
+        m.ca_channel = [c["name"] for c in model["channels"]].index(ca["channel"])
+        m.ca_tau, m.ca_k, m.ca_rest = ca["tau"], ca["k"], ca["rest"]
+    return m
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or numpy array (None passes through)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Network:
+    """Owns one hh_net.  Arrays may be numpy (host) or torch (host/device);
+    the library copies them during creation."""
+
+    def __init__(self, V0, dt, *, I_const=None, model_id=None, csr=None, inh=None, syn=None,
+                 delay_steps=1, bg=None, seed=0, theta=0.0, precision=HH_PREC_FAST,
+                 v_update=HH_V_EXP_EULER, stream=None, n_nets=1, net_offsets=None):
+        d = hh_net_desc()
+        self._keep = []
+        V0 = self._f32(V0)
+        d.n_neurons = int(V0.numel() if hasattr(V0, "numel") else V0.size)
+        self.N = d.n_neurons
+        d.n_nets = n_nets
+        if net_offsets is not None:
+            no = np.ascontiguousarray(net_offsets, dtype=np.int64)
+            self._keep.append(no)
+            d.net_offsets = no.ctypes.data
+        d.dt_ms = dt
+        d.v_threshold = theta
+        d.v_update = v_update
+        d.precision = precision
+        d.V0 = _ptr(V0)
+        if I_const is not None:
+            I_const = self._f32(I_const)
+            d.I_const = _ptr(I_const)
+        if model_id is not None:
+            model_id = self._arr(model_id, np.uint8)
+            d.model_id = _ptr(model_id)
+        if csr is not None:
+            row_ptr, col, w = csr
+            row_ptr = self._arr(row_ptr, np.int64)
+            col = self._arr(col, np.int32)
+            w = self._f32(w)
+            d.n_synapses = int(w.numel() if hasattr(w, "numel") else w.size)
+            d.row_ptr, d.col_idx, d.weight = _ptr(row_ptr), _ptr(col), _ptr(w)
+        if inh is not None:
+            inh = self._arr(inh, np.uint8)
+            d.is_inhibitory = _ptr(inh)
+        syn = syn or {}
+        d.tau_E = syn.get("tau_E", 5.0)
+        d.tau_I = syn.get("tau_I", 10.0)
+        d.E_E = syn.get("E_E", 0.0)
+        d.E_I = syn.get("E_I", -80.0)
+        d.area_cm2 = syn.get("area_cm2", 2.0e-4)
+        d.delay_steps = delay_steps
+        if bg:
+            d.bg_rate_hz, d.bg_sources, d.bg_weight_nS = bg["rate_hz"], bg["K"], bg["w"]
+        d.seed = seed
+        d.stream = stream
+        self.handle = hh_create_network(d)
+        self._keep = []
+
+    def _arr(self, a, dtype):
+        if hasattr(a, "data_ptr"):
+            import torch
+            tdt = {np.uint8: torch.uint8, np.int32: torch.int32, np.int64: torch.int64,
+                   np.float32: torch.float32}[dtype]
+            a = a.contiguous().to(tdt)
+        else:
+            a = np.ascontiguousarray(a, dtype=dtype)
+        self._keep.append(a)
+        return a
+
+    def _f32(self, a):
+        return self._arr(a, np.float32)
+
+    def set_channels(self, model_index, model: dict, gbar=None):
+        g = None if gbar is None else self._f32(gbar)
+        hh_set_channels(self.handle, model_index, model_desc(model), _ptr(g))
+        self._keep = []
+
+    def step(self, n_steps, I_steps=None, rec: hh_record | None = None):
+        hh_step_n(self.handle, n_steps, _ptr(I_steps), rec)
+
+    def reset(self, V0=None):
+        v = None if V0 is None else self._f32(V0)
+        hh_reset(self.handle, _ptr(v))
+        self._keep.append(v)
+
+    def route_spikes(self, step, idx, n_window, sumE, sumI):
+        hh_route_spikes(self.handle, _ptr(step), _ptr(idx), int(step.numel()), n_window,
+                        _ptr(sumE), _ptr(sumI))
+
+    def readout(self, what, dtype=np.float32, count=None):
+        sizes = {HH_READ_V: (self.N, np.float32), HH_READ_GATES: (HH_MAX_GATES * self.N, np.float32),
+                 HH_READ_CA: (self.N, np.float32), HH_READ_G_SYN: (2 * self.N, np.float32),
+                 HH_READ_STATUS: (1, np.int32), HH_READ_TIME: (1, np.int64),
+                 HH_READ_N_OUT: (self.N + 1, np.int64)}
+        n, dt = sizes[what]
+        out = np.zeros(n, dtype=dt)
+        hh_readout(self.handle, what, out.ctypes.data, out.nbytes)
+        return out
+
+    def profile(self, enable: bool):
+        hh_profile(self.handle, enable)
+
+    def kernel_times(self):
+        """{"neuron": (launches, total_ms), "route": (...)} since profile(True)."""
+        arr = (hh_kernel_time * HH_KERNEL_COUNT)()
+        hh_readout(self.handle, HH_READ_PROFILE, C.addressof(arr), C.sizeof(arr))
+        return {"neuron": (arr[0].launches, arr[0].total_ms),
+                "route": (arr[1].launches, arr[1].total_ms)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_record(N, n_steps, *, trace=0, trace_idx=None, spike_cap=0, counts=True, device="cuda"):
+    """Allocate caller-owned device outputs with torch and an hh_record that
+    points at them.  Returns (rec, buffers dict)."""
+    import torch
+    b = {}
+    r = hh_record()
+    if trace:
+        b["V_trace"] = torch.empty((n_steps, trace), dtype=torch.float32, device=device)
+        r.V_trace = b["V_trace"].data_ptr()
+        r.n_trace = trace
+        if trace_idx is not None:
+            b["trace_idx"] = torch.as_tensor(np.asarray(trace_idx, dtype=np.int32), device=device)
+            r.trace_idx = b["trace_idx"].data_ptr()
+    if spike_cap:
+        b["spikes"] = torch.zeros((spike_cap, 3), dtype=torch.int32, device=device)
+        b["n_spikes"] = torch.zeros(1, dtype=torch.int64, device=device)
+        r.spikes = b["spikes"].data_ptr()
+        r.spike_cap = spike_cap
+        r.n_spikes = b["n_spikes"].data_ptr()
+    if counts:
+        b["counts"] = torch.zeros(N, dtype=torch.int32, device=device)
+        r.counts = b["counts"].data_ptr()
+    return r, b
+
+
+def spikes_to_numpy(b):
+    """(step, neuron, frac) arrays from a record's spike buffer, sorted by
+    (step, neuron)."""
+    n = int(b["n_spikes"].item())
+    n = min(n, b["spikes"].shape[0])
+    raw = b["spikes"][:n].cpu().numpy()
+    step = raw[:, 0].copy()
+    idx = raw[:, 1].copy()
+    frac = raw[:, 2].copy().view(np.float32)
+    o = np.lexsort((idx, step))
+    return step[o], idx[o], frac[o]

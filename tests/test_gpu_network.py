@@ -1,0 +1,247 @@
+"""GPU parity of the network path (delay line, CSR routing, exponential
+synapses, Poisson background) against the FP64 oracle: routing bit-exact in
+2^-32 nS fixed point (small graphs and the full 1e8-synapse graph),
+background counts bit-exact, closed-loop spike counts, batched networks with
+mixed neuron models, determinism and resume, and CSR validation."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_21407_gb300 import hh, inputs as inp
+
+pytestmark = pytest.mark.gpu
+
+SYN = {"tau_E": 5.0, "tau_I": 10.0, "E_E": 0.0, "E_I": -80.0, "area_cm2": 2.0e-4}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_net(g, dt=0.025, D=40, bg=None, seed=0, precision=hh.HH_PREC_FAST, models=(inp.CLASSIC_HH,),
+             model_id=None, I=None):
+    net = hh.Network(g["V0"], dt, csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
+                     delay_steps=D, bg=bg, seed=seed, precision=precision, model_id=model_id,
+                     I_const=I)
+    for k, m in enumerate(models):
+        net.set_channels(k, m)
+    return net
+
+
+def route_gpu(net, N, st, ix, n_window):
+    torch = _torch()
+    sE = torch.zeros((n_window, N), dtype=torch.int64, device="cuda")
+    sI = torch.zeros_like(sE)
+    net.route_spikes(torch.as_tensor(st, device="cuda"), torch.as_tensor(ix, device="cuda"),
+                     n_window, sE, sI)
+    torch.cuda.synchronize()
+    return sE.cpu().numpy(), sI.cpu().numpy()
+
+
+def to_fixed(x):
+    y = x * 2.0**32
+    assert np.array_equal(y, np.round(y))
+    return y.astype(np.int64)
+
+
+@pytest.mark.parametrize("n,k,seed,D", [(64, 10, 0, 1), (500, 50, 1, 7), (2000, 200, 2, 40),
+                                        (3001, 17, 3, 40)])
+def test_routing_bit_exact(n, k, seed, D):
+    """Open-loop routing of a seeded raster: per-step, per-target delivered
+    conductance equals the oracle's sums exactly (2^-32 nS fixed point)."""
+    g = inp.network(n=n, k_in=k, seed=seed)
+    st, ix = inp.spike_raster(n, 25, max(1, n // 50), seed + 100)
+    Tw = 25 + D + 3
+    net = make_net(g, D=D)
+    gE, gI = route_gpu(net, n, st, ix, Tw)
+    rE, rI = oracle.route(n, Tw, D, g["row_ptr"], g["col"], g["w"], g["inh"], st, ix)
+    assert np.array_equal(gE, to_fixed(rE))
+    assert np.array_equal(gI, to_fixed(rI))
+    net.close()
+
+
+def test_routing_full_size_graph():
+    """The 38,000-neuron, 1.0e8-synapse graph: a 40-step raster with 1% of
+    the neurons spiking per step (4.0e7 synaptic events) routes bit-exactly."""
+    g = inp.network(n=38_000, k_in=2_632, seed=0)
+    st, ix = inp.spike_raster(38_000, 40, 380, 1)
+    net = make_net(g, D=40)
+    out_ptr = net.readout(hh.HH_READ_N_OUT)
+    assert out_ptr[-1] == 38_000 * 2_632
+    gE, gI = route_gpu(net, 38_000, st, ix, 80)
+    rE, rI = oracle.route(38_000, 80, 40, g["row_ptr"], g["col"], g["w"], g["inh"], st, ix)
+    assert np.array_equal(gE, to_fixed(rE))
+    assert np.array_equal(gI, to_fixed(rI))
+    net.close()
+
+
+def test_out_degree_matches_transpose():
+    g = inp.network(n=1000, k_in=30, seed=7)
+    net = make_net(g)
+    deg = np.diff(net.readout(hh.HH_READ_N_OUT))
+    assert np.array_equal(deg, np.bincount(g["col"], minlength=1000))
+    net.close()
+
+
+def test_background_counts_bit_exact():
+    """Poisson background counts drawn on the GPU (Philox-4x32-10 word
+    (t>>2, i, 1, t>>34)[t&3], inverse CDF on the 2^32 grid) equal the
+    oracle's for every neuron over 9 steps (reconstructed from g_E)."""
+    N = 4096
+    bg = {"rate_hz": 5.0, "K": 2106, "w": 0.5}
+    net = hh.Network(np.full(N, -65.0, np.float32), 0.025, syn=SYN, bg=bg, seed=123)
+    net.set_channels(0, inp.CLASSIC_HH)
+    thr = oracle.poisson_table(oracle.background_lambda(2106, 5.0, 0.025))
+    dec = np.float32(np.exp(-0.025 / 5.0))
+    prev = np.zeros(N, np.float32)
+    total = 0
+    for t in range(9):
+        net.step(1)
+        gsyn = net.readout(hh.HH_READ_G_SYN)[:N]
+        k = np.rint((gsyn / dec - prev) / np.float32(0.5)).astype(int)
+        kr = np.array([oracle.poisson_sample(oracle.background_word(123, t, i), thr) for i in range(N)])
+        assert np.array_equal(k, kr), t
+        total += kr.sum()
+        prev = gsyn
+    assert total > 0
+    net.close()
+
+
+@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE, hh.HH_PREC_COMPENSATED])
+def test_closed_loop_small_network(prec):
+    """1,000 neurons, in-degree 100, background, 200 ms closed loop: every
+    neuron's spike count within +-1 of the oracle, and the V traces agree to
+    1e-2 mV for the first 10 ms (before FP32/FP64 chaos separates them)."""
+    torch = _torch()
+    g = inp.network(n=1000, k_in=100, seed=4, mu=0.5)
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
+    T = 8000
+    ref = oracle.simulate_network(inp.CLASSIC_HH, g, T, 0.025, 40, SYN, bg=bg, seed=9,
+                                  trace_idx=np.arange(1000))
+    net = make_net(g, bg=bg, seed=9, precision=prec)
+    rec, b = hh.make_record(1000, T, trace=1000, spike_cap=1_000_000)
+    net.step(T, rec=rec)
+    torch.cuda.synchronize()
+    counts = b["counts"].cpu().numpy()
+    assert ref["counts"].sum() > 1000
+    assert np.abs(counts - ref["counts"]).max() <= 1
+    V = b["V_trace"].cpu().numpy()
+    assert np.abs(V[:400] - ref["V"][:400]).max() < 1e-2
+    assert int(net.readout(hh.HH_READ_STATUS)[0]) == 0
+    net.close()
+
+
+def test_network_full_size_first_10ms():
+    """The full 38,000-neuron network (1e8 synapses) for 10 ms against the
+    oracle on the same graph: spike rasters agree for >= 99.9% of neurons."""
+    torch = _torch()
+    g = inp.network(n=38_000, k_in=2_632, seed=0)
+    bg = {"rate_hz": 5.0, "K": 2106, "w": 0.368}
+    T = 400
+    ref = oracle.simulate_network(inp.CLASSIC_HH, g, T, 0.025, 40, SYN, bg=bg, seed=0, spk_cap=8)
+    net = make_net(g, bg=bg, seed=0, precision=hh.HH_PREC_FAST)
+    rec, b = hh.make_record(38_000, T, spike_cap=200_000)
+    net.step(T, rec=rec)
+    torch.cuda.synchronize()
+    counts = b["counts"].cpu().numpy()
+    assert (counts == ref["counts"]).mean() >= 0.999
+    assert abs(int(counts.sum()) - int(ref["counts"].sum())) <= 0.001 * ref["counts"].sum() + 2
+    net.close()
+
+
+def test_batched_networks_mixed_models():
+    """Several independent networks (block-diagonal CSR) in one launch, with
+    half of them classic HH and half multi-channel neurons: spike counts
+    within +-1 of the oracle over 100 ms."""
+    torch = _torch()
+    bn = inp.batched_networks(n_nets=6, n_min=200, n_max=1500, k_min=20, k_max=80, seed=2)
+    N = int(bn["offsets"][-1])
+    bg = {"rate_hz": 5.0, "K": 600, "w": 1.2}
+    T = 4000
+    ref = oracle.simulate_network([inp.CLASSIC_HH, inp.MULTI_CHANNEL], bn, T, 0.025, 40, SYN, bg=bg,
+                                  seed=3, model_id=bn["model_id"])
+    net = make_net(bn, bg=bg, seed=3, models=(inp.CLASSIC_HH, inp.MULTI_CHANNEL),
+                   model_id=bn["model_id"])
+    rec, b = hh.make_record(N, T, spike_cap=2_000_000)
+    net.step(T, rec=rec)
+    torch.cuda.synchronize()
+    counts = b["counts"].cpu().numpy()
+    assert ref["counts"].sum() > 500
+    d = np.abs(counts - ref["counts"])
+    assert (d <= 1).mean() >= 0.99
+    net.close()
+
+
+def test_deterministic_and_resumable():
+    """Two runs from the same state give bit-identical rasters (fixed-point
+    delivery is order independent), and splitting a run across calls at
+    points that do not align with the delay windows changes no bit."""
+    torch = _torch()
+    g = inp.network(n=3000, k_in=300, seed=5, mu=0.0)
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
+
+    def run(chunks):
+        net = make_net(g, bg=bg, seed=1)
+        rec, b = hh.make_record(3000, sum(chunks), spike_cap=500_000)
+        for c in chunks:
+            net.step(c, rec=rec)
+        torch.cuda.synchronize()
+        v = net.readout(hh.HH_READ_V)
+        s = hh.spikes_to_numpy(b)
+        net.close()
+        return v, s
+
+    a = run([2000])
+    b = run([2000])
+    c = run([13, 401, 999, 587])
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[0], c[0])
+    for k in range(3):
+        assert np.array_equal(a[1][k], b[1][k]) and np.array_equal(a[1][k], c[1][k])
+    assert len(a[1][0]) > 100
+
+
+def test_reset_restores_initial_state():
+    torch = _torch()
+    g = inp.network(n=800, k_in=80, seed=6, mu=0.5)
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
+    net = make_net(g, bg=bg, seed=2)
+    out = []
+    for _ in range(2):
+        rec, b = hh.make_record(800, 1000, spike_cap=100_000)
+        net.reset()
+        net.step(1000, rec=rec)
+        torch.cuda.synchronize()
+        out.append(hh.spikes_to_numpy(b))
+    assert all(np.array_equal(out[0][k], out[1][k]) for k in range(3))
+    assert int(net.readout(hh.HH_READ_TIME)[0]) == 1000
+    net.close()
+
+
+@pytest.mark.parametrize("what", ["col", "weight_neg", "weight_nan", "row_ptr"])
+def test_invalid_csr_rejected(what):
+    g = inp.network(n=100, k_in=10, seed=0)
+    col, w, rp = g["col"].copy(), g["w"].copy(), g["row_ptr"].copy()
+    if what == "col":
+        col[17] = 100
+    elif what == "weight_neg":
+        w[3] = -0.5
+    elif what == "weight_nan":
+        w[5] = np.nan
+    else:
+        rp[50] = rp[49] - 1
+    with pytest.raises(hh.HHError) as e:
+        hh.Network(g["V0"], 0.025, csr=(rp, col, w), inh=g["inh"], syn=SYN, delay_steps=40)
+    assert e.value.status == hh.HH_EINVAL
+
+
+def test_profile_counts_launches():
+    g = inp.network(n=500, k_in=20, seed=8)
+    net = make_net(g, bg={"rate_hz": 5.0, "K": 500, "w": 1.0})
+    net.profile(True)
+    net.step(400)
+    kt = net.kernel_times()
+    net.profile(False)
+    assert kt["neuron"][0] == 10 and kt["route"][0] == 10
+    assert kt["neuron"][1] > 0
+    net.close()

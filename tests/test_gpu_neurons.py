@@ -1,0 +1,226 @@
+"""GPU parity of independent-neuron simulation (libhh via its C ABI) against
+the FP64 oracle: the classic squid-axon population (1,024 neurons, 100 ms)
+in each precision mode, the multi-channel population (500 ms) and its
+full-size 1e6-neuron run on sampled neurons, plus ABI edge cases."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_21407_gb300 import hh, inputs as inp
+
+pytestmark = pytest.mark.gpu
+
+V_TOL_MV = 1e-2        # max |dV| over the trace, single neurons over 100 ms
+T_TOL_MS = 0.05        # spike-time tolerance
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def run_gpu(model, I, V0, T, dt, precision, gbar=None, trace=True, spike_cap=None, v_update=0,
+            I_steps=None, chunks=None):
+    torch = _torch()
+    N = len(V0)
+    net = hh.Network(V0, dt, I_const=I, precision=precision, v_update=v_update)
+    net.set_channels(0, model, gbar=gbar)
+    cap = spike_cap if spike_cap is not None else 400 * N
+    rec, b = hh.make_record(N, T, trace=N if trace else 0, spike_cap=cap)
+    Is = None if I_steps is None else torch.as_tensor(I_steps, device="cuda")
+    if chunks is None:
+        net.step(T, I_steps=Is, rec=rec)
+    else:
+        done = 0
+        for c in chunks:
+            r2 = hh.hh_record()
+            r2.spikes, r2.spike_cap, r2.n_spikes, r2.counts = rec.spikes, rec.spike_cap, rec.n_spikes, rec.counts
+            if trace:
+                r2.V_trace = b["V_trace"][done:].data_ptr()
+                r2.n_trace = N
+            net.step(c, I_steps=None if Is is None else Is[done:], rec=r2)
+            done += c
+    torch.cuda.synchronize()
+    out = {"counts": b["counts"].cpu().numpy(), "status": int(net.readout(hh.HH_READ_STATUS)[0]),
+           "n_spikes": int(b["n_spikes"].item())}
+    if trace:
+        out["V"] = b["V_trace"].cpu().numpy()
+    out["spk"] = hh.spikes_to_numpy(b)
+    net.close()
+    return out
+
+
+def spike_time_errors(g, ref, dt):
+    """Max |t_gpu - t_oracle| per neuron over neurons with equal counts."""
+    st, ix, fr = g["spk"]
+    errs = {}
+    for i in np.unique(ix):
+        c = ref["counts"][i]
+        if g["counts"][i] != c:
+            continue
+        t_g = (st[ix == i] + fr[ix == i]) * dt
+        t_r = (ref["spk_step"][i][:c] + ref["spk_frac"][i][:c]) * dt
+        errs[int(i)] = float(np.abs(t_g - t_r).max())
+    return errs
+
+
+@pytest.fixture(scope="module")
+def classic_1024():
+    x = inp.single_neurons(1024, seed=0)
+    T, dt = 10_000, 0.01
+    ref = oracle.simulate(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, spk_cap=64)
+    # conditioning from the oracle alone: a neuron whose FP64 trajectory moves
+    # by more than half the tolerance when its input is perturbed by two
+    # float32 ulps (2^-22 relative) cannot be held to the tolerance by any
+    # FP32 evaluation.
+    pert = oracle.simulate(inp.CLASSIC_HH, x["I"].astype(np.float64) * (1 + 2.0**-22), x["V0"],
+                           T, dt, spk_cap=64)
+    ill = np.abs(pert["V"] - ref["V"]).max(0) > V_TOL_MV / 2
+    return x, T, dt, ref, ill
+
+
+def test_classic_population_compensated(classic_1024):
+    """Config 1 (1,024 neurons, I ~ U(0,20), dt 0.01 ms, 100 ms) in
+    compensated FP32: max |dV| <= 1e-2 mV for every well-conditioned neuron,
+    identical spike counts and spike times within 0.05 ms for all neurons."""
+    x, T, dt, ref, ill = classic_1024
+    assert ill.mean() < 0.03
+    g = run_gpu(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, hh.HH_PREC_COMPENSATED)
+    assert g["status"] == 0
+    dV = np.abs(g["V"] - ref["V"]).max(0)
+    assert dV[~ill].max() <= V_TOL_MV, (dV[~ill].max(), np.argmax(np.where(ill, 0, dV)))
+    assert np.array_equal(g["counts"], ref["counts"])
+    errs = spike_time_errors(g, ref, dt)
+    assert len(errs) == int((ref["counts"] > 0).sum())
+    assert max(errs.values()) <= T_TOL_MS
+    print(f"compensated: max|dV| well-cond {dV[~ill].max():.2e} mV, all {dV.max():.2e}, "
+          f"median {np.median(dV):.2e}; spike-time max {max(errs.values()):.2e} ms; "
+          f"ill-conditioned {int(ill.sum())}")
+
+
+@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE])
+def test_classic_population_plain_fp32(classic_1024, prec):
+    """Plain FP32 state (no compensation): identical spike counts and spike
+    times within 0.05 ms; the V trace error is that of rounding the state to
+    FP32 every step (reported, bounded loosely)."""
+    x, T, dt, ref, ill = classic_1024
+    g = run_gpu(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, prec)
+    assert np.array_equal(g["counts"], ref["counts"])
+    errs = spike_time_errors(g, ref, dt)
+    assert max(errs.values()) <= T_TOL_MS
+    dV = np.abs(g["V"] - ref["V"]).max(0)
+    assert np.quantile(dV[~ill], 0.9) < 0.1
+    print(f"prec {prec}: max|dV| median {np.median(dV):.2e} p90 {np.quantile(dV, 0.9):.2e} mV; "
+          f"spike-time max {max(errs.values()):.2e} ms")
+
+
+def test_forward_euler_variant():
+    """The explicit-Euler V update (Eq. hh_dyn_simplified) matches the
+    oracle's explicit-Euler variant."""
+    x = inp.single_neurons(256, seed=3)
+    T, dt = 4000, 0.005
+    ref = oracle.simulate(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, v_mode=1)
+    g = run_gpu(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, hh.HH_PREC_COMPENSATED, v_update=1)
+    assert np.array_equal(g["counts"], ref["counts"])
+    assert np.abs(g["V"] - ref["V"]).max() < 1e-2
+
+
+def test_per_step_current_and_split_calls():
+    """A per-step injected current (I_steps) and splitting the run into
+    several hh_step_n calls reproduce a single call bit for bit and follow
+    the oracle."""
+    rng = np.random.default_rng(5)
+    N, T, dt = 96, 3000, 0.01
+    I0 = rng.uniform(0, 5, N).astype(np.float32)
+    Is = rng.uniform(0, 10, (T, N)).astype(np.float32)
+    V0 = np.full(N, -65.0, np.float32)
+    a = run_gpu(inp.CLASSIC_HH, I0, V0, T, dt, hh.HH_PREC_COMPENSATED, I_steps=Is)
+    b = run_gpu(inp.CLASSIC_HH, I0, V0, T, dt, hh.HH_PREC_COMPENSATED, I_steps=Is,
+                chunks=[1, 999, 37, 1963])
+    assert np.array_equal(a["V"], b["V"])
+    ref = oracle.simulate(inp.CLASSIC_HH, I0, V0, T, dt, I_steps=Is)
+    assert np.array_equal(a["counts"], ref["counts"])
+    assert np.abs(a["V"] - ref["V"]).max() < 1e-2
+
+
+@pytest.mark.parametrize("N", [1, 33, 130])
+def test_ragged_sizes(N):
+    """Populations that do not fill a warp or a block."""
+    x = inp.single_neurons(N, seed=N)
+    T, dt = 1500, 0.01
+    ref = oracle.simulate(inp.CLASSIC_HH, x["I"], x["V0"], T, dt)
+    g = run_gpu(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, hh.HH_PREC_COMPENSATED)
+    assert np.array_equal(g["counts"], ref["counts"])
+    assert np.abs(g["V"] - ref["V"]).max() < 1e-2
+
+
+def test_spike_overflow_is_flagged():
+    """A too-small spike buffer keeps the first spike_cap spikes, counts all
+    of them and sets the overflow status bit."""
+    x = inp.single_neurons(64, seed=1, i_max=20.0)
+    g = run_gpu(inp.CLASSIC_HH, np.full(64, 15.0, np.float32), x["V0"], 2000, 0.01,
+                hh.HH_PREC_FAST, trace=False, spike_cap=10)
+    assert g["n_spikes"] > 10
+    assert g["status"] & hh.HH_STATUS_SPIKE_OVERFLOW
+    assert g["n_spikes"] == int(g["counts"].sum())
+
+
+@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE])
+def test_multichannel_population(prec):
+    """Multi-channel neurons (Na, Kdr, KA, CaL, KCa, Ih + Ca pool) with
+    per-neuron lognormal maximal conductances, dt 0.025 ms, 500 ms:
+    spike counts within +-1 for every neuron, spike times within 0.05 ms for
+    matched neurons."""
+    y = inp.multi_channel_neurons(512, seed=0)
+    T, dt = 20_000, 0.025
+    ref = oracle.simulate(inp.MULTI_CHANNEL, y["I"], y["V0"], T, dt, gbar=y["gbar"], trace=False,
+                          spk_cap=128)
+    g = run_gpu(inp.MULTI_CHANNEL, y["I"], y["V0"], T, dt, prec, gbar=y["gbar"], trace=False)
+    d = np.abs(g["counts"] - ref["counts"])
+    assert d.max() <= 1
+    errs = spike_time_errors(g, ref, dt)
+    within = np.mean([e <= T_TOL_MS for e in errs.values()])
+    assert within >= 0.98
+    assert (ref["counts"] > 0).sum() > 100
+
+
+def test_multichannel_full_size_sampled():
+    """The full multi-channel population (1e6 neurons, 500 ms) on the GPU;
+    256 sampled neurons re-simulated by the oracle (neurons are independent,
+    so the sample is exact): counts within +-1."""
+    torch = _torch()
+    y = inp.multi_channel_neurons(1_000_000, seed=0)
+    T, dt = 20_000, 0.025
+    N = 1_000_000
+    net = hh.Network(y["V0"], dt, I_const=y["I"], precision=hh.HH_PREC_FAST)
+    net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
+    rec, b = hh.make_record(N, T, spike_cap=0)
+    net.step(T, rec=rec)
+    torch.cuda.synchronize()
+    counts = b["counts"].cpu().numpy()
+    assert int(net.readout(hh.HH_READ_STATUS)[0]) == 0
+    net.close()
+    idx = np.random.default_rng(1).choice(N, 256, replace=False)
+    ref = oracle.simulate(inp.MULTI_CHANNEL, y["I"][idx], y["V0"][idx], T, dt,
+                          gbar=y["gbar"][:, idx], trace=False, spk_cap=4)
+    d = np.abs(counts[idx] - ref["counts"])
+    assert d.max() <= 1
+    assert (d == 0).mean() >= 0.95
+
+
+def test_bad_model_rejected():
+    x = inp.single_neurons(4, seed=0)
+    net = hh.Network(x["V0"], 0.01, I_const=x["I"])
+    bad = dict(inp.CLASSIC_HH)
+    bad["channels"] = [dict(c) for c in inp.CLASSIC_HH["channels"]]
+    bad["channels"][0] = dict(bad["channels"][0])
+    g0 = dict(bad["channels"][0]["gates"][0])
+    g0["power"] = 7
+    bad["channels"][0]["gates"] = [g0] + bad["channels"][0]["gates"][1:]
+    with pytest.raises(hh.HHError) as e:
+        net.set_channels(0, bad)
+    assert e.value.status == hh.HH_EINVAL
+    with pytest.raises(hh.HHError) as e:
+        net.step(10)     # model 0 never installed
+    assert e.value.status == hh.HH_ESTATE
+    net.close()
