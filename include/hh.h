@@ -298,6 +298,68 @@ typedef struct {
 enum { HH_KERNEL_NEURON = 0, HH_KERNEL_ROUTE = 1, HH_KERNEL_COUNT = 2 };
 hh_status hh_profile(hh_net* net, int32_t enable);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free stepping of independent neurons                      */
+/* ------------------------------------------------------------------ */
+
+/* Some callers cannot call cudaMalloc: code running inside another
+ * framework's memory pool or arena, a host process that must not grow its
+ * device footprint after start-up, or a runtime that hands out device memory
+ * only from its own allocator.  hh_step_neurons_noalloc lets them step a
+ * population of independent neurons (no synapses) in buffers they already
+ * own.  It has no counterpart in the paper: it is the same neuron kernel as
+ * hh_step_n, with its only scratch space -- the map from neuron to
+ * V-trace slot used when rec->trace_idx is given -- held in a file-scope
+ * device array of the library instead of library-allocated memory.
+ *
+ * Limits and behaviour:
+ *   - n_neurons <= HH_NOALLOC_MAX_NEURONS (larger sizes return HH_EINVAL);
+ *     the static scratch (4 MiB of slot map plus one status word that takes
+ *     the status bits when s->status is NULL) stays resident on every GPU
+ *     that loads the library until the process exits.
+ *   - The first call on a device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress with that device current) and caches
+ *     it; make that first call before any stream capture.
+ *   - Every call shares the one scratch array and overwrites the part it
+ *     uses (it resets the slot map at the start of each call that records
+ *     a trace with trace_idx).  Calls whose work overlaps on the GPU -- on
+ *     different streams, or from several threads -- race on it.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ * All state and I/O pointers are device memory owned by the caller; the
+ * state arrays are updated in place. */
+#define HH_NOALLOC_MAX_NEURONS (1 << 20)
+
+typedef struct {
+    int64_t n_neurons;       /* 1 .. HH_NOALLOC_MAX_NEURONS                   */
+    double dt_ms;            /* > 0                                            */
+    float v_threshold;       /* mV                                             */
+    int32_t v_update;        /* HH_V_*                                         */
+    int32_t precision;       /* HH_PREC_*; COMPENSATED needs V_lo, gates_lo    */
+    float* V;                /* device [N], updated in place                  */
+    float* V_lo;             /* device [N] or NULL                            */
+    float* gates;            /* device [HH_MAX_GATES][N], updated in place    */
+    float* gates_lo;         /* device [HH_MAX_GATES][N] or NULL              */
+    float* Ca;               /* device [N]                                    */
+    const float* I_const;    /* device [N] constant current, or NULL          */
+    const float* gbar;       /* device [HH_MAX_CHANNELS][N] per-neuron maximal
+                                conductances, or NULL for the model's         */
+    int32_t* status;         /* device int32 the call ORs HH_STATUS_* bits
+                                into, or NULL to discard them                 */
+    int32_t init_state;      /* 1: first set gates to p_inf(V), Ca to rest    */
+    void* stream;            /* cudaStream_t, NULL = legacy default stream    */
+} hh_neurons_noalloc;
+
+/* Advance the population by n_steps (Methods, Eq. hh_eq_full with the
+ * exponential-Euler discretisation, as hh_step_n for a network without
+ * synapses); t0 is the absolute index of the first step (spike records).
+ * m: the neuron model, host memory.  I_steps: device [n_steps][N] or NULL.
+ * rec: as for hh_step_n, or NULL.  Asynchronous on s->stream.
+ * Errors: HH_EINVAL (sizes beyond the limits, NULL state pointers, an
+ * invalid model, COMPENSATED without lo arrays), HH_ECUDA. */
+hh_status hh_step_neurons_noalloc(const hh_model_desc* m, const hh_neurons_noalloc* s,
+                                  int64_t t0, int32_t n_steps, const float* I_steps,
+                                  const hh_record* rec);
+
 /* Release everything the network owns (waits for its queued work). NULL ok. */
 void hh_destroy(hh_net* net);
 

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -842,3 +843,116 @@ const char* hh_last_error(void) { return g_err.c_str(); }
 int32_t hh_version(void) { return 0x000100; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free stepping of independent neurons.  The neuron kernel's only
+// scratch (the neuron -> V-trace-slot map, and one word that receives the
+// status bits when the caller passes no status pointer) lives in this
+// file-scope array; host code reaches it through the device address
+// cudaGetSymbolAddress returns for each device, looked up once per device
+// and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) int32_t g_noalloc_trace_slot[HH_NOALLOC_MAX_NEURONS + 64];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_addr[64] = {};
+
+hh_status noalloc_scratch(int32_t** out)
+{
+    int dev = 0;
+    HH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64)
+        return fail(HH_EUNSUPPORTED, "device index %d outside 0..63", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_trace_slot);
+        if (e != cudaSuccess || !p)
+            return fail(HH_ECUDA, "cudaGetSymbolAddress of the scratch array failed on device %d: %s",
+                        dev, cudaGetErrorString(e));
+        g_noalloc_addr[dev] = static_cast<int32_t*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return HH_OK;
+}
+
+}  // namespace
+
+extern "C" hh_status hh_step_neurons_noalloc(const hh_model_desc* m, const hh_neurons_noalloc* s,
+                                             int64_t t0, int32_t n_steps, const float* I_steps,
+                                             const hh_record* rec)
+{
+    if (!m || !s)
+        return fail(HH_EINVAL, "model and state descriptor must not be NULL");
+    const int64_t N = s->n_neurons;
+    if (N < 1 || N > HH_NOALLOC_MAX_NEURONS)
+        return fail(HH_EINVAL, "n_neurons %lld outside 1..%d (the static scratch holds %d neurons)",
+                    (long long)N, HH_NOALLOC_MAX_NEURONS, HH_NOALLOC_MAX_NEURONS);
+    if (n_steps < 0 || t0 < 0 || t0 + n_steps > (int64_t)INT32_MAX)
+        return fail(HH_EINVAL, "n_steps/t0 out of range");
+    if (!(s->dt_ms > 0.0) || !std::isfinite(s->dt_ms) || !finite_f(s->v_threshold))
+        return fail(HH_EINVAL, "dt_ms must be > 0 and v_threshold finite");
+    if (s->v_update != HH_V_EXP_EULER && s->v_update != HH_V_FWD_EULER)
+        return fail(HH_EINVAL, "unknown v_update %d", s->v_update);
+    if (s->precision < HH_PREC_FAST || s->precision > HH_PREC_COMPENSATED)
+        return fail(HH_EINVAL, "unknown precision %d", s->precision);
+    if (!s->V || !s->gates || !s->Ca)
+        return fail(HH_EINVAL, "V, gates and Ca are required");
+    if (s->precision == HH_PREC_COMPENSATED && (!s->V_lo || !s->gates_lo))
+        return fail(HH_EINVAL, "HH_PREC_COMPENSATED needs V_lo and gates_lo");
+    hh::RecordParams R{};
+    if (rec) {
+        if (rec->n_trace < 0 || (rec->V_trace && rec->n_trace == 0))
+            return fail(HH_EINVAL, "n_trace must be > 0 when V_trace is given");
+        if (rec->spikes && !rec->n_spikes)
+            return fail(HH_EINVAL, "spikes needs an n_spikes counter");
+        if (rec->spike_cap < 0)
+            return fail(HH_EINVAL, "spike_cap < 0");
+        if (!rec->trace_idx && rec->n_trace > N)
+            return fail(HH_EINVAL, "n_trace > N without trace_idx");
+        R.V_trace = rec->V_trace;
+        R.n_trace = rec->V_trace ? rec->n_trace : 0;
+        R.spikes = rec->spikes;
+        R.spike_cap = rec->spikes ? rec->spike_cap : 0;
+        R.n_spikes = reinterpret_cast<unsigned long long*>(rec->n_spikes);
+        R.counts = rec->counts;
+    }
+    hh::DevModels models{};
+    hh_status st = prep_model(m, s->dt_ms, &models.m[0]);
+    if (st != HH_OK)
+        return st;
+    models.n = 1;
+    models.max_gates = models.m[0].n_gates > 0 ? models.m[0].n_gates : 1;
+    int32_t* scratch = nullptr;
+    if ((st = noalloc_scratch(&scratch)) != HH_OK)
+        return st;
+    cudaStream_t stream = (cudaStream_t)s->stream;
+
+    hh::NeuronParams p{};
+    p.N = N;
+    p.dt = (float)s->dt_ms;
+    p.theta = s->v_threshold;
+    p.v_update = s->v_update;
+    p.V = s->V;
+    p.Vlo = s->V_lo;
+    p.P = s->gates;
+    p.Plo = s->gates_lo;
+    p.Ca = s->Ca;
+    p.gbar = s->gbar;
+    p.I_const = s->I_const;
+    p.status = s->status ? s->status : scratch + HH_NOALLOC_MAX_NEURONS;
+    p.R = 1;
+    if (s->init_state)
+        HH_CUDA(hh::launch_init_state(models, p, nullptr, -1, s->precision, stream));
+    if (n_steps == 0)
+        return HH_OK;
+    if (R.V_trace && rec->trace_idx) {
+        HH_CUDA(cudaMemsetAsync(scratch, 0xff, (size_t)N * sizeof(int32_t), stream));
+        HH_CUDA(hh::launch_trace_slots(rec->trace_idx, rec->n_trace, N, scratch, stream));
+        p.trace_slot = scratch;
+    }
+    HH_CUDA(hh::launch_independent(models, p, s->precision, t0, n_steps, I_steps, R, stream));
+    return HH_OK;
+}

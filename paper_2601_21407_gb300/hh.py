@@ -75,6 +75,17 @@ class hh_spike(C.Structure):
     _fields_ = [("step", C.c_int32), ("neuron", C.c_int32), ("frac", C.c_float)]
 
 
+class hh_neurons_noalloc(C.Structure):
+    _fields_ = [("n_neurons", C.c_int64), ("dt_ms", C.c_double), ("v_threshold", C.c_float),
+                ("v_update", C.c_int32), ("precision", C.c_int32), ("V", C.c_void_p),
+                ("V_lo", C.c_void_p), ("gates", C.c_void_p), ("gates_lo", C.c_void_p),
+                ("Ca", C.c_void_p), ("I_const", C.c_void_p), ("gbar", C.c_void_p),
+                ("status", C.c_void_p), ("init_state", C.c_int32), ("stream", C.c_void_p)]
+
+
+HH_NOALLOC_MAX_NEURONS = 1 << 20
+
+
 class hh_kernel_time(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -86,7 +97,8 @@ class hh_record(C.Structure):
 
 
 EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_route_spikes",
-           "hh_readout", "hh_profile", "hh_destroy", "hh_last_error", "hh_version"]
+           "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_destroy", "hh_last_error",
+           "hh_version"]
 
 
 def lib_path() -> str:
@@ -117,6 +129,9 @@ def lib():
             L.hh_readout.argtypes = [vp, C.c_int32, vp, C.c_size_t, P(C.c_size_t)]
             L.hh_profile.restype = C.c_int
             L.hh_profile.argtypes = [vp, C.c_int32]
+            L.hh_step_neurons_noalloc.restype = C.c_int
+            L.hh_step_neurons_noalloc.argtypes = [P(hh_model_desc), P(hh_neurons_noalloc), C.c_int64,
+                                                  C.c_int32, vp, P(hh_record)]
             L.hh_destroy.restype = None
             L.hh_destroy.argtypes = [vp]
             L.hh_last_error.restype = C.c_char_p
@@ -165,6 +180,12 @@ def hh_readout(net: int, what: int, dst_ptr, cap: int) -> int:
 
 def hh_profile(net: int, enable: bool):
     _check(lib().hh_profile(net, 1 if enable else 0))
+
+
+def hh_step_neurons_noalloc(model: hh_model_desc, state: hh_neurons_noalloc, t0: int, n_steps: int,
+                            I_steps_ptr=None, rec: hh_record | None = None):
+    _check(lib().hh_step_neurons_noalloc(C.byref(model), C.byref(state), t0, n_steps, I_steps_ptr,
+                                         C.byref(rec) if rec is not None else None))
 
 
 def hh_destroy(net: int):

@@ -44,6 +44,7 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void){
  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hh_fn), sizeof(hh_gate), sizeof(hh_channel),
    sizeof(hh_model_desc), sizeof(hh_net_desc), sizeof(hh_record), sizeof(hh_spike));
+ printf("%zu %zu\\n", sizeof(hh_neurons_noalloc), offsetof(hh_neurons_noalloc, status));
  printf("%zu %zu %zu %zu %zu\\n", offsetof(hh_net_desc, dt_ms), offsetof(hh_net_desc, n_synapses),
    offsetof(hh_net_desc, seed), offsetof(hh_net_desc, stream), offsetof(hh_model_desc, ca_tau));
  return 0; }
@@ -55,7 +56,8 @@ int main(void){
     got = [int(x) for x in out]
     want = [C.sizeof(hh.hh_fn), C.sizeof(hh.hh_gate), C.sizeof(hh.hh_channel),
             C.sizeof(hh.hh_model_desc), C.sizeof(hh.hh_net_desc), C.sizeof(hh.hh_record),
-            C.sizeof(hh.hh_spike), hh.hh_net_desc.dt_ms.offset, hh.hh_net_desc.n_synapses.offset,
+            C.sizeof(hh.hh_spike), C.sizeof(hh.hh_neurons_noalloc),
+            hh.hh_neurons_noalloc.status.offset, hh.hh_net_desc.dt_ms.offset, hh.hh_net_desc.n_synapses.offset,
             hh.hh_net_desc.seed.offset, hh.hh_net_desc.stream.offset,
             hh.hh_model_desc.ca_tau.offset]
     assert got == want
