@@ -278,7 +278,7 @@ def run_gpu(args):
                          "frac": achieved_gops / peak_gops, "traffic": None,
                          "peak_source": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} SFU ops/clk x "
                                         f"{sm_max:.0f} MHz ({pk_kind} sm_max)",
-                         "ops_per_neuron_step": mufu, "kernel": "k_net_window"},
+                         "ops_per_neuron_step": mufu, "kernel": "hh_jit_window (k_net_window specialised by NVRTC)"},
             "clocks": clk,
         }
         if cpu is not None:

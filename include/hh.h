@@ -137,6 +137,18 @@ typedef struct {
 enum { HH_PREC_FAST = 0, HH_PREC_ACCURATE = 1, HH_PREC_COMPENSATED = 2 };
 enum { HH_V_EXP_EULER = 0, HH_V_FWD_EULER = 1 };
 
+/* Neuron kernels:
+ *   HH_KERNELS_SPECIALISED  compiled with NVRTC for the installed models at
+ *                           the first hh_step_n after hh_set_channels (the
+ *                           model table becomes compile-time constants;
+ *                           about a second per new model set, cached for the
+ *                           life of the process);
+ *   HH_KERNELS_TABLE        precompiled kernels that read the model table at
+ *                           run time (no compilation; slower per step).
+ * Both run the same device code and give the same results up to the
+ * compiler's instruction selection (FMA contraction).                     */
+enum { HH_KERNELS_SPECIALISED = 0, HH_KERNELS_TABLE = 1 };
+
 typedef struct {
     int64_t n_neurons;          /* N >= 1 (all networks together)            */
     int32_t n_nets;             /* >= 1 independent networks, concatenated     */
@@ -148,6 +160,7 @@ typedef struct {
     float v_threshold;          /* spike threshold theta (mV)                 */
     int32_t v_update;           /* HH_V_*                                     */
     int32_t precision;          /* HH_PREC_*                                  */
+    int32_t kernels;            /* HH_KERNELS_*                               */
     const float* V0;            /* [N] initial V, any memory (copied)        */
     const float* I_const;       /* [N] constant injected current, any memory,
                                    or NULL for none                            */
@@ -237,7 +250,9 @@ typedef struct {
  *   rec    : outputs, or NULL.
  * Asynchronous on the network's stream.  Errors: HH_EINVAL (n_steps < 0,
  * trace_idx out of range is not checked: the caller guarantees it),
- * HH_ESTATE (a model index used by model_id was never installed), HH_ECUDA. */
+ * HH_ESTATE (a model index used by model_id was never installed), HH_ECUDA
+ * (also when the specialised kernels fail to compile: the message holds the
+ * compiler log). */
 hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps,
                     const hh_record* rec);
 

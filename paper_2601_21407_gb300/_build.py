@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhh.so")
-SOURCES = ["hh_kernels.cu", "hh_abi.cu"]
+SOURCES = ["hh_kernels.cu", "hh_abi.cu", "hh_jit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,9 +45,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # the shared device code is compiled into the library and also embedded
+    # verbatim for the run-time (NVRTC) specialisation of the neuron kernels
+    src = open(os.path.join(CSRC, "hh_device.cuh")).read()
+    assert ')HHSRC"' not in src
+    with open(os.path.join(BUILD, "hh_device_src.inc"), "w") as f:
+        f.write('R"HHSRC(' + src + ')HHSRC"\n')
     cc = nvcc()
+    cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(cc)))
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                     "-I", os.path.join(HERE, "..", "include")]
+                     "-I", os.path.join(HERE, "..", "include"), "-I", BUILD]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
     procs, objs = [], []
@@ -65,7 +72,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         if p.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + logs[-1])
     tmp = LIB + f".{os.getpid()}.tmp"
-    link = [cc, "-shared"] + ARCH + objs + ["-o", tmp, "-lcudart"]
+    libdir = os.path.join(cuda_home, "lib64")
+    link = [cc, "-shared"] + ARCH + objs + ["-o", tmp, "-lcudart", "-lnvrtc", "-L", libdir,
+                                            "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

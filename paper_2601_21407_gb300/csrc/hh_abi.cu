@@ -41,6 +41,9 @@ struct hh_net {
     double dt = 0.0;
     float theta = 0.0f;
     int32_t v_update = 0, precision = 0;
+    int32_t kernels = HH_KERNELS_SPECIALISED;
+    hh::JitKernels jit{};
+    bool jit_ready = false;
     cudaStream_t st = nullptr;
     int64_t t = 0;
     int64_t window_index = 0;
@@ -349,6 +352,7 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
     n->theta = d->v_threshold;
     n->v_update = d->v_update;
     n->precision = d->precision;
+    n->kernels = d->kernels;
     n->st = (cudaStream_t)d->stream;
     cudaStream_t st = n->st;
 
@@ -481,9 +485,12 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
             op[0] = 0;
             for (int64_t j = 0; j < N; ++j)
                 op[j + 1] = op[j] + hc[j];
+            // 4 entries of padding: the routing kernel reads rows as aligned int4/float4
             if ((e = n->alloc(&n->out_ptr, N + 1)) != cudaSuccess ||
-                (e = n->alloc(&n->out_post, S)) != cudaSuccess ||
-                (e = n->alloc(&n->out_w, S)) != cudaSuccess) {
+                (e = n->alloc(&n->out_post, S + 4)) != cudaSuccess ||
+                (e = n->alloc(&n->out_w, S + 4)) != cudaSuccess ||
+                (e = cudaMemsetAsync(n->out_post + S, 0, 4 * sizeof(int32_t), st)) != cudaSuccess ||
+                (e = cudaMemsetAsync(n->out_w + S, 0, 4 * sizeof(float), st)) != cudaSuccess) {
                 rc = fail(HH_ENOMEM, "allocating the out-CSR: %s", cudaGetErrorString(e));
                 break;
             }
@@ -572,6 +579,8 @@ hh_status hh_create_network(const hh_net_desc* d, hh_net** out)
         return fail(HH_EINVAL, "unknown v_update %d", d->v_update);
     if (d->precision < HH_PREC_FAST || d->precision > HH_PREC_COMPENSATED)
         return fail(HH_EINVAL, "unknown precision %d", d->precision);
+    if (d->kernels != HH_KERNELS_SPECIALISED && d->kernels != HH_KERNELS_TABLE)
+        return fail(HH_EINVAL, "unknown kernels %d", d->kernels);
     if (!d->V0)
         return fail(HH_EINVAL, "V0 is required");
     hh_net* n = new (std::nothrow) hh_net();
@@ -601,6 +610,7 @@ hh_status hh_set_channels(hh_net* net, int32_t model_index, const hh_model_desc*
         return s;
     net->models.m[model_index] = dm;
     net->installed[model_index] = true;
+    net->jit_ready = false;
     net->models.max_gates = max_gates_installed(net);
     net->models.n = HH_MAX_MODELS;
     if (gbar || net->gbar) {
@@ -689,7 +699,19 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         net->ev_used.push_back({kind, {e0, e1}});
         return e;
     };
+    if (net->kernels == HH_KERNELS_SPECIALISED && !net->jit_ready) {
+        std::string err;
+        if (!hh::jit_get(net->models, net->installed, net->precision, &net->jit, &err))
+            return fail(HH_ECUDA, "%s", err.c_str());
+        net->jit_ready = true;
+    }
+    const bool spec = net->kernels == HH_KERNELS_SPECIALISED;
     if (!net->has_syn && !net->has_bg) {
+        if (spec)
+            HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
+                return hh::jit_launch_independent(net->jit, p, net->t, n_steps, I_steps, R, net->st);
+            }));
+        else
         HH_CUDA(timed(HH_KERNEL_NEURON, [&] { return hh::launch_independent(net->models, p, net->precision, net->t, n_steps, I_steps, R,
                                        net->st); }));
     } else {
@@ -701,10 +723,13 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
             hh::RecordParams Rw = R;
             if (Rw.V_trace)
                 Rw.V_trace += (int64_t)w0 * Rw.n_trace;
+            const float* Iw = I_steps ? I_steps + (int64_t)w0 * net->N : nullptr;
             HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
-                return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, parity,
-                                             I_steps ? I_steps + (int64_t)w0 * net->N : nullptr, Rw,
-                                             net->list, net->st);
+                if (spec)
+                    return hh::jit_launch_window(net->jit, p, net->t + w0, W, parity, Iw, Rw, net->list,
+                                                 net->st);
+                return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, parity, Iw,
+                                             Rw, net->list, net->st);
             }));
             if (net->has_syn)
                 HH_CUDA(timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, parity, net->st); }));

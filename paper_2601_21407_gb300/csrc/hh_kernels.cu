@@ -1,19 +1,18 @@
-// CUDA kernels of the Hodgkin-Huxley hot path (sm_103a).
+// CUDA kernels of the Hodgkin-Huxley hot path compiled into libhh.so (sm_103a).
 //
-//   k_independent  many time steps of independent neurons in one launch, the
-//                  neuron state held in registers across steps (Methods,
-//                  Eq. hh_eq_full with exponential-Euler gates and V).
-//   k_net_window   up to D (synaptic delay) steps of a network: the input of
-//                  every step in the window was produced by spikes at least D
-//                  steps earlier, so neurons stay independent inside the
-//                  window and only the window boundary needs a grid-wide
-//                  ordering (the routing launch).  Per step: delivery from the
-//                  delay ring + Poisson background, rates, gates, V, Ca,
-//                  threshold, warp-aggregated spike compaction, synaptic decay.
+//   k_independent  (table interpreter) many time steps of independent neurons
+//                  in one launch, state in registers (Methods, Eq. hh_eq_full
+//                  with exponential-Euler gates and V)
+//   k_net_window   (table interpreter) up to D steps of a network per launch:
+//                  delivery from the delay ring + Poisson background, rates,
+//                  gates, V, Ca, threshold, warp-aggregated spike compaction,
+//                  synaptic decay
 //   k_route        spike propagation over the out-CSR: one warp per spike,
-//                  coalesced reads of (target, weight), 64-bit fixed-point
-//                  atomic adds into the delay ring (order independent).
+//                  128-bit reads of (target, weight), 64-bit fixed-point
+//                  atomic adds into the delay ring (order independent)
 //   transpose/check/init/trace helpers.
+// The neuron bodies live in hh_device.cuh and are shared with the per-model
+// kernels compiled at run time (hh_jit.cu).
 #include <cstdint>
 
 #include "hh_internal.h"
@@ -21,489 +20,71 @@
 namespace hh {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float ex2a(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rcpa(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Arithmetic policies: SFU approximations or IEEE-accurate FP32.
-template <bool FAST>
-struct Mth;
-
-template <>
-struct Mth<true> {
-    static __device__ __forceinline__ float expv(const DevFn& f, float V) { return ex2a(fmaf(V, f.s, f.b)); }
-    static __device__ __forceinline__ float expv2(const DevFn& f, float V) { return ex2a(fmaf(V, f.s2, f.b2)); }
-    static __device__ __forceinline__ float div(float a, float b) { return a * rcpa(b); }
-};
-
-template <>
-struct Mth<false> {
-    static __device__ __forceinline__ float expv(const DevFn& f, float V) { return expf((V - f.vh) * f.ik); }
-    static __device__ __forceinline__ float expv2(const DevFn& f, float V) { return expf((V - f.vh2) * f.ik2); }
-    static __device__ __forceinline__ float div(float a, float b) { return a / b; }
-};
-
-// c + form(V) for the closed forms of the ABI (HH_FN_*).
-template <bool FAST>
-__device__ __forceinline__ float rate(const DevFn& f, float V)
-{
-    using M = Mth<FAST>;
-    float r;
-    switch (f.form) {
-    case HH_FN_CONST:
-        r = f.a;
-        break;
-    case HH_FN_EXP:
-        r = f.a * M::expv(f, V);
-        break;
-    case HH_FN_SIGMOID:
-        r = M::div(f.a, 1.0f + M::expv(f, V));
-        break;
-    case HH_FN_LINOID: {
-        // a x / (1 - e^{-x/k}) = a k * y/(1 - e^{-y}), y = x/k.  Near y = 0 the
-        // SFU path uses the Bernoulli series 1 + y/2 + y^2/12 - y^4/720
-        // (truncation < 1e-10 for |y| < 0.1); the accurate path uses expm1f.
-        const float x = V - f.vh;
-        if (FAST) {
-            const float y = x * f.ik;
-            if (fabsf(y) < 0.1f) {
-                const float y2 = y * y;
-                r = f.a * f.k * (1.0f + 0.5f * y + y2 * (1.0f / 12.0f - y2 * (1.0f / 720.0f)));
-            } else {
-                r = f.a * x * rcpa(1.0f - ex2a(-y * kLog2e));
-            }
-        } else {
-            r = (x == 0.0f) ? f.a * f.k : f.a * x / (-expm1f(-x * f.ik));
-        }
-        break;
+// Dynamics read from a model table in the kernel parameters.
+struct TableDyn {
+    const DevModels& Ms;
+    template <int MAXG, int PREC>
+    __device__ __forceinline__ void load(int mid, const NeuronParams& P, int64_t i,
+                                         State<MAXG, PREC>& s) const
+    {
+        load_conductances(Ms.m[mid], P.gbar, P.N, i, s);
     }
-    default:  // HH_FN_BELL
-        r = M::div(f.a, M::expv(f, V) + M::expv2(f, V));
-        break;
+    template <int MAXG, int PREC>
+    __device__ __forceinline__ void step(int mid, float dt, int v_update, float I, float gsE, float EE,
+                                         float gsI, float EI, State<MAXG, PREC>& s) const
+    {
+        neuron_step<MAXG, PREC>(Ms.m[mid], dt, v_update, I, gsE, EE, gsI, EI, s);
     }
-    return r + f.c;
-}
-
-// Steady-state value and dt/tau of one gate at (V, Ca).
-template <bool FAST>
-__device__ __forceinline__ void gate_inf_z(const DevGate& g, float V, float Ca, float dt, float& inf,
-                                           float& z)
-{
-    using M = Mth<FAST>;
-    if (g.kind == HH_GATE_AB) {
-        const float al = rate<FAST>(g.f1, V), be = rate<FAST>(g.f2, V);
-        const float s = al + be;
-        inf = M::div(al, s);
-        z = dt * s;
-    } else if (g.kind == HH_GATE_INFTAU) {
-        inf = rate<FAST>(g.f1, V);
-        z = M::div(dt, rate<FAST>(g.f2, V));
-    } else {
-        inf = M::div(Ca, Ca + g.f1.a);
-        z = M::div(dt, rate<FAST>(g.f2, V));
-    }
-}
-
-// 1 - e^{-z} for z >= 0 with a small relative error.  The SFU path uses the
-// Taylor polynomial of -expm1(-z) up to z^8 below z = 0.5 (truncation
-// < 1.2e-8 relative) and 1 - 2^{-z log2 e} above; the accurate path expm1f.
-// Forming the update as an increment (p_inf - p)(1 - e^{-z}) keeps the
-// relaxation rate exact to rounding even when z is small, where
-// p_inf + (p - p_inf) e^{-z} would turn the absolute error of e^{-z} near 1
-// into a relative error of order ulp/z on every step.
-template <bool FAST>
-__device__ __forceinline__ float em1(float z)
-{
-    if (FAST) {
-        if (z < 0.5f) {
-            float c = fmaf(z, -1.0f / 40320.0f, 1.0f / 5040.0f);
-            c = fmaf(z, c, -1.0f / 720.0f);
-            c = fmaf(z, c, 1.0f / 120.0f);
-            c = fmaf(z, c, -1.0f / 24.0f);
-            c = fmaf(z, c, 1.0f / 6.0f);
-            c = fmaf(z, c, -0.5f);
-            c = fmaf(z, c, 1.0f);
-            return z * c;
-        }
-        return 1.0f - ex2a(-z * kLog2e);
-    }
-    return -expm1f(-z);
-}
-
-__device__ __forceinline__ float powi(float p, int n)
-{
-    switch (n) {
-    case 1: return p;
-    case 2: return p * p;
-    case 3: return p * p * p;
-    default: {
-        const float q = p * p;
-        return q * q;
-    }
-    }
-}
-
-// hi + lo += d with an error-free two-sum and renormalisation.
-__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float d)
-{
-    const float s = __fadd_rn(hi, d);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
-    const float lo2 = __fadd_rn(lo, err);
-    const float h2 = __fadd_rn(s, lo2);
-    lo = __fsub_rn(lo2, __fsub_rn(h2, s));
-    hi = h2;
-}
-
-template <int MAXG, int PREC>
-struct State {
-    float V, Vlo, Ca;
-    float p[MAXG];
-    float plo[MAXG];
-    // per-neuron conductance layout: gate q closes channel ch_last[q]
-    float gq[MAXG];   // maximal conductance of the channel closed at gate q
-    float gconst, gconstE;  // gate-less channels: sum gbar, sum gbar*E
 };
 
 template <int MAXG, int PREC>
-__device__ __forceinline__ void load_conductances(const DevModel& M, const float* __restrict__ gbar,
-                                                  int64_t N, int64_t i, State<MAXG, PREC>& s)
-{
-    s.gconst = 0.0f;
-    s.gconstE = 0.0f;
-#pragma unroll
-    for (int c = 0; c < kMaxChannels; ++c) {
-        if (c < M.n_ch && M.ch_ng[c] == 0) {
-            const float g = gbar ? gbar[(int64_t)c * N + i] : M.gbar[c];
-            s.gconst += g;
-            s.gconstE += g * M.E[c];
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < MAXG; ++q) {
-        s.gq[q] = 0.0f;
-        if (q < M.n_gates && M.gate_last[q]) {
-            const int c = M.gate_ch[q];
-            s.gq[q] = gbar ? gbar[(int64_t)c * N + i] : M.gbar[c];
-        }
-    }
-}
-
-// One exponential-Euler step of one neuron (order: rates at V_t, gates,
-// conductances with the new gates, V, Ca).  gsE/gsI in mS/cm^2.
-template <int MAXG, int PREC>
-__device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_update, float I,
-                                            float gsE, float EE, float gsI, float EI,
-                                            State<MAXG, PREC>& s)
-{
-    constexpr bool FAST = PREC == HH_PREC_FAST;
-    using Mt = Mth<FAST>;
-    const float V = s.V;
-#pragma unroll
-    for (int q = 0; q < MAXG; ++q) {
-        if (q < M.n_gates) {
-            float inf, z;
-            gate_inf_z<FAST>(M.g[q], V, s.Ca, dt, inf, z);
-            if (PREC == HH_PREC_COMPENSATED) {
-                const float d = ((inf - s.p[q]) - s.plo[q]) * em1<false>(z);
-                two_sum_add(s.p[q], s.plo[q], d);
-            } else {
-                s.p[q] = fmaf(inf - s.p[q], em1<FAST>(z), s.p[q]);
-            }
-        }
-    }
-    float G = gsE + gsI + s.gconst;
-    float Ip = gsE * (V - EE) + gsI * (V - EI) + (s.gconst * V - s.gconstE);
-    float gCa = 0.0f, ECa = 0.0f;
-    float eta = 1.0f;
-#pragma unroll
-    for (int q = 0; q < MAXG; ++q) {
-        if (q < M.n_gates) {
-            eta *= powi(s.p[q], M.g[q].power);
-            if (M.gate_last[q]) {
-                const float gx = s.gq[q] * eta;
-                const float Ex = M.gate_E[q];
-                G += gx;
-                Ip += gx * (V - Ex);
-                if (M.gate_ca[q]) {
-                    gCa = gx;
-                    ECa = Ex;
-                }
-                eta = 1.0f;
-            }
-        }
-    }
-    // V: exponential Euler with frozen conductances, as an increment
-    //   dV = (V_inf - V)(1 - e^{-dt G/C}) = (I - I_ion)/G (1 - e^{-dt G/C}),
-    // I_ion = sum g (V - E) formed term by term (no cancellation near rest);
-    // or explicit Euler dV = dt/C (I - I_ion).
-    const float Iion = PREC == HH_PREC_COMPENSATED ? Ip + G * s.Vlo : Ip;
-    float dV;
-    if (v_update == HH_V_EXP_EULER)
-        dV = Mt::div(I - Iion, G) * em1<FAST>(dt * G * M.inv_C);
-    else
-        dV = dt * M.inv_C * (I - Iion);
-    if (PREC == HH_PREC_COMPENSATED)
-        two_sum_add(s.V, s.Vlo, dV);
-    else
-        s.V = V + dV;
-    if (M.ca_ch >= 0) {
-        const float ICa = gCa * (V - ECa);
-        const float Cainf = M.ca_rest - M.ca_k * M.ca_tau * ICa;
-        s.Ca = fmaf(s.Ca - Cainf, M.ca_decay, Cainf);
-    }
-}
-
-template <int MAXG, int PREC>
-__device__ __forceinline__ void load_state(const NeuronParams& P, int64_t i, State<MAXG, PREC>& s)
-{
-    s.V = P.V[i];
-    s.Vlo = PREC == HH_PREC_COMPENSATED ? P.Vlo[i] : 0.0f;
-    s.Ca = P.Ca[i];
-#pragma unroll
-    for (int q = 0; q < MAXG; ++q) {
-        s.p[q] = P.P[(int64_t)q * P.N + i];
-        s.plo[q] = PREC == HH_PREC_COMPENSATED ? P.Plo[(int64_t)q * P.N + i] : 0.0f;
-    }
-}
-
-template <int MAXG, int PREC>
-__device__ __forceinline__ void store_state(const NeuronParams& P, int64_t i, const State<MAXG, PREC>& s)
-{
-    P.V[i] = s.V;
-    if (PREC == HH_PREC_COMPENSATED)
-        P.Vlo[i] = s.Vlo;
-    P.Ca[i] = s.Ca;
-#pragma unroll
-    for (int q = 0; q < MAXG; ++q) {
-        P.P[(int64_t)q * P.N + i] = s.p[q];
-        if (PREC == HH_PREC_COMPENSATED)
-            P.Plo[(int64_t)q * P.N + i] = s.plo[q];
-    }
-}
-
-// Warp-aggregated append of this step's spikes to the caller's record:
-// one atomic per warp (ballot + popc), each spiking lane writes its slot.
-__device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t idx, float frac,
-                                              const RecordParams& R, int32_t* status)
-{
-    const unsigned b = __ballot_sync(kFull, spk);
-    if (b == 0u || R.n_spikes == nullptr)
-        return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(b) - 1;
-    unsigned long long base = 0;
-    if (lane == leader)
-        base = atomicAdd(R.n_spikes, (unsigned long long)__popc(b));
-    base = __shfl_sync(kFull, base, leader);
-    if (spk) {
-        const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
-        if (pos < (unsigned long long)R.spike_cap) {
-            hh_spike e;
-            e.step = step;
-            e.neuron = idx;
-            e.frac = frac;
-            R.spikes[pos] = e;
-        } else {
-            atomicOr(status, HH_STATUS_SPIKE_OVERFLOW);
-        }
-    }
-}
-
-__device__ __forceinline__ void list_append(bool spk, int32_t step, int32_t idx, int32_t* counter,
-                                            int32_t* lstep, int32_t* lidx, int64_t cap)
-{
-    const unsigned b = __ballot_sync(kFull, spk);
-    if (b == 0u)
-        return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(b) - 1;
-    int base = 0;
-    if (lane == leader)
-        base = atomicAdd(counter, __popc(b));
-    base = __shfl_sync(kFull, base, leader);
-    if (spk) {
-        const int pos = base + __popc(b & ((1u << lane) - 1u));
-        if (pos < cap) {
-            lstep[pos] = step;
-            lidx[pos] = idx;
-        }
-    }
-}
-
-// Philox-4x32-10 (Salmon et al., SC'11).
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-    return c;
-}
-
-__device__ __forceinline__ uint32_t pick(const uint4& v, int w)
-{
-    return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
-}
-
-// -------------------------------------------------------------------------
-// Independent neurons: n_steps in one launch, state in registers.
-// -------------------------------------------------------------------------
-template <int MAXG, int PREC>
-__global__ void __launch_bounds__(128) k_independent(const DevModels Ms, const NeuronParams P,
+__global__ void __launch_bounds__(128) k_independent(const __grid_constant__ DevModels Ms,
+                                                     const __grid_constant__ NeuronParams P,
                                                      int64_t t0, int32_t n_steps,
                                                      const float* __restrict__ I_steps,
-                                                     const RecordParams R)
+                                                     const __grid_constant__ RecordParams R)
 {
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = gi < P.N;
-    const int64_t i = valid ? gi : 0;
-    const DevModel& M = Ms.m[P.model_id ? P.model_id[i] : 0];
-    State<MAXG, PREC> s;
-    load_state(P, i, s);
-    load_conductances(M, P.gbar, P.N, i, s);
-    const float Ic = P.I_const ? P.I_const[i] : 0.0f;
-    int32_t slot = -1;
-    if (R.V_trace)
-        slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
-    if (!valid)
-        slot = -1;
-    int32_t cnt = 0;
-    for (int32_t k = 0; k < n_steps; ++k) {
-        const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
-        const float Vt = s.V;
-        neuron_step<MAXG, PREC>(M, P.dt, P.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, s);
-        const bool spk = valid && Vt < P.theta && s.V >= P.theta;
-        cnt += spk;
-        const float frac = spk ? (P.theta - Vt) / (s.V - Vt) : 0.0f;
-        record_spikes(spk, (int32_t)(t0 + k), (int32_t)i, frac, R, P.status);
-        if (slot >= 0)
-            R.V_trace[(int64_t)k * R.n_trace + slot] = s.V;
-    }
-    if (valid) {
-        store_state(P, i, s);
-        if (R.counts && cnt)
-            R.counts[i] += cnt;
-        if (!isfinite(s.V))
-            atomicOr(P.status, HH_STATUS_NONFINITE);
-    }
+    independent_body<MAXG, PREC>(TableDyn{Ms}, P, t0, n_steps, I_steps, R);
 }
 
-// -------------------------------------------------------------------------
-// Network window: W <= D steps; spikes go to the window list for routing.
-// -------------------------------------------------------------------------
 template <int MAXG, int PREC>
-__global__ void __launch_bounds__(128) k_net_window(const DevModels Ms, const NeuronParams P,
+__global__ void __launch_bounds__(128) k_net_window(const __grid_constant__ DevModels Ms,
+                                                    const __grid_constant__ NeuronParams P,
                                                     int64_t t0, int32_t W,
                                                     const float* __restrict__ I_steps,
-                                                    const RecordParams R, const SpikeList L,
+                                                    const __grid_constant__ RecordParams R,
+                                                    const __grid_constant__ SpikeList L,
                                                     int32_t parity)
 {
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi == 0)
-        L.counter[parity ^ 1] = 0;  // the next window's list (its reader has finished)
-    const bool valid = gi < P.N;
-    const int64_t i = valid ? gi : 0;
-    const DevModel& M = Ms.m[P.model_id ? P.model_id[i] : 0];
-    State<MAXG, PREC> s;
-    load_state(P, i, s);
-    load_conductances(M, P.gbar, P.N, i, s);
-    float gE = P.gE[i], gI = P.gI[i];
-    const float Ic = P.I_const ? P.I_const[i] : 0.0f;
-    int32_t slot = -1;
-    if (R.V_trace)
-        slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
-    if (!valid)
-        slot = -1;
-    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-    uint4 rnd = make_uint4(0, 0, 0, 0);
-    int32_t cnt = 0;
-    int32_t ring_slot = (int32_t)(t0 % P.R);
-    // The delay-line slots of this window were completed by earlier routing
-    // launches: prefetch one step ahead so the L2 latency overlaps compute.
-    long long nE = 0, nI = 0;
-    if (valid && W > 0) {
-        nE = P.ringE[(int64_t)ring_slot * P.N + i];
-        nI = P.ringI[(int64_t)ring_slot * P.N + i];
-    }
-    for (int32_t k = 0; k < W; ++k) {
-        const int64_t t = t0 + k;
-        const long long e = nE, h = nI;
-        const int32_t next_slot = ring_slot + 1 == P.R ? 0 : ring_slot + 1;
-        if (valid && k + 1 < W) {
-            nE = P.ringE[(int64_t)next_slot * P.N + i];
-            nI = P.ringI[(int64_t)next_slot * P.N + i];
-        }
-        // a. delayed synaptic input (fixed point 2^-32 nS) and background
-        if (valid) {
-            const int64_t o = (int64_t)ring_slot * P.N + i;
-            if (e) {
-                gE += __ll2float_rn(e) * 2.3283064365386963e-10f;
-                P.ringE[o] = 0;
-            }
-            if (h) {
-                gI += __ll2float_rn(h) * 2.3283064365386963e-10f;
-                P.ringI[o] = 0;
-            }
-        }
-        if (P.bg_n > 0) {
-            if (k == 0 || (t & 3) == 0) {
-                const uint64_t q = (uint64_t)t >> 2;
-                rnd = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
-            }
-            const unsigned long long u = pick(rnd, (int)(t & 3));
-            int32_t c = 0;
-            while (c < P.bg_n && u >= P.bg_thr[c])
-                ++c;
-            gE += (float)c * P.bg_w;
-        }
-        const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
-        const float Vt = s.V;
-        neuron_step<MAXG, PREC>(M, P.dt, P.v_update, I, gE * P.to_mS, P.E_E, gI * P.to_mS, P.E_I, s);
-        const bool spk = valid && Vt < P.theta && s.V >= P.theta;
-        cnt += spk;
-        list_append(spk, (int32_t)t, (int32_t)i, L.counter + parity, L.step, L.idx, L.cap);
-        if (R.n_spikes) {
-            const float frac = spk ? (P.theta - Vt) / (s.V - Vt) : 0.0f;
-            record_spikes(spk, (int32_t)t, (int32_t)i, frac, R, P.status);
-        }
-        if (slot >= 0)
-            R.V_trace[(int64_t)k * R.n_trace + slot] = s.V;
-        gE *= P.decE;
-        gI *= P.decI;
-        ring_slot = next_slot;
-    }
-    if (valid) {
-        store_state(P, i, s);
-        P.gE[i] = gE;
-        P.gI[i] = gI;
-        if (R.counts && cnt)
-            R.counts[i] += cnt;
-        if (!isfinite(s.V))
-            atomicOr(P.status, HH_STATUS_NONFINITE);
-    }
+    window_body<MAXG, PREC>(TableDyn{Ms}, P, t0, W, I_steps, R, L, parity);
+}
+
+// w (nS, finite, 0 <= w < 65536) as a 64-bit fixed-point count of 2^-32 nS,
+// from the float's bits with integer operations only (the 64-bit float ->
+// integer conversion executes on the FP64 unit).  Exact for w >= 2^-9 nS;
+// below, rounded to nearest with ties up.
+__device__ __forceinline__ unsigned long long nS_to_fixed(float w)
+{
+    const unsigned b = __float_as_uint(w);
+    const int e = (int)(b >> 23);
+    const unsigned m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int sh = (e ? e : 1) - 118;  // w 2^32 = m 2^(e - 150 + 32)
+    if (sh >= 0)
+        return (unsigned long long)m << sh;
+    if (sh < -40)
+        return 0ull;
+    return ((unsigned long long)m + (1ull << (-sh - 1))) >> (-sh);
 }
 
 // -------------------------------------------------------------------------
-// Spike routing: one warp per spike; the spike count is read on the device.
+// Spike routing: one warp per spike.  The out-row is walked in 128-edge
+// chunks aligned to 4 edges: lane l reads the int4 of targets and the float4
+// of weights at chunk + 4l (the arrays carry 4 entries of padding), masks the
+// entries outside the row and issues one RED.ADD.64 per edge.  Two chunks
+// are in flight per iteration.  The spike count is read on the device.
 // -------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_route(const RouteParams RP, const int32_t* __restrict__ st,
+__global__ void __launch_bounds__(256) k_route(const __grid_constant__ RouteParams RP,
+                                               const int32_t* __restrict__ st,
                                                const int32_t* __restrict__ ix,
                                                const int32_t* __restrict__ n_dev, int64_t n_host,
                                                int64_t cap)
@@ -529,10 +110,28 @@ __global__ void __launch_bounds__(256) k_route(const RouteParams RP, const int32
         }
         unsigned long long* dst =
             reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
-        const int64_t e1 = RP.out_ptr[j + 1];
-        for (int64_t e = RP.out_ptr[j] + lane; e < e1; e += 32) {
-            const long long q = __float2ll_rn(RP.out_w[e] * 4294967296.0f);
-            atomicAdd(dst + RP.out_post[e], (unsigned long long)q);
+        const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
+        for (int64_t base = (e0 & ~(int64_t)3); base < e1; base += 256) {
+            const int64_t ea = base + 4 * lane;
+            const int64_t eb = ea + 128;
+            int4 pa = make_int4(0, 0, 0, 0), pb = pa;
+            float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
+            if (ea < e1) {
+                pa = *reinterpret_cast<const int4*>(RP.out_post + ea);
+                wa = *reinterpret_cast<const float4*>(RP.out_w + ea);
+            }
+            if (eb < e1) {
+                pb = *reinterpret_cast<const int4*>(RP.out_post + eb);
+                wb = *reinterpret_cast<const float4*>(RP.out_w + eb);
+            }
+            const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+            const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t e = (q < 4 ? ea : eb) + (q & 3);
+                if (e >= e0 && e < e1)
+                    atomicAdd(dst + pp[q], nS_to_fixed(ww[q]));
+            }
         }
     }
 }
@@ -541,7 +140,7 @@ __global__ void __launch_bounds__(256) k_route(const RouteParams RP, const int32
 // Helpers
 // -------------------------------------------------------------------------
 template <int MAXG>
-__global__ void k_init_state(const DevModels Ms, const NeuronParams P, const float* __restrict__ V0,
+__global__ void k_init_state(const __grid_constant__ DevModels Ms, const __grid_constant__ NeuronParams P, const float* __restrict__ V0,
                              int32_t model_index)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -608,7 +207,7 @@ __global__ void k_fill_out(const int64_t* __restrict__ row_ptr, const int32_t* _
     }
 }
 
-__global__ void k_fill_gbar(const DevModels Ms, int64_t N, const uint8_t* __restrict__ model_id,
+__global__ void k_fill_gbar(const __grid_constant__ DevModels Ms, int64_t N, const uint8_t* __restrict__ model_id,
                             int32_t model_index, const float* __restrict__ src, float* gbar)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -694,7 +293,7 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
 cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity,
                                 cudaStream_t st)
 {
-    k_route<<<152 * 4, 256, 0, st>>>(RP, L.step, L.idx, L.counter + parity, 0, L.cap);
+    k_route<<<152 * 8, 256, 0, st>>>(RP, L.step, L.idx, L.counter + parity, 0, L.cap);
     return cudaGetLastError();
 }
 
@@ -703,7 +302,7 @@ cudaError_t launch_route_list(const RouteParams& RP, const int32_t* step, const 
 {
     if (n <= 0)
         return cudaSuccess;
-    k_route<<<152 * 4, 256, 0, st>>>(RP, step, idx, nullptr, n, n);
+    k_route<<<152 * 8, 256, 0, st>>>(RP, step, idx, nullptr, n, n);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ HH_GATE = {"ab": 0, "inftau": 1, "ca": 2}
 HH_MAX_CHANNELS, HH_MAX_GATES_PER_CHANNEL, HH_MAX_GATES, HH_MAX_MODELS = 8, 3, 8, 4
 HH_PREC_FAST, HH_PREC_ACCURATE, HH_PREC_COMPENSATED = 0, 1, 2
 HH_V_EXP_EULER, HH_V_FWD_EULER = 0, 1
+HH_KERNELS_SPECIALISED, HH_KERNELS_TABLE = 0, 1
 (HH_READ_V, HH_READ_GATES, HH_READ_CA, HH_READ_G_SYN, HH_READ_STATUS, HH_READ_TIME,
  HH_READ_N_OUT, HH_READ_PROFILE) = range(8)
 HH_KERNEL_NEURON, HH_KERNEL_ROUTE, HH_KERNEL_COUNT = 0, 1, 2
@@ -62,7 +63,8 @@ class hh_model_desc(C.Structure):
 class hh_net_desc(C.Structure):
     _fields_ = [("n_neurons", C.c_int64), ("n_nets", C.c_int32), ("net_offsets", C.c_void_p),
                 ("dt_ms", C.c_double), ("v_threshold", C.c_float), ("v_update", C.c_int32),
-                ("precision", C.c_int32), ("V0", C.c_void_p), ("I_const", C.c_void_p),
+                ("precision", C.c_int32), ("kernels", C.c_int32), ("V0", C.c_void_p),
+                ("I_const", C.c_void_p),
                 ("model_id", C.c_void_p), ("n_synapses", C.c_int64), ("row_ptr", C.c_void_p),
                 ("col_idx", C.c_void_p), ("weight", C.c_void_p), ("is_inhibitory", C.c_void_p),
                 ("tau_E", C.c_float), ("tau_I", C.c_float), ("E_E", C.c_float),
@@ -236,7 +238,8 @@ class Network:
 
     def __init__(self, V0, dt, *, I_const=None, model_id=None, csr=None, inh=None, syn=None,
                  delay_steps=1, bg=None, seed=0, theta=0.0, precision=HH_PREC_FAST,
-                 v_update=HH_V_EXP_EULER, stream=None, n_nets=1, net_offsets=None):
+                 v_update=HH_V_EXP_EULER, stream=None, n_nets=1, net_offsets=None,
+                 kernels=HH_KERNELS_SPECIALISED):
         d = hh_net_desc()
         self._keep = []
         V0 = self._f32(V0)
@@ -251,6 +254,7 @@ class Network:
         d.v_threshold = theta
         d.v_update = v_update
         d.precision = precision
+        d.kernels = kernels
         d.V0 = _ptr(V0)
         if I_const is not None:
             I_const = self._f32(I_const)

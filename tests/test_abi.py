@@ -47,6 +47,7 @@ int main(void){
  printf("%zu %zu\\n", sizeof(hh_neurons_noalloc), offsetof(hh_neurons_noalloc, status));
  printf("%zu %zu %zu %zu %zu\\n", offsetof(hh_net_desc, dt_ms), offsetof(hh_net_desc, n_synapses),
    offsetof(hh_net_desc, seed), offsetof(hh_net_desc, stream), offsetof(hh_model_desc, ca_tau));
+ printf("%zu\\n", offsetof(hh_net_desc, V0));
  return 0; }
 """)
     exe = tmp_path / "probe"
@@ -59,7 +60,7 @@ int main(void){
             C.sizeof(hh.hh_spike), C.sizeof(hh.hh_neurons_noalloc),
             hh.hh_neurons_noalloc.status.offset, hh.hh_net_desc.dt_ms.offset, hh.hh_net_desc.n_synapses.offset,
             hh.hh_net_desc.seed.offset, hh.hh_net_desc.stream.offset,
-            hh.hh_model_desc.ca_tau.offset]
+            hh.hh_model_desc.ca_tau.offset, hh.hh_net_desc.V0.offset]
     assert got == want
 
 

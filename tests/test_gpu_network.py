@@ -20,10 +20,10 @@ def _torch():
 
 
 def make_net(g, dt=0.025, D=40, bg=None, seed=0, precision=hh.HH_PREC_FAST, models=(inp.CLASSIC_HH,),
-             model_id=None, I=None):
+             model_id=None, I=None, kernels=hh.HH_KERNELS_SPECIALISED):
     net = hh.Network(g["V0"], dt, csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
                      delay_steps=D, bg=bg, seed=seed, precision=precision, model_id=model_id,
-                     I_const=I)
+                     I_const=I, kernels=kernels)
     for k, m in enumerate(models):
         net.set_channels(k, m)
     return net
@@ -108,8 +108,11 @@ def test_background_counts_bit_exact():
     net.close()
 
 
-@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE, hh.HH_PREC_COMPENSATED])
-def test_closed_loop_small_network(prec):
+@pytest.mark.parametrize("prec,kernels", [(hh.HH_PREC_FAST, hh.HH_KERNELS_SPECIALISED),
+                                          (hh.HH_PREC_ACCURATE, hh.HH_KERNELS_SPECIALISED),
+                                          (hh.HH_PREC_COMPENSATED, hh.HH_KERNELS_SPECIALISED),
+                                          (hh.HH_PREC_FAST, hh.HH_KERNELS_TABLE)])
+def test_closed_loop_small_network(prec, kernels):
     """1,000 neurons, in-degree 100, background, 200 ms closed loop: every
     neuron's spike count within +-1 of the oracle, and the V traces agree to
     1e-2 mV for the first 10 ms (before FP32/FP64 chaos separates them)."""
@@ -119,7 +122,7 @@ def test_closed_loop_small_network(prec):
     T = 8000
     ref = oracle.simulate_network(inp.CLASSIC_HH, g, T, 0.025, 40, SYN, bg=bg, seed=9,
                                   trace_idx=np.arange(1000))
-    net = make_net(g, bg=bg, seed=9, precision=prec)
+    net = make_net(g, bg=bg, seed=9, precision=prec, kernels=kernels)
     rec, b = hh.make_record(1000, T, trace=1000, spike_cap=1_000_000)
     net.step(T, rec=rec)
     torch.cuda.synchronize()

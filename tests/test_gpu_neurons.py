@@ -20,10 +20,10 @@ def _torch():
 
 
 def run_gpu(model, I, V0, T, dt, precision, gbar=None, trace=True, spike_cap=None, v_update=0,
-            I_steps=None, chunks=None):
+            I_steps=None, chunks=None, kernels=hh.HH_KERNELS_SPECIALISED):
     torch = _torch()
     N = len(V0)
-    net = hh.Network(V0, dt, I_const=I, precision=precision, v_update=v_update)
+    net = hh.Network(V0, dt, I_const=I, precision=precision, v_update=v_update, kernels=kernels)
     net.set_channels(0, model, gbar=gbar)
     cap = spike_cap if spike_cap is not None else 400 * N
     rec, b = hh.make_record(N, T, trace=N if trace else 0, spike_cap=cap)
@@ -79,13 +79,15 @@ def classic_1024():
     return x, T, dt, ref, ill
 
 
-def test_classic_population_compensated(classic_1024):
+@pytest.mark.parametrize("kernels", [hh.HH_KERNELS_SPECIALISED, hh.HH_KERNELS_TABLE])
+def test_classic_population_compensated(classic_1024, kernels):
     """Config 1 (1,024 neurons, I ~ U(0,20), dt 0.01 ms, 100 ms) in
     compensated FP32: max |dV| <= 1e-2 mV for every well-conditioned neuron,
-    identical spike counts and spike times within 0.05 ms for all neurons."""
+    identical spike counts and spike times within 0.05 ms for all neurons,
+    with the run-time specialised and the table-driven kernels."""
     x, T, dt, ref, ill = classic_1024
     assert ill.mean() < 0.03
-    g = run_gpu(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, hh.HH_PREC_COMPENSATED)
+    g = run_gpu(inp.CLASSIC_HH, x["I"], x["V0"], T, dt, hh.HH_PREC_COMPENSATED, kernels=kernels)
     assert g["status"] == 0
     dV = np.abs(g["V"] - ref["V"]).max(0)
     assert dV[~ill].max() <= V_TOL_MV, (dV[~ill].max(), np.argmax(np.where(ill, 0, dV)))
@@ -206,6 +208,21 @@ def test_multichannel_full_size_sampled():
     d = np.abs(counts[idx] - ref["counts"])
     assert d.max() <= 1
     assert (d == 0).mean() >= 0.95
+
+
+@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE])
+def test_specialised_matches_table_kernels(prec):
+    """The NVRTC-specialised kernels and the table interpreter run the same
+    device code: identical spike counts and V within 1e-3 mV over 100 ms of
+    multi-channel neurons (instruction selection may differ in FMA use)."""
+    y = inp.multi_channel_neurons(300, seed=4)
+    T, dt = 4000, 0.025
+    a = run_gpu(inp.MULTI_CHANNEL, y["I"], y["V0"], T, dt, prec, gbar=y["gbar"],
+                kernels=hh.HH_KERNELS_SPECIALISED)
+    b = run_gpu(inp.MULTI_CHANNEL, y["I"], y["V0"], T, dt, prec, gbar=y["gbar"],
+                kernels=hh.HH_KERNELS_TABLE)
+    assert np.array_equal(a["counts"], b["counts"])
+    assert np.abs(a["V"][:1000] - b["V"][:1000]).max() < 1e-3
 
 
 def test_bad_model_rejected():
