@@ -277,6 +277,27 @@ hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* s
                           int64_t n_spk, int32_t n_window, int64_t* sum_E, int64_t* sum_I);
 
 /* ------------------------------------------------------------------ */
+/* Dense projections on the tensor cores                                */
+/* ------------------------------------------------------------------ */
+
+/* C[s][m][n] = sum over the K range of split s of A[m][k] * Bt[n][k]
+ * The BF16 x BF16 -> FP32 product on the tcgen05 tensor cores that the
+ * differentiable layer uses for its input and recurrent projections and
+ * their weight gradients (the input current of an HH layer is produced by
+ * the previous layer's weights, Methods "Analysis of C_m").
+ *   A : device bf16 [M][lda], row-major (K contiguous), lda >= K, lda % 8 == 0
+ *   Bt: device bf16 [N][ldb], row-major (K contiguous: the transpose of the
+ *       K x N matrix B), ldb >= K, ldb % 8 == 0
+ *   C : device fp32 [splits][M][N]; split s holds the partial product over
+ *       K blocks [s*P, (s+1)*P) of 64, P = ceil(ceil(K/64)/splits); the
+ *       caller sums the splits (splits = 1 gives C = A B)
+ *   N % 32 == 0; A, Bt, C 16-byte aligned; status: device int32 that bounded
+ *       device waits OR a nonzero code into on failure (caller zeroes it).
+ * Asynchronous on `stream`.  Errors: HH_EINVAL, HH_ECUDA. */
+hh_status hh_gemm_bf16(const void* A, int32_t lda, const void* Bt, int32_t ldb, float* C, int32_t M,
+                       int32_t N, int32_t K, int32_t splits, int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Readout                                                              */
 /* ------------------------------------------------------------------ */
 

@@ -841,6 +841,29 @@ hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap, size_t* n
     return HH_OK;
 }
 
+hh_status hh_gemm_bf16(const void* A, int32_t lda, const void* Bt, int32_t ldb, float* C, int32_t M,
+                       int32_t N, int32_t K, int32_t splits, int32_t* status, void* stream)
+{
+    if (!A || !Bt || !C || !status)
+        return fail(HH_EINVAL, "A, Bt, C and status must not be NULL");
+    hh::GemmArgs g{};
+    g.A = A;
+    g.a_rows = M;
+    g.lda = lda;
+    g.Bt = Bt;
+    g.b_rows = N;
+    g.ldb = ldb;
+    g.C = C;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.splits = splits;
+    if (const char* why = hh::gemm_check(g))
+        return fail(HH_EINVAL, "%s", why);
+    HH_CUDA(hh::launch_gemm_bf16(g, status, (cudaStream_t)stream));
+    return HH_OK;
+}
+
 hh_status hh_profile(hh_net* net, int32_t enable)
 {
     if (!net)

@@ -53,6 +53,20 @@ cudaError_t launch_fill_gbar(const DevModels& M, int64_t N, const uint8_t* model
 cudaError_t launch_trace_slots(const int32_t* trace_idx, int32_t n_trace, int64_t N,
                                int32_t* slot, cudaStream_t st);
 
+// BF16 GEMM on tcgen05 (hh_gemm.cu): C[s][m][n] = sum_{k in split s}
+// A[a_row0+m][k] Bt[b_row0+n][k]; A, Bt K-major bf16 with leading dimensions
+// lda, ldb (elements, multiples of 8); C fp32 [splits][M][N].
+struct GemmArgs {
+    const void* A;
+    int a_rows, lda, a_row0;
+    const void* Bt;
+    int b_rows, ldb, b_row0;
+    float* C;
+    int M, N, K, splits;
+};
+const char* gemm_check(const GemmArgs& g);
+cudaError_t launch_gemm_bf16(const GemmArgs& g, int32_t* err, cudaStream_t st);
+
 // Neuron kernels specialised for a model set, compiled with NVRTC (hh_jit.cu).
 struct JitKernels {
     cudaKernel_t independent = nullptr;

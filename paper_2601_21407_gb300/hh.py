@@ -99,8 +99,8 @@ class hh_record(C.Structure):
 
 
 EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_route_spikes",
-           "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_destroy", "hh_last_error",
-           "hh_version"]
+           "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
+           "hh_last_error", "hh_version"]
 
 
 def lib_path() -> str:
@@ -134,6 +134,9 @@ def lib():
             L.hh_step_neurons_noalloc.restype = C.c_int
             L.hh_step_neurons_noalloc.argtypes = [P(hh_model_desc), P(hh_neurons_noalloc), C.c_int64,
                                                   C.c_int32, vp, P(hh_record)]
+            L.hh_gemm_bf16.restype = C.c_int
+            L.hh_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_int32, vp, vp]
             L.hh_destroy.restype = None
             L.hh_destroy.argtypes = [vp]
             L.hh_last_error.restype = C.c_char_p
@@ -188,6 +191,15 @@ def hh_step_neurons_noalloc(model: hh_model_desc, state: hh_neurons_noalloc, t0:
                             I_steps_ptr=None, rec: hh_record | None = None):
     _check(lib().hh_step_neurons_noalloc(C.byref(model), C.byref(state), t0, n_steps, I_steps_ptr,
                                          C.byref(rec) if rec is not None else None))
+
+
+def hh_gemm_bf16(A, Bt, C, M, N, K, splits=1, status=None, stream=None):
+    """C[splits][M][N] (fp32) = A[M][K] (bf16) x B (bf16 given as Bt[N][K]);
+    torch device tensors."""
+    lda = A.stride(0)
+    ldb = Bt.stride(0)
+    _check(lib().hh_gemm_bf16(A.data_ptr(), lda, Bt.data_ptr(), ldb, C.data_ptr(), M, N, K, splits,
+                              status.data_ptr(), stream))
 
 
 def hh_destroy(net: int):

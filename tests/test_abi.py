@@ -18,7 +18,7 @@ HEADER = os.path.join(ROOT, "include", "hh.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hh_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(hh_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol():
