@@ -298,6 +298,80 @@ hh_status hh_gemm_bf16(const void* A, int32_t lda, const void* Bt, int32_t ldb, 
                        int32_t N, int32_t K, int32_t splits, int32_t* status, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Differentiable recurrent HH layer (BPTT)                             */
+/* ------------------------------------------------------------------ */
+
+/* A recurrent layer of n_hidden HH point neurons trained by
+ * back-propagation through time (Methods, "Gradient learning support":
+ * gradients of the discretised state update derived by hand; "Engineering
+ * optimization": re-computation).  Per outer step t (substeps x dt_ms):
+ *   I_t = bias + X_t W_in + S_{t-1} W_rec     (bf16 tensor-core products,
+ *                                               fp32 accumulation)
+ *   K = substeps exponential-Euler steps with I_t held;
+ *   S_t = sum_k H(V_k - theta)(1 - H(V_{k-1} - theta))  (smooth = 0), or
+ *         the same with H replaced by 0.5 + 0.5 b x/(1 + b|x|) (smooth = 1)
+ *   r = mean_t S_t,  logits = r W_out^T,  loss = mean_b CE(logits_b, y_b).
+ * The backward pass replaces dH/dx by 1/(1 + b|x|)^2 (b = surrogate_beta)
+ * and treats the (1 - H(V_{k-1} - theta)) factor as a constant.  W_in and
+ * W_rec are rounded to bf16 when set; S is rounded to bf16 for the
+ * recurrent product (exact for 0/1 spikes).  Neurons start at v_init with
+ * gates at steady state; checkpoints every checkpoint_every outer steps. */
+typedef struct hh_layer hh_layer;
+
+typedef struct {
+    int32_t batch;            /* B >= 1                                       */
+    int32_t n_in;             /* input channels                               */
+    int32_t n_hidden;         /* N, a multiple of 32                          */
+    int32_t n_out;            /* classes                                      */
+    int32_t n_steps;          /* T outer steps                                */
+    int32_t substeps;         /* K in 1..16                                   */
+    double dt_ms;             /* substep                                      */
+    float v_threshold, v_init, surrogate_beta;
+    int32_t precision;        /* HH_PREC_FAST or HH_PREC_ACCURATE            */
+    int32_t smooth;           /* 0 Heaviside + surrogate, 1 smooth spikes     */
+    int32_t checkpoint_every; /* outer steps between state checkpoints        */
+    void* stream;
+} hh_layer_desc;
+
+typedef struct {
+    float* dW_in;   /* device [n_in][N]   */
+    float* dW_rec;  /* device [N][N]      */
+    float* dW_out;  /* device [n_out][N]  */
+    float* dbias;   /* device [N]         */
+} hh_grads;
+
+enum { HH_LAYER_SPIKES = 0, /* float [T][B][N] spikes of the last forward  */
+       HH_LAYER_V = 1,      /* float [B][N] V after the last forward       */
+       HH_LAYER_STATUS = 2  /* int32: nonzero if a bounded device wait failed */ };
+
+/* Create a layer for one model (alpha/beta or inf/tau gates, no calcium pool)
+ * and allocate every buffer it needs.  Synchronous.  Errors: HH_EINVAL,
+ * HH_EUNSUPPORTED (model or precision), HH_ENOMEM, HH_ECUDA. */
+hh_status hh_layer_create(const hh_layer_desc* d, const hh_model_desc* model, hh_layer** out);
+
+/* W_in [n_in][N], W_rec [N][N], W_out [n_out][N], bias [N]: fp32, any memory
+ * (copied; W_in and W_rec rounded to bf16).  Synchronous. */
+hh_status hh_layer_set_weights(hh_layer* layer, const float* W_in, const float* W_rec,
+                               const float* W_out, const float* bias);
+
+/* Forward pass.  X: device fp32 [T][B][n_in] (0/1 spike inputs); labels:
+ * device int32 [B]; loss: device fp32 [1]; logits: device [B][n_out] or
+ * NULL.  Asynchronous.  Errors: HH_EINVAL, HH_ECUDA. */
+hh_status hh_layer_forward(hh_layer* layer, const float* X, const int32_t* labels, float* loss,
+                           float* logits);
+
+/* Backward pass of the last forward: fills the caller's device gradient
+ * buffers (overwritten, not accumulated).  Asynchronous.  Errors: HH_EINVAL,
+ * HH_ESTATE (no forward yet), HH_ECUDA. */
+hh_status hh_backward(hh_layer* layer, const hh_grads* g);
+
+/* Copy HH_LAYER_* into dst (any memory); synchronous. */
+hh_status hh_layer_readout(hh_layer* layer, int32_t what, void* dst, size_t cap_bytes,
+                           size_t* n_bytes);
+
+void hh_layer_destroy(hh_layer* layer);
+
+/* ------------------------------------------------------------------ */
 /* Readout                                                              */
 /* ------------------------------------------------------------------ */
 

@@ -11,12 +11,13 @@
 #include "hh_internal.h"
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
+namespace hh {
 hh_status fail(hh_status s, const char* fmt, ...)
 {
-    char buf[512];
+    char buf[2048];
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
@@ -24,6 +25,10 @@ hh_status fail(hh_status s, const char* fmt, ...)
     g_err = buf;
     return s;
 }
+}  // namespace hh
+
+namespace {
+using hh::fail;
 
 #define HH_CUDA(call)                                                                   \
     do {                                                                                \
@@ -258,6 +263,9 @@ hh::DevFn prep_fn(const hh_fn& f)
     return d;
 }
 
+}  // namespace
+
+namespace hh {
 hh_status prep_model(const hh_model_desc* m, double dt, hh::DevModel* out)
 {
     if (!(m->C_m > 0.0f) || !finite_f(m->C_m))
@@ -331,6 +339,10 @@ hh_status prep_model(const hh_model_desc* m, double dt, hh::DevModel* out)
     *out = d;
     return HH_OK;
 }
+}  // namespace hh
+
+namespace {
+using hh::prep_model;
 
 template <class T>
 cudaError_t copy_in(T* dst, const T* src, size_t count, cudaStream_t st)

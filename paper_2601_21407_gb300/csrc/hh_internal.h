@@ -26,6 +26,11 @@ struct RouteParams {
     int32_t n_window;
 };
 
+// error reporting into the thread-local hh_last_error() message (hh_abi.cu)
+hh_status fail(hh_status s, const char* fmt, ...);
+// validate a user model and prepare it for the device (hh_abi.cu)
+hh_status prep_model(const hh_model_desc* m, double dt, DevModel* out);
+
 // launchers (hh_kernels.cu); all asynchronous on `st`
 cudaError_t launch_init_state(const DevModels& M, const NeuronParams& P, const float* V0,
                               int32_t model_index, int precision, cudaStream_t st);

@@ -1,0 +1,949 @@
+// Differentiable recurrent HH layer: forward over T outer steps of K
+// exponential-Euler substeps, and a hand-derived BPTT adjoint with
+// recomputation from checkpoints (Methods, "Gradient learning support" and
+// "Engineering optimization": manually derived gradients, re-computation).
+//
+//   I_t = bias + X_t W_in + S_{t-1} W_rec           (tcgen05 GEMMs, bf16 in, fp32 acc)
+//   K substeps of the neuron update with I_t held; S_t = sum_k c_{t,k},
+//   c_{t,k} = H(V_k - theta)(1 - H(V_{k-1} - theta))   (or the smooth step)
+//   r = (1/T) sum_t S_t,  logits = r W_out^T,  loss = mean_b CE(logits_b, y_b)
+// Backward: dlogits = (softmax - onehot)/B; dS_t = dr/T + dI_{t+1} W_rec^T;
+// through each substep in reverse with the surrogate 1/(1 + beta|x|)^2 for
+// dH/dx; dW_in = X^T dI, dW_rec = S_prev^T dI, dbias = sum dI (GEMMs over the
+// T*B rows, dI split into bf16 hi + lo parts so the products keep ~16 bits).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <vector>
+
+#include "hh_internal.h"
+
+namespace hh {
+namespace {
+
+constexpr int kMaxSub = 16;
+
+__device__ __forceinline__ float sur_d(float x, float beta)
+{
+    const float d = 1.0f + beta * fabsf(x);
+    return 1.0f / (d * d);
+}
+__device__ __forceinline__ float smooth_s(float x, float beta)
+{
+    return 0.5f + 0.5f * beta * x / (1.0f + beta * fabsf(x));
+}
+__device__ __forceinline__ float smooth_d(float x, float beta)
+{
+    const float d = 1.0f + beta * fabsf(x);
+    return 0.5f * beta / (d * d);
+}
+
+// value (without the offset c) and derivative d/dV of a rate form, accurate FP32
+__device__ __forceinline__ void rate_vd(const DevFn& f, float V, float& r, float& dr)
+{
+    switch (f.form) {
+    case HH_FN_CONST:
+        r = f.a;
+        dr = 0.0f;
+        break;
+    case HH_FN_EXP: {
+        const float e = expf((V - f.vh) * f.ik);
+        r = f.a * e;
+        dr = r * f.ik;
+        break;
+    }
+    case HH_FN_SIGMOID: {
+        const float e = expf((V - f.vh) * f.ik);
+        const float q = 1.0f / (1.0f + e);
+        r = f.a * q;
+        dr = -f.a * e * q * q * f.ik;
+        break;
+    }
+    case HH_FN_LINOID: {
+        // a k g(y), g(y) = y / (1 - e^{-y}), y = (V - vh)/k; dr = a g'(y)
+        const float y = (V - f.vh) * f.ik;
+        if (fabsf(y) < 1e-3f) {
+            r = f.a * f.k * (1.0f + 0.5f * y + y * y * (1.0f / 12.0f));
+            dr = f.a * (0.5f + y * (1.0f / 6.0f));
+        } else {
+            const float em = -expm1f(-y);  // 1 - e^{-y}
+            const float g = y / em;
+            r = f.a * f.k * g;
+            dr = f.a * (em - y * (1.0f - em)) / (em * em);
+        }
+        break;
+    }
+    default: {  // bell
+        const float e1 = expf((V - f.vh) * f.ik), e2 = expf((V - f.vh2) * f.ik2);
+        const float den = e1 + e2;
+        r = f.a / den;
+        dr = -f.a * (e1 * f.ik + e2 * f.ik2) / (den * den);
+        break;
+    }
+    }
+    r += f.c;
+}
+
+// Reverse of one substep (state V, p before it, current I): on entry lamV,
+// lamP hold the adjoints of the state after the substep; on exit those of
+// the state before it; lamI accumulates dL/dI.
+template <int MAXG>
+__device__ __forceinline__ void substep_adjoint(const DevModel& M, const State<MAXG, 1>& s0, float dt, float I,
+                                                float& lamV, float* lamP, float& lamI)
+{
+    const float V = s0.V;
+    float pn[MAXG], Eq[MAXG], dpdV[MAXG];
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q) {
+        pn[q] = 0.0f;
+        Eq[q] = 0.0f;
+        dpdV[q] = 0.0f;
+        if (q < M.n_gates) {
+            const DevGate& g = M.g[q];
+            const float p = s0.p[q];
+            float inf, dinf, z, dz;
+            if (g.kind == HH_GATE_AB) {
+                float al, dal, be, dbe;
+                rate_vd(g.f1, V, al, dal);
+                rate_vd(g.f2, V, be, dbe);
+                const float sum = al + be;
+                inf = al / sum;
+                dinf = (dal * be - al * dbe) / (sum * sum);
+                z = dt * sum;
+                dz = dt * (dal + dbe);
+            } else {
+                float tau, dtau;
+                rate_vd(g.f1, V, inf, dinf);
+                rate_vd(g.f2, V, tau, dtau);
+                z = dt / tau;
+                dz = -dt * dtau / (tau * tau);
+            }
+            const float E = -expm1f(-z);
+            Eq[q] = E;
+            pn[q] = p + (inf - p) * E;
+            dpdV[q] = E * dinf + (inf - p) * (1.0f - E) * dz;
+        }
+    }
+    float G = s0.gconst, Ip = s0.gconst * V - s0.gconstE;
+    {
+        float eta = 1.0f;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            if (q < M.n_gates) {
+                eta *= powi(pn[q], M.g[q].power);
+                if (M.gate_last[q]) {
+                    const float gx = s0.gq[q] * eta;
+                    G += gx;
+                    Ip += gx * (V - M.gate_E[q]);
+                    eta = 1.0f;
+                }
+            }
+    }
+    const float EV = -expm1f(-dt * G * M.inv_C);
+    const float A = (I - Ip) / G;
+    lamI += lamV * EV / G;
+    float lamVpre = lamV * (1.0f - EV);
+    float lamPn[MAXG];
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q)
+        lamPn[q] = lamP[q];
+    // conductance paths: dV'/dg_c = -EV ((V - E_c) + A)/G + A (1 - EV) dt/C
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q) {
+        if (q < M.n_gates && M.gate_last[q]) {
+            const int c = M.gate_ch[q];
+            const int f = M.ch_first[c], ng = M.ch_ng[c];
+            const float dVdg = -EV * ((V - M.gate_E[q]) + A) / G + A * (1.0f - EV) * dt * M.inv_C;
+            const float lg = lamV * dVdg * s0.gq[q];
+#pragma unroll
+            for (int r = 0; r < MAXG; ++r) {
+                if (r >= f && r < f + ng) {
+                    float d = (float)M.g[r].power * powi(pn[r], M.g[r].power - 1 > 0 ? M.g[r].power - 1 : 1);
+                    if (M.g[r].power == 1)
+                        d = 1.0f;
+#pragma unroll
+                    for (int u = 0; u < MAXG; ++u)
+                        if (u >= f && u < f + ng && u != r)
+                            d *= powi(pn[u], M.g[u].power);
+                    lamPn[r] += lg * d;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q) {
+        if (q < M.n_gates) {
+            lamVpre += lamPn[q] * dpdV[q];
+            lamP[q] = lamPn[q] * (1.0f - Eq[q]);
+        }
+    }
+    lamV = lamVpre;
+}
+
+struct LayerParams {
+    int64_t BN;          // B * N
+    int32_t B, N, T, K, ckpt;
+    float dt, theta, beta;
+    int32_t v_update, smooth;
+    const float* bias;   // [N]
+    const float* XW;     // [T*B][N]
+    const float* recp;   // [splits][B][N] or null
+    int32_t rec_splits;
+    float* I_all;        // [T][B][N]
+    float* V;            // [B*N]
+    float* P;            // [kMaxGates][B*N]
+    float* ckptV;        // [n_ckpt][B*N]
+    float* ckptP;        // [n_ckpt][kMaxGates][B*N]
+    uint16_t* S;         // bf16 [(T+1)*B][N]; rows [0,B) zero
+    float* Sf;           // fp32 [T][B*N] spikes (for readout / records)
+    float* acc;          // [B*N]
+    float* segV;         // [ckpt][B*N]
+    float* segP;         // [ckpt][kMaxGates][B*N]
+    float* lamV;         // [B*N]
+    float* lamP;         // [kMaxGates][B*N]
+    const float* ds_direct;  // [B*N]
+    const float* dsp;    // [splits][B*N] partials of dI_{t+1} W_rec^T
+    int32_t ds_splits;
+    float* dI_all;       // [T][B*N]
+    uint16_t* dIb;       // bf16 [B][2N]  (hi | lo) of dI_t
+};
+
+__device__ __forceinline__ uint16_t f2bf(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(r >> 16);
+}
+__device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+template <int MAXG, int PREC>
+__device__ __forceinline__ void layer_load(const DevModel& M, const LayerParams& L, const float* V, const float* P,
+                                           int64_t i, State<MAXG, PREC>& s)
+{
+    s.V = V[i];
+    s.Vlo = 0.0f;
+    s.Ca = 0.0f;
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q) {
+        s.p[q] = P[(int64_t)q * L.BN + i];
+        s.plo[q] = 0.0f;
+    }
+    load_conductances(M, nullptr, L.BN, i, s);
+}
+
+template <int MAXG, int PREC>
+__global__ void __launch_bounds__(128) k_layer_fwd(const __grid_constant__ DevModels Ms,
+                                                   const __grid_constant__ LayerParams L, int t)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.BN)
+        return;
+    const DevModel& M = Ms.m[0];
+    const int n = (int)(i % L.N), b = (int)(i / L.N);
+    float I = L.bias[n] + L.XW[((int64_t)t * L.B + b) * L.N + n];
+    if (L.recp)
+        for (int s = 0; s < L.rec_splits; ++s)
+            I += L.recp[(int64_t)s * L.BN + i];
+    L.I_all[(int64_t)t * L.BN + i] = I;
+    State<MAXG, PREC> st;
+    layer_load(M, L, L.V, L.P, i, st);
+    float spk = 0.0f;
+    for (int k = 0; k < L.K; ++k) {
+        const float Vp = st.V;
+        neuron_step<MAXG, PREC>(M, L.dt, L.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, st);
+        if (L.smooth)
+            spk += smooth_s(st.V - L.theta, L.beta) * (1.0f - smooth_s(Vp - L.theta, L.beta));
+        else
+            spk += (st.V >= L.theta && !(Vp >= L.theta)) ? 1.0f : 0.0f;
+    }
+    L.V[i] = st.V;
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q)
+        L.P[(int64_t)q * L.BN + i] = st.p[q];
+    L.S[(int64_t)(t + 1) * L.BN + i] = f2bf(spk);
+    L.Sf[(int64_t)t * L.BN + i] = spk;
+    L.acc[i] += spk;
+    if ((t + 1) % L.ckpt == 0) {
+        const int c = (t + 1) / L.ckpt;
+        L.ckptV[(int64_t)c * L.BN + i] = st.V;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            L.ckptP[((int64_t)c * kMaxGates + q) * L.BN + i] = st.p[q];
+    }
+}
+
+// Recompute the states at the start of every outer step of segment g.
+template <int MAXG, int PREC>
+__global__ void __launch_bounds__(128) k_layer_recompute(const __grid_constant__ DevModels Ms,
+                                                         const __grid_constant__ LayerParams L, int g)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.BN)
+        return;
+    const DevModel& M = Ms.m[0];
+    State<MAXG, PREC> st;
+    layer_load(M, L, L.ckptV + (int64_t)g * L.BN, L.ckptP + (int64_t)g * kMaxGates * L.BN, i, st);
+    const int t0 = g * L.ckpt, t1 = min(L.T, t0 + L.ckpt);
+    for (int t = t0; t < t1; ++t) {
+        const int j = t - t0;
+        L.segV[(int64_t)j * L.BN + i] = st.V;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            L.segP[((int64_t)j * kMaxGates + q) * L.BN + i] = st.p[q];
+        const float I = L.I_all[(int64_t)t * L.BN + i];
+        for (int k = 0; k < L.K; ++k)
+            neuron_step<MAXG, PREC>(M, L.dt, L.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, st);
+    }
+}
+
+// Reverse of outer step t: recompute its K substeps from the segment state,
+// then sweep them backwards.
+template <int MAXG, int PREC>
+__global__ void __launch_bounds__(128) k_layer_bwd(const __grid_constant__ DevModels Ms,
+                                                   const __grid_constant__ LayerParams L, int t)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.BN)
+        return;
+    const DevModel& M = Ms.m[0];
+    const int j = t % L.ckpt;
+    State<MAXG, PREC> st;
+    layer_load(M, L, L.segV + (int64_t)j * L.BN, L.segP + (int64_t)j * kMaxGates * L.BN, i, st);
+    const float I = L.I_all[(int64_t)t * L.BN + i];
+    // states before each substep (V_0..V_{K-1}) and V_K
+    float Vs[kMaxSub + 1];
+    float Ps[kMaxSub][MAXG];
+    for (int k = 0; k < L.K; ++k) {
+        Vs[k] = st.V;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            Ps[k][q] = st.p[q];
+        neuron_step<MAXG, PREC>(M, L.dt, L.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, st);
+    }
+    Vs[L.K] = st.V;
+    float ds = L.ds_direct[i];
+    if (L.dsp)
+        for (int s = 0; s < L.ds_splits; ++s)
+            ds += L.dsp[(int64_t)s * L.BN + i];
+    float lamV = L.lamV[i];
+    float lamP[MAXG];
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q)
+        lamP[q] = L.lamP[(int64_t)q * L.BN + i];
+    float lamI = 0.0f;
+    State<MAXG, 1> s0;
+    s0.Ca = 0.0f;
+    s0.Vlo = 0.0f;
+    load_conductances(M, nullptr, L.BN, i, s0);
+    for (int k = L.K; k >= 1; --k) {
+        const float Vk = Vs[k], Vp = Vs[k - 1];
+        // spike c_k depends on V_k (and on V_{k-1})
+        if (L.smooth)
+            lamV += ds * smooth_d(Vk - L.theta, L.beta) * (1.0f - smooth_s(Vp - L.theta, L.beta));
+        else if (!(Vp >= L.theta))
+            lamV += ds * sur_d(Vk - L.theta, L.beta);
+        s0.V = Vp;
+#pragma unroll
+        for (int q = 0; q < MAXG; ++q)
+            s0.p[q] = Ps[k - 1][q];
+        substep_adjoint<MAXG>(M, s0, L.dt, I, lamV, lamP, lamI);
+        if (L.smooth)
+            lamV -= ds * smooth_s(Vk - L.theta, L.beta) * smooth_d(Vp - L.theta, L.beta);
+    }
+    L.lamV[i] = lamV;
+#pragma unroll
+    for (int q = 0; q < MAXG; ++q)
+        L.lamP[(int64_t)q * L.BN + i] = lamP[q];
+    L.dI_all[(int64_t)t * L.BN + i] = lamI;
+    const int n = (int)(i % L.N), b = (int)(i / L.N);
+    const uint16_t hi = f2bf(lamI);
+    L.dIb[(int64_t)b * 2 * L.N + n] = hi;
+    L.dIb[(int64_t)b * 2 * L.N + L.N + n] = f2bf(lamI - bf2f(hi));
+}
+
+// logits, loss (mean CE) and dlogits; one block per sample.
+__global__ void k_layer_readout(const float* __restrict__ acc, const float* __restrict__ W_out,
+                                const int32_t* __restrict__ labels, int N, int n_out, float inv_T, int B,
+                                float* logits, float* loss_b, float* dlogits)
+{
+    extern __shared__ float sh[];  // n_out
+    const int b = blockIdx.x;
+    for (int o = threadIdx.x >> 5; o < n_out; o += blockDim.x >> 5) {
+        float s = 0.0f;
+        for (int n = threadIdx.x & 31; n < N; n += 32)
+            s += acc[(int64_t)b * N + n] * inv_T * W_out[(int64_t)o * N + n];
+        for (int off = 16; off; off >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0)
+            sh[o] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mx = -INFINITY;
+        for (int o = 0; o < n_out; ++o)
+            mx = fmaxf(mx, sh[o]);
+        double z = 0.0;
+        for (int o = 0; o < n_out; ++o)
+            z += exp((double)(sh[o] - mx));
+        const int y = labels[b];
+        loss_b[b] = (float)(log(z) - (double)(sh[y] - mx));
+        for (int o = 0; o < n_out; ++o) {
+            if (logits)
+                logits[(int64_t)b * n_out + o] = sh[o];
+            const float p = (float)(exp((double)(sh[o] - mx)) / z);
+            dlogits[(int64_t)b * n_out + o] = (p - (o == y ? 1.0f : 0.0f)) / (float)B;
+        }
+    }
+}
+
+__global__ void k_layer_loss(const float* __restrict__ loss_b, int B, float* loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < B; ++b)
+            s += loss_b[b];
+        *loss = (float)(s / B);
+    }
+}
+
+// dW_out[o][n] = sum_b dlogits[b][o] r[b][n];  ds_direct[b][n] = (1/T) sum_o dlogits[b][o] W_out[o][n]
+__global__ void k_layer_bwd_readout(const float* __restrict__ acc, const float* __restrict__ W_out,
+                                    const float* __restrict__ dlogits, int B, int N, int n_out, float inv_T,
+                                    float* dW_out, float* ds_direct)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int64_t)n_out * N) {
+        const int o = (int)(i / N), n = (int)(i % N);
+        float s = 0.0f;
+        for (int b = 0; b < B; ++b)
+            s += dlogits[(int64_t)b * n_out + o] * acc[(int64_t)b * N + n] * inv_T;
+        dW_out[i] = s;
+    }
+    if (i < (int64_t)B * N) {
+        const int b = (int)(i / N), n = (int)(i % N);
+        float s = 0.0f;
+        for (int o = 0; o < n_out; ++o)
+            s += dlogits[(int64_t)b * n_out + o] * W_out[(int64_t)o * N + n];
+        ds_direct[i] = s * inv_T;
+    }
+}
+
+// X (fp32 0/1, [rows][n_in]) -> bf16 [rows][ld] with zero padding
+__global__ void k_to_bf16_pad(const float* __restrict__ X, int64_t rows, int cols, int ld, uint16_t* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * ld)
+        return;
+    const int64_t r = i / ld;
+    const int c = (int)(i % ld);
+    out[i] = c < cols ? f2bf(X[r * cols + c]) : (uint16_t)0;
+}
+
+// out[c][r] = in[r][c] for r < rows, c < cols; out has leading dimension ldo
+// (entries r >= rows of out are left untouched).  32x32 tiles via shared memory.
+template <class Tin>
+__global__ void k_transpose_bf16(const Tin* __restrict__ in, int64_t rows, int cols, int ldi, uint16_t* out,
+                                 int64_t ldo, uint16_t* out_lo)
+{
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k, c = c0 + threadIdx.x;
+        float v = 0.0f;
+        if (r < rows && c < cols) {
+            if constexpr (sizeof(Tin) == 2)
+                v = bf2f(in[r * ldi + c]);
+            else
+                v = in[r * ldi + c];
+        }
+        tile[k][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) {
+            const float v = tile[threadIdx.x][k];
+            const uint16_t hi = f2bf(v);
+            out[c * ldo + r] = hi;
+            if (out_lo)
+                out_lo[c * ldo + r] = f2bf(v - bf2f(hi));
+        }
+    }
+}
+
+// dst[r][c] = sum_s part[s][c][r]  (transpose back while summing split partials)
+__global__ void k_reduce_transpose(const float* __restrict__ part, int splits, int prow, int pcol, int rows,
+                                   int cols, float* dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * cols)
+        return;
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k)
+        s += part[((int64_t)k * prow + c) * pcol + r];
+    dst[i] = s;
+}
+
+// dbias[n] = sum_{t,b} dI[t][b][n]
+__global__ void k_colsum(const float* __restrict__ dI, int64_t rows, int N, float* out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N)
+        return;
+    float s = 0.0f;
+    for (int64_t r = 0; r < rows; ++r)
+        s += dI[r * N + n];
+    out[n] = s;
+}
+
+__global__ void k_layer_init(const __grid_constant__ DevModels Ms, const __grid_constant__ LayerParams L, float V0)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.BN)
+        return;
+    const DevModel& M = Ms.m[0];
+    L.V[i] = V0;
+    L.ckptV[i] = V0;
+    for (int q = 0; q < kMaxGates; ++q) {
+        float inf = 0.0f, z;
+        if (q < M.n_gates)
+            gate_inf_z<false>(M.g[q], V0, 0.0f, 1.0f, inf, z);
+        L.P[(int64_t)q * L.BN + i] = inf;
+        L.ckptP[(int64_t)q * L.BN + i] = inf;
+    }
+    L.acc[i] = 0.0f;
+    L.lamV[i] = 0.0f;
+    for (int q = 0; q < kMaxGates; ++q)
+        L.lamP[(int64_t)q * L.BN + i] = 0.0f;
+}
+
+int grid1(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace
+
+#define HH_LAYER_DISPATCH(MAXG_, PREC_, CALL)                                         \
+    do {                                                                              \
+        if ((MAXG_) <= 4) {                                                           \
+            if ((PREC_) == HH_PREC_FAST) { constexpr int G = 4, Q = HH_PREC_FAST; CALL; }      \
+            else { constexpr int G = 4, Q = HH_PREC_ACCURATE; CALL; }                 \
+        } else {                                                                      \
+            if ((PREC_) == HH_PREC_FAST) { constexpr int G = 8, Q = HH_PREC_FAST; CALL; }      \
+            else { constexpr int G = 8, Q = HH_PREC_ACCURATE; CALL; }                 \
+        }                                                                             \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+struct LayerImpl {
+    int B, n_in, n_in_pad, N, n_out, T, K, ckpt, n_ckpt, TB, TBp;
+    float dt, theta, beta, V0;
+    int precision, smooth;
+    cudaStream_t st;
+    DevModels models{};
+    // weights
+    float *W_out, *bias;
+    uint16_t *WinT, *WrecT, *Wrec2;   // [N][n_in_pad], [N][N], [N][2N]
+    // forward
+    uint16_t *Xb, *S;                 // [TB][n_in_pad], [(T+1)*B][N]
+    float *XW, *recp, *I_all, *Sf, *V, *P, *ckptV, *ckptP, *acc, *dlogits, *loss_b;
+    // backward
+    float *segV, *segP, *lamV, *lamP, *ds_direct, *dsp, *dI_all, *wpart;
+    uint16_t *dIb, *dIT_hi, *dIT_lo, *XT, *SpT;
+    int32_t* status;
+    int rec_splits, ds_splits, w_splits;
+    bool forward_done;
+};
+
+LayerParams layer_params(const LayerImpl& L)
+{
+    LayerParams p{};
+    p.BN = (int64_t)L.B * L.N;
+    p.B = L.B;
+    p.N = L.N;
+    p.T = L.T;
+    p.K = L.K;
+    p.ckpt = L.ckpt;
+    p.dt = L.dt;
+    p.theta = L.theta;
+    p.beta = L.beta;
+    p.v_update = HH_V_EXP_EULER;
+    p.smooth = L.smooth;
+    p.bias = L.bias;
+    p.XW = L.XW;
+    p.recp = nullptr;
+    p.rec_splits = L.rec_splits;
+    p.I_all = L.I_all;
+    p.V = L.V;
+    p.P = L.P;
+    p.ckptV = L.ckptV;
+    p.ckptP = L.ckptP;
+    p.S = L.S;
+    p.Sf = L.Sf;
+    p.acc = L.acc;
+    p.segV = L.segV;
+    p.segP = L.segP;
+    p.lamV = L.lamV;
+    p.lamP = L.lamP;
+    p.ds_direct = L.ds_direct;
+    p.dsp = nullptr;
+    p.ds_splits = L.ds_splits;
+    p.dI_all = L.dI_all;
+    p.dIb = L.dIb;
+    return p;
+}
+
+cudaError_t layer_forward(LayerImpl& L, const float* X, const int32_t* labels, float* loss, float* logits)
+{
+    cudaStream_t st = L.st;
+    cudaError_t e;
+    LayerParams p = layer_params(L);
+    const int64_t BN = p.BN;
+    // inputs -> bf16, input projection for all steps at once
+    k_to_bf16_pad<<<grid1((int64_t)L.TB * L.n_in_pad, 256), 256, 0, st>>>(X, L.TB, L.n_in, L.n_in_pad, L.Xb);
+    GemmArgs gx{L.Xb, L.TB, L.n_in_pad, 0, L.WinT, L.N, L.n_in_pad, 0, L.XW, L.TB, L.N, L.n_in_pad, 1};
+    if ((e = launch_gemm_bf16(gx, L.status, st)) != cudaSuccess)
+        return e;
+    k_layer_init<<<grid1(BN, 256), 256, 0, st>>>(L.models, p, L.V0);
+    if ((e = cudaMemsetAsync(L.S, 0, (size_t)L.B * L.N * 2, st)) != cudaSuccess)
+        return e;
+    const int mg = L.models.m[0].n_gates;
+    for (int t = 0; t < L.T; ++t) {
+        LayerParams pt = p;
+        if (t > 0) {
+            // recurrent projection S_{t-1} W_rec (S rows [t*B, (t+1)*B))
+            GemmArgs gr{L.S, (L.T + 1) * L.B, L.N, t * L.B, L.WrecT, L.N, L.N, 0, L.recp, L.B, L.N, L.N,
+                        L.rec_splits};
+            if ((e = launch_gemm_bf16(gr, L.status, st)) != cudaSuccess)
+                return e;
+            pt.recp = L.recp;
+        }
+        HH_LAYER_DISPATCH(mg, L.precision, (k_layer_fwd<G, Q><<<grid1(BN, 128), 128, 0, st>>>(L.models, pt, t)));
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
+    k_layer_readout<<<L.B, 256, L.n_out * sizeof(float), st>>>(L.acc, L.W_out, labels, L.N, L.n_out,
+                                                               1.0f / L.T, L.B, logits, L.loss_b, L.dlogits);
+    k_layer_loss<<<1, 32, 0, st>>>(L.loss_b, L.B, loss);
+    L.forward_done = true;
+    return cudaGetLastError();
+}
+
+cudaError_t layer_backward(LayerImpl& L, float* dW_in, float* dW_rec, float* dW_out, float* dbias)
+{
+    cudaStream_t st = L.st;
+    cudaError_t e;
+    LayerParams p = layer_params(L);
+    const int64_t BN = p.BN;
+    k_layer_bwd_readout<<<grid1(std::max<int64_t>(BN, (int64_t)L.n_out * L.N), 256), 256, 0, st>>>(
+        L.acc, L.W_out, L.dlogits, L.B, L.N, L.n_out, 1.0f / L.T, dW_out, L.ds_direct);
+    if ((e = cudaMemsetAsync(L.lamV, 0, BN * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(L.lamP, 0, BN * kMaxGates * sizeof(float), st)) != cudaSuccess)
+        return e;
+    const int mg = L.models.m[0].n_gates;
+    for (int g = L.n_ckpt - 1; g >= 0; --g) {
+        const int t0 = g * L.ckpt;
+        if (t0 >= L.T)
+            continue;
+        HH_LAYER_DISPATCH(mg, L.precision, (k_layer_recompute<G, Q><<<grid1(BN, 128), 128, 0, st>>>(L.models, p, g)));
+        const int t1 = std::min(L.T, t0 + L.ckpt);
+        for (int t = t1 - 1; t >= t0; --t) {
+            LayerParams pt = p;
+            pt.dsp = (t < L.T - 1) ? L.dsp : nullptr;
+            HH_LAYER_DISPATCH(mg, L.precision, (k_layer_bwd<G, Q><<<grid1(BN, 128), 128, 0, st>>>(L.models, pt, t)));
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return e;
+            if (t > 0) {
+                // dS_{t-1} = dI_t W_rec^T with dI_t = hi + lo (K = 2N)
+                GemmArgs gd{L.dIb, L.B, 2 * L.N, 0, L.Wrec2, L.N, 2 * L.N, 0, L.dsp, L.B, L.N, 2 * L.N,
+                            L.ds_splits};
+                if ((e = launch_gemm_bf16(gd, L.status, st)) != cudaSuccess)
+                    return e;
+            }
+        }
+    }
+    // weight gradients over the T*B rows
+    {
+        dim3 blk(32, 8);
+        dim3 g1((L.N + 31) / 32, (L.TB + 31) / 32);
+        k_transpose_bf16<float><<<g1, blk, 0, st>>>(L.dI_all, L.TB, L.N, L.N, L.dIT_hi, L.TBp, L.dIT_lo);
+        dim3 g2((L.n_in_pad + 31) / 32, (L.TB + 31) / 32);
+        k_transpose_bf16<uint16_t><<<g2, blk, 0, st>>>(L.Xb, L.TB, L.n_in_pad, L.n_in_pad, L.XT, L.TBp, nullptr);
+        k_transpose_bf16<uint16_t><<<g1, blk, 0, st>>>(L.S, L.TB, L.N, L.N, L.SpT, L.TBp, nullptr);
+        const int s = L.w_splits;
+        const int64_t pin = (int64_t)L.N * L.n_in_pad;
+        GemmArgs a1{L.dIT_hi, L.N, L.TBp, 0, L.XT, L.n_in_pad, L.TBp, 0, L.wpart, L.N, L.n_in_pad, L.TBp, s};
+        GemmArgs a2 = a1;
+        a2.A = L.dIT_lo;
+        a2.C = L.wpart + s * pin;
+        if ((e = launch_gemm_bf16(a1, L.status, st)) != cudaSuccess ||
+            (e = launch_gemm_bf16(a2, L.status, st)) != cudaSuccess)
+            return e;
+        k_reduce_transpose<<<grid1((int64_t)L.n_in * L.N, 256), 256, 0, st>>>(L.wpart, 2 * s, L.N, L.n_in_pad,
+                                                                              L.n_in, L.N, dW_in);
+        const int64_t prc = (int64_t)L.N * L.N;
+        GemmArgs b1{L.dIT_hi, L.N, L.TBp, 0, L.SpT, L.N, L.TBp, 0, L.wpart, L.N, L.N, L.TBp, s};
+        GemmArgs b2 = b1;
+        b2.A = L.dIT_lo;
+        b2.C = L.wpart + s * prc;
+        if ((e = launch_gemm_bf16(b1, L.status, st)) != cudaSuccess ||
+            (e = launch_gemm_bf16(b2, L.status, st)) != cudaSuccess)
+            return e;
+        k_reduce_transpose<<<grid1(prc, 256), 256, 0, st>>>(L.wpart, 2 * s, L.N, L.N, L.N, L.N, dW_rec);
+        k_colsum<<<grid1(L.N, 128), 128, 0, st>>>(L.dI_all, L.TB, L.N, dbias);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hh
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_dup_bf16(const float* __restrict__ W, int64_t rows, int cols, uint16_t* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols)
+        return;
+    const int64_t r = i / cols;
+    const int c = (int)(i % cols);
+    const uint16_t v = hh::f2bf(W[i]);
+    out[r * 2 * cols + c] = v;
+    out[r * 2 * cols + cols + c] = v;
+}
+
+#define HH_LCUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return hh::fail(e_ == cudaErrorMemoryAllocation ? HH_ENOMEM : HH_ECUDA, "%s: %s", \
+                            #call, cudaGetErrorString(e_));                                  \
+    } while (0)
+
+}  // namespace
+
+struct hh_layer {
+    hh::LayerImpl L{};
+    std::vector<void*> allocs;
+    template <class T>
+    cudaError_t alloc(T** p, size_t n)
+    {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            allocs.push_back(*p);
+            e = cudaMemset(*p, 0, (n ? n : 1) * sizeof(T));
+        }
+        return e;
+    }
+    void release()
+    {
+        cudaStreamSynchronize(L.st);
+        for (void* p : allocs)
+            cudaFree(p);
+        allocs.clear();
+    }
+};
+
+extern "C" {
+
+hh_status hh_layer_create(const hh_layer_desc* d, const hh_model_desc* model, hh_layer** out)
+{
+    if (!out)
+        return hh::fail(HH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d || !model)
+        return hh::fail(HH_EINVAL, "descriptor and model must not be NULL");
+    if (d->batch < 1 || d->n_in < 1 || d->n_out < 1 || d->n_steps < 1)
+        return hh::fail(HH_EINVAL, "batch, n_in, n_out and n_steps must be >= 1");
+    if (d->n_hidden < 32 || d->n_hidden % 32 != 0)
+        return hh::fail(HH_EINVAL, "n_hidden must be a positive multiple of 32 (tensor-core tiles)");
+    if (d->substeps < 1 || d->substeps > 16)
+        return hh::fail(HH_EINVAL, "substeps must be in 1..16");
+    if (d->checkpoint_every < 1)
+        return hh::fail(HH_EINVAL, "checkpoint_every must be >= 1");
+    if (!(d->dt_ms > 0.0) || !(d->surrogate_beta > 0.0f))
+        return hh::fail(HH_EINVAL, "dt_ms and surrogate_beta must be > 0");
+    if (d->precision != HH_PREC_FAST && d->precision != HH_PREC_ACCURATE)
+        return hh::fail(HH_EUNSUPPORTED, "the layer supports HH_PREC_FAST and HH_PREC_ACCURATE");
+    if ((int64_t)d->n_steps * d->batch > ((int64_t)1 << 30))
+        return hh::fail(HH_EINVAL, "n_steps * batch too large");
+    hh::DevModel dm{};
+    hh_status s = hh::prep_model(model, d->dt_ms, &dm);
+    if (s != HH_OK)
+        return s;
+    if (dm.ca_ch >= 0)
+        return hh::fail(HH_EUNSUPPORTED, "the layer supports models without a calcium pool");
+    for (int q = 0; q < dm.n_gates; ++q)
+        if (dm.g[q].kind == HH_GATE_CA)
+            return hh::fail(HH_EUNSUPPORTED, "the layer supports alpha/beta and inf/tau gates");
+    hh_layer* ly = new (std::nothrow) hh_layer();
+    if (!ly)
+        return hh::fail(HH_ENOMEM, "host allocation failed");
+    hh::LayerImpl& L = ly->L;
+    L.B = d->batch;
+    L.n_in = d->n_in;
+    L.n_in_pad = (d->n_in + 31) / 32 * 32;
+    L.N = d->n_hidden;
+    L.n_out = d->n_out;
+    L.T = d->n_steps;
+    L.K = d->substeps;
+    L.ckpt = d->checkpoint_every;
+    L.n_ckpt = (L.T + L.ckpt - 1) / L.ckpt;
+    L.TB = L.T * L.B;
+    L.TBp = (L.TB + 7) / 8 * 8;
+    L.dt = (float)d->dt_ms;
+    L.theta = d->v_threshold;
+    L.beta = d->surrogate_beta;
+    L.V0 = d->v_init;
+    L.precision = d->precision;
+    L.smooth = d->smooth ? 1 : 0;
+    L.st = (cudaStream_t)d->stream;
+    L.models.n = 1;
+    L.models.max_gates = dm.n_gates;
+    L.models.m[0] = dm;
+    L.rec_splits = std::max(1, std::min(8, L.N / 128));
+    L.ds_splits = std::max(1, std::min(8, 2 * L.N / 256));
+    L.w_splits = std::max(1, std::min(8, L.TBp / 4096));
+    const size_t BN = (size_t)L.B * L.N, N = L.N, TB = L.TB, TBp = L.TBp;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t n) {
+        if (e == cudaSuccess)
+            e = ly->alloc(p, n);
+    };
+    A(&L.W_out, (size_t)L.n_out * N);
+    A(&L.bias, N);
+    A(&L.WinT, N * L.n_in_pad);
+    A(&L.WrecT, N * N);
+    A(&L.Wrec2, N * 2 * N);
+    A(&L.Xb, TB * L.n_in_pad);
+    A(&L.S, (TB + L.B) * N);
+    A(&L.XW, TB * N);
+    A(&L.recp, (size_t)L.rec_splits * BN);
+    A(&L.I_all, TB * N);
+    A(&L.Sf, TB * N);
+    A(&L.V, BN);
+    A(&L.P, BN * hh::kMaxGates);
+    A(&L.ckptV, (size_t)(L.n_ckpt + 1) * BN);
+    A(&L.ckptP, (size_t)(L.n_ckpt + 1) * hh::kMaxGates * BN);
+    A(&L.acc, BN);
+    A(&L.dlogits, (size_t)L.B * L.n_out);
+    A(&L.loss_b, (size_t)L.B);
+    A(&L.segV, (size_t)L.ckpt * BN);
+    A(&L.segP, (size_t)L.ckpt * hh::kMaxGates * BN);
+    A(&L.lamV, BN);
+    A(&L.lamP, BN * hh::kMaxGates);
+    A(&L.ds_direct, BN);
+    A(&L.dsp, (size_t)L.ds_splits * BN);
+    A(&L.dI_all, TB * N);
+    A(&L.dIb, BN * 2);
+    A(&L.dIT_hi, N * TBp);
+    A(&L.dIT_lo, N * TBp);
+    A(&L.XT, (size_t)L.n_in_pad * TBp);
+    A(&L.SpT, N * TBp);
+    A(&L.wpart, (size_t)2 * L.w_splits * N * std::max<size_t>(N, L.n_in_pad));
+    A(&L.status, 1);
+    if (e != cudaSuccess) {
+        ly->release();
+        delete ly;
+        return hh::fail(e == cudaErrorMemoryAllocation ? HH_ENOMEM : HH_ECUDA, "layer allocation: %s",
+                        cudaGetErrorString(e));
+    }
+    *out = ly;
+    return HH_OK;
+}
+
+hh_status hh_layer_set_weights(hh_layer* ly, const float* W_in, const float* W_rec, const float* W_out,
+                               const float* bias)
+{
+    if (!ly || !W_in || !W_rec || !W_out || !bias)
+        return hh::fail(HH_EINVAL, "layer and weights must not be NULL");
+    hh::LayerImpl& L = ly->L;
+    cudaStream_t st = L.st;
+    float *win = nullptr, *wrec = nullptr;
+    const size_t nin = (size_t)L.n_in * L.N, nrec = (size_t)L.N * L.N;
+    HH_LCUDA(cudaMalloc(&win, nin * sizeof(float)));
+    cudaError_t e = cudaMalloc(&wrec, nrec * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(win, W_in, nin * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(wrec, W_rec, nrec * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(L.W_out, W_out, (size_t)L.n_out * L.N * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(L.bias, bias, (size_t)L.N * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) {
+        dim3 blk(32, 8);
+        hh::k_transpose_bf16<float><<<dim3((L.N + 31) / 32, (L.n_in + 31) / 32), blk, 0, st>>>(
+            win, L.n_in, L.N, L.N, L.WinT, L.n_in_pad, nullptr);
+        hh::k_transpose_bf16<float><<<dim3((L.N + 31) / 32, (L.N + 31) / 32), blk, 0, st>>>(
+            wrec, L.N, L.N, L.N, L.WrecT, L.N, nullptr);
+        k_dup_bf16<<<hh::grid1((int64_t)nrec, 256), 256, 0, st>>>(wrec, L.N, L.N, L.Wrec2);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(win);
+    cudaFree(wrec);
+    if (e == cudaSuccess)
+        e = e2;
+    if (e != cudaSuccess)
+        return hh::fail(HH_ECUDA, "setting weights: %s", cudaGetErrorString(e));
+    L.forward_done = false;
+    return HH_OK;
+}
+
+hh_status hh_layer_forward(hh_layer* ly, const float* X, const int32_t* labels, float* loss, float* logits)
+{
+    if (!ly || !X || !labels || !loss)
+        return hh::fail(HH_EINVAL, "layer, X, labels and loss must not be NULL");
+    HH_LCUDA(hh::layer_forward(ly->L, X, labels, loss, logits));
+    return HH_OK;
+}
+
+hh_status hh_backward(hh_layer* ly, const hh_grads* g)
+{
+    if (!ly || !g || !g->dW_in || !g->dW_rec || !g->dW_out || !g->dbias)
+        return hh::fail(HH_EINVAL, "layer and every gradient buffer must be given");
+    if (!ly->L.forward_done)
+        return hh::fail(HH_ESTATE, "hh_backward needs a preceding hh_layer_forward");
+    HH_LCUDA(hh::layer_backward(ly->L, g->dW_in, g->dW_rec, g->dW_out, g->dbias));
+    return HH_OK;
+}
+
+hh_status hh_layer_readout(hh_layer* ly, int32_t what, void* dst, size_t cap, size_t* n_bytes)
+{
+    if (!ly || !dst)
+        return hh::fail(HH_EINVAL, "layer and dst must not be NULL");
+    if (n_bytes)
+        *n_bytes = 0;
+    hh::LayerImpl& L = ly->L;
+    HH_LCUDA(cudaStreamSynchronize(L.st));
+    const void* src = nullptr;
+    size_t need = 0;
+    switch (what) {
+    case HH_LAYER_SPIKES: src = L.Sf; need = (size_t)L.TB * L.N * sizeof(float); break;
+    case HH_LAYER_V: src = L.V; need = (size_t)L.B * L.N * sizeof(float); break;
+    case HH_LAYER_STATUS: src = L.status; need = sizeof(int32_t); break;
+    default: return hh::fail(HH_EINVAL, "unknown layer readout %d", what);
+    }
+    if (cap < need)
+        return hh::fail(HH_EOVERFLOW, "layer readout %d needs %zu bytes", what, need);
+    HH_LCUDA(cudaMemcpy(dst, src, need, cudaMemcpyDefault));
+    if (n_bytes)
+        *n_bytes = need;
+    return HH_OK;
+}
+
+void hh_layer_destroy(hh_layer* ly)
+{
+    if (!ly)
+        return;
+    ly->release();
+    delete ly;
+}
+
+}  // extern "C"

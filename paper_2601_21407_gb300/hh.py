@@ -88,6 +88,22 @@ class hh_neurons_noalloc(C.Structure):
 HH_NOALLOC_MAX_NEURONS = 1 << 20
 
 
+class hh_layer_desc(C.Structure):
+    _fields_ = [("batch", C.c_int32), ("n_in", C.c_int32), ("n_hidden", C.c_int32),
+                ("n_out", C.c_int32), ("n_steps", C.c_int32), ("substeps", C.c_int32),
+                ("dt_ms", C.c_double), ("v_threshold", C.c_float), ("v_init", C.c_float),
+                ("surrogate_beta", C.c_float), ("precision", C.c_int32), ("smooth", C.c_int32),
+                ("checkpoint_every", C.c_int32), ("stream", C.c_void_p)]
+
+
+class hh_grads(C.Structure):
+    _fields_ = [("dW_in", C.c_void_p), ("dW_rec", C.c_void_p), ("dW_out", C.c_void_p),
+                ("dbias", C.c_void_p)]
+
+
+HH_LAYER_SPIKES, HH_LAYER_V, HH_LAYER_STATUS = 0, 1, 2
+
+
 class hh_kernel_time(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -100,7 +116,8 @@ class hh_record(C.Structure):
 
 EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_route_spikes",
            "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
-           "hh_last_error", "hh_version"]
+           "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
+           "hh_layer_forward", "hh_backward", "hh_layer_readout", "hh_layer_destroy"]
 
 
 def lib_path() -> str:
@@ -137,6 +154,18 @@ def lib():
             L.hh_gemm_bf16.restype = C.c_int
             L.hh_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_int32, vp, vp]
+            L.hh_layer_create.restype = C.c_int
+            L.hh_layer_create.argtypes = [P(hh_layer_desc), P(hh_model_desc), P(vp)]
+            L.hh_layer_set_weights.restype = C.c_int
+            L.hh_layer_set_weights.argtypes = [vp, vp, vp, vp, vp]
+            L.hh_layer_forward.restype = C.c_int
+            L.hh_layer_forward.argtypes = [vp, vp, vp, vp, vp]
+            L.hh_backward.restype = C.c_int
+            L.hh_backward.argtypes = [vp, P(hh_grads)]
+            L.hh_layer_readout.restype = C.c_int
+            L.hh_layer_readout.argtypes = [vp, C.c_int32, vp, C.c_size_t, P(C.c_size_t)]
+            L.hh_layer_destroy.restype = None
+            L.hh_layer_destroy.argtypes = [vp]
             L.hh_destroy.restype = None
             L.hh_destroy.argtypes = [vp]
             L.hh_last_error.restype = C.c_char_p
@@ -397,3 +426,50 @@ def spikes_to_numpy(b):
     frac = raw[:, 2].copy().view(np.float32)
     o = np.lexsort((idx, step))
     return step[o], idx[o], frac[o]
+
+
+class Layer:
+    """Owns one hh_layer (differentiable recurrent HH layer).  Device tensors
+    are torch tensors; the library does the work."""
+
+    def __init__(self, model: dict, *, batch, n_in, n_hidden, n_out, n_steps, substeps=10,
+                 dt=0.01, theta=0.0, v_init=-65.0, beta=0.5, precision=HH_PREC_FAST, smooth=False,
+                 checkpoint_every=25, stream=None):
+        d = hh_layer_desc(batch, n_in, n_hidden, n_out, n_steps, substeps, dt, theta, v_init, beta,
+                          precision, 1 if smooth else 0, checkpoint_every, stream)
+        self.shape = (n_steps, batch, n_in, n_hidden, n_out)
+        h = C.c_void_p()
+        _check(lib().hh_layer_create(C.byref(d), C.byref(model_desc(model)), C.byref(h)))
+        self.handle = h.value
+
+    def set_weights(self, W_in, W_rec, W_out, bias):
+        ws = [np.ascontiguousarray(w, dtype=np.float32) if not hasattr(w, "data_ptr") else w.contiguous()
+              for w in (W_in, W_rec, W_out, bias)]
+        _check(lib().hh_layer_set_weights(self.handle, *[_ptr(w) for w in ws]))
+
+    def forward(self, X, labels, loss, logits=None):
+        _check(lib().hh_layer_forward(self.handle, X.data_ptr(), labels.data_ptr(), loss.data_ptr(),
+                                      None if logits is None else logits.data_ptr()))
+
+    def backward(self, dW_in, dW_rec, dW_out, dbias):
+        g = hh_grads(dW_in.data_ptr(), dW_rec.data_ptr(), dW_out.data_ptr(), dbias.data_ptr())
+        _check(lib().hh_backward(self.handle, C.byref(g)))
+
+    def readout(self, what):
+        T, B, _, N, _ = self.shape
+        n = {HH_LAYER_SPIKES: T * B * N, HH_LAYER_V: B * N, HH_LAYER_STATUS: 1}[what]
+        out = np.zeros(n, dtype=np.int32 if what == HH_LAYER_STATUS else np.float32)
+        nb = C.c_size_t()
+        _check(lib().hh_layer_readout(self.handle, what, out.ctypes.data, out.nbytes, C.byref(nb)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hh_layer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
