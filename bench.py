@@ -283,10 +283,86 @@ def run_gpu(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if not args.no_extras:
+            line["extra"] = extras(dev, pk)
         print(json.dumps(line), flush=True)
     net.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def extras(dev, pk):
+    """Throughput of the other workloads on the same GPU (not the headline):
+    single classic neurons (1,024 x 10,000 steps, dt 0.01 ms), the
+    differentiable layer (B=128, 700 inputs, 1,024 neurons, T=250 x 10
+    substeps, forward + BPTT), 1e6 multi-channel neurons (20,000 steps,
+    dt 0.025 ms), and the tcgen05 GEMM on the layer's two large shapes."""
+    import torch
+
+    from paper_2601_21407_gb300 import hh
+    out = {}
+
+    def timed(fn, reps=1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    x = inp.single_neurons(1024, seed=0)
+    for name, prec in (("compensated", hh.HH_PREC_COMPENSATED), ("fast", hh.HH_PREC_FAST)):
+        net = hh.Network(x["V0"], 0.01, I_const=x["I"], precision=prec)
+        net.set_channels(0, inp.CLASSIC_HH)
+        rec, b = hh.make_record(1024, 10_000, spike_cap=100_000)
+        net.step(10)
+        ms = timed(lambda: net.step(10_000, rec=rec), reps=3)
+        out[f"single_neurons_1024_{name}"] = {"neuron_steps_per_s": 1024 * 10_000 / (ms * 1e-3),
+                                              "ms_per_100ms_sim": ms}
+        net.close()
+
+    y = inp.multi_channel_neurons(1_000_000, seed=0)
+    net = hh.Network(y["V0"], 0.025, I_const=y["I"], precision=hh.HH_PREC_FAST)
+    net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
+    net.step(10)
+    rec, b = hh.make_record(1_000_000, 20_000, spike_cap=0)
+    ms = timed(lambda: net.step(20_000, rec=rec))
+    out["multichannel_1e6_500ms"] = {"neuron_steps_per_s": 1e6 * 20_000 / (ms * 1e-3), "ms": ms,
+                                     "mean_rate_hz": float(b["counts"].sum().item()) / 1e6 / 0.5}
+    net.close()
+    del y
+
+    d = inp.recurrent_layer(B=128, n_in=700, n_hid=1024, n_out=20, T=250, seed=0)
+    lay = hh.Layer(inp.CLASSIC_HH, batch=128, n_in=700, n_hidden=1024, n_out=20, n_steps=250,
+                   substeps=10, dt=0.01, precision=hh.HH_PREC_FAST, checkpoint_every=25)
+    lay.set_weights(d["W_in"], d["W_rec"], d["W_out"], d["bias"])
+    X = torch.as_tensor(d["X"], device=dev)
+    lab = torch.as_tensor(d["labels"], device=dev)
+    loss = torch.zeros(1, device=dev)
+    g = [torch.zeros(s, device=dev) for s in ((700, 1024), (1024, 1024), (20, 1024), (1024,))]
+    lay.forward(X, lab, loss)
+    lay.backward(*g)
+    fwd = timed(lambda: lay.forward(X, lab, loss), reps=3)
+    both = timed(lambda: (lay.forward(X, lab, loss), lay.backward(*g)), reps=3)
+    out["bptt_layer_b128_t250"] = {"bptt_steps_per_s": 1e3 / both, "forward_ms": fwd,
+                                   "backward_ms": both - fwd, "loss": float(loss.item()),
+                                   "status": int(lay.readout(hh.HH_LAYER_STATUS)[0])}
+    lay.close()
+
+    peak = float(pk.get("bf16_tflops", 1933.0))
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    for name, (M, N, K, splits) in {"input_projection_32000x1024x704": (32000, 1024, 704, 1),
+                                    "weight_grad_1024x704x32000": (1024, 704, 32000, 7)}.items():
+        A = torch.randn(M, K, device=dev).to(torch.bfloat16)
+        Bt = torch.randn(N, K, device=dev).to(torch.bfloat16)
+        Cc = torch.empty((splits, M, N), device=dev)
+        hh.hh_gemm_bf16(A, Bt, Cc, M, N, K, splits=splits, status=st)
+        ms = timed(lambda: hh.hh_gemm_bf16(A, Bt, Cc, M, N, K, splits=splits, status=st), reps=10)
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        out[f"gemm_{name}"] = {"tflops": tf, "frac_of_measured_bf16": tf / peak, "us": ms * 1e3}
+    return out
 
 
 def cpu_baseline_sample(cores, sim_steps=None):
@@ -350,14 +426,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ncu_case():
-    """Small fixed case for ncu captures: the benchmark network, 120 time steps
-    (three delay windows), then one open-loop routing launch of a 40-step
-    raster with 1% of the neurons spiking per step."""
+def ncu_case(name):
+    """Small fixed cases for ncu captures.
+    network: the benchmark network, 120 time steps (three delay windows),
+             then one open-loop routing launch of a 40-step raster with 1% of
+             the neurons spiking per step;
+    gemm:    the layer's input projection (32000 x 1024 x 704, bf16) twice;
+    layer:   the differentiable layer at full width (B=128, 700 inputs, 1,024
+             neurons) for T=25 outer steps, forward and backward."""
     import torch
 
     from paper_2601_21407_gb300 import hh
     torch.cuda.set_device(0)
+    if name == "gemm":
+        M, N, K = 32000, 1024, 704
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+        Bt = torch.randn(N, K, device="cuda").to(torch.bfloat16)
+        Cc = torch.empty((1, M, N), device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            hh.hh_gemm_bf16(A, Bt, Cc, M, N, K, status=st)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "gemm", "status": int(st.item())}))
+        return
+    if name == "layer":
+        d = inp.recurrent_layer(B=128, n_in=700, n_hid=1024, n_out=20, T=25, seed=0)
+        lay = hh.Layer(inp.CLASSIC_HH, batch=128, n_in=700, n_hidden=1024, n_out=20, n_steps=25,
+                       substeps=10, dt=0.01, precision=hh.HH_PREC_FAST, checkpoint_every=25)
+        lay.set_weights(d["W_in"], d["W_rec"], d["W_out"], d["bias"])
+        X = torch.as_tensor(d["X"], device="cuda")
+        lab = torch.as_tensor(d["labels"], device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        g = [torch.zeros(s, device="cuda") for s in ((700, 1024), (1024, 1024), (20, 1024), (1024,))]
+        lay.forward(X, lab, loss)
+        lay.backward(*g)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "layer", "loss": float(loss.item()),
+                          "status": int(lay.readout(hh.HH_LAYER_STATUS)[0])}))
+        lay.close()
+        return
     g = inp.network(n=W["n"], k_in=W["k_in"], exc_frac=W["exc_frac"], seed=W["seed"],
                     mu=W["mu"], sigma=W["sigma"])
     net = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
@@ -383,11 +490,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="run the small fixed case used for ncu captures and exit")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (single neurons, BPTT layer, 1e6 neurons, GEMM)")
+    ap.add_argument("--ncu-case", nargs="?", const="network", default=None,
+                    choices=["network", "gemm", "layer"],
+                    help="run a small fixed case used for ncu captures and exit")
     args = ap.parse_args()
     if args.ncu_case:
-        ncu_case()
+        ncu_case(args.ncu_case)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -486,15 +486,30 @@ __global__ void k_reduce_transpose(const float* __restrict__ part, int splits, i
     dst[i] = s;
 }
 
-// dbias[n] = sum_{t,b} dI[t][b][n]
-__global__ void k_colsum(const float* __restrict__ dI, int64_t rows, int N, float* out)
+// dbias[n] = sum_{t,b} dI[t][b][n], in two deterministic passes: chunk sums
+// part[c][n] over rows [c*rows/chunks, (c+1)*rows/chunks), then their sum.
+constexpr int kColChunks = 128;
+__global__ void k_colsum_part(const float* __restrict__ dI, int64_t rows, int N, float* part)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (n >= N)
+        return;
+    const int64_t r0 = rows * c / kColChunks, r1 = rows * (c + 1) / kColChunks;
+    float s = 0.0f;
+    for (int64_t r = r0; r < r1; ++r)
+        s += dI[r * N + n];
+    part[(int64_t)c * N + n] = s;
+}
+
+__global__ void k_colsum_final(const float* __restrict__ part, int N, float* out)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N)
         return;
     float s = 0.0f;
-    for (int64_t r = 0; r < rows; ++r)
-        s += dI[r * N + n];
+    for (int c = 0; c < kColChunks; ++c)
+        s += part[(int64_t)c * N + n];
     out[n] = s;
 }
 
@@ -692,7 +707,8 @@ cudaError_t layer_backward(LayerImpl& L, float* dW_in, float* dW_rec, float* dW_
             (e = launch_gemm_bf16(b2, L.status, st)) != cudaSuccess)
             return e;
         k_reduce_transpose<<<grid1(prc, 256), 256, 0, st>>>(L.wpart, 2 * s, L.N, L.N, L.N, L.N, dW_rec);
-        k_colsum<<<grid1(L.N, 128), 128, 0, st>>>(L.dI_all, L.TB, L.N, dbias);
+        k_colsum_part<<<dim3(grid1(L.N, 128), kColChunks), 128, 0, st>>>(L.dI_all, L.TB, L.N, L.wpart);
+        k_colsum_final<<<grid1(L.N, 128), 128, 0, st>>>(L.wpart, L.N, dbias);
     }
     return cudaGetLastError();
 }
@@ -845,7 +861,8 @@ hh_status hh_layer_create(const hh_layer_desc* d, const hh_model_desc* model, hh
     A(&L.dIT_lo, N * TBp);
     A(&L.XT, (size_t)L.n_in_pad * TBp);
     A(&L.SpT, N * TBp);
-    A(&L.wpart, (size_t)2 * L.w_splits * N * std::max<size_t>(N, L.n_in_pad));
+    A(&L.wpart, std::max((size_t)2 * L.w_splits * N * std::max<size_t>(N, L.n_in_pad),
+                         (size_t)hh::kColChunks * N));
     A(&L.status, 1);
     if (e != cudaSuccess) {
         ly->release();
