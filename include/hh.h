@@ -277,6 +277,60 @@ hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* s
                           int64_t n_spk, int32_t n_window, int64_t* sum_E, int64_t* sum_I);
 
 /* ------------------------------------------------------------------ */
+/* Learned multi-step surrogate                                         */
+/* ------------------------------------------------------------------ */
+
+/* A small MLP (features -> 64 -> 64 -> state increments, tanh, bf16 weights
+ * with fp32 accumulation on the tensor cores) that advances V, the gates and
+ * Ca of an independent neuron by `window` steps at once while the neuron is
+ * inside the sub-threshold envelope it was trained on.  It has no
+ * counterpart in the paper (whose operators use polynomial approximations of
+ * the rates, Methods "Engineering optimization"); the plain exponential-
+ * Euler integrator generates its training data, integrates every window the
+ * surrogate declines, and judges its error.
+ * Features: (V + 65)/20, 2p - 1 per gate, log(Ca/Ca_rest)/2, I/10,
+ * log(gbar_c / default gbar_c)/0.3 per channel.  Targets: the increments
+ * over the window, scaled to unit variance.  A window is taken from the MLP
+ * when V < v_envelope at its start, every feature lies within the range seen
+ * in training (widened by 2 %), and the prediction keeps V below the
+ * envelope, the gates in [0, 1] and Ca positive; otherwise the plain kernel
+ * integrates it (so every spike comes from the plain integrator). */
+typedef struct {
+    int32_t window;          /* steps per MLP evaluation, 1..1000           */
+    float v_envelope;        /* mV                                          */
+    int32_t train_neurons;   /* training trajectories (>= 128)              */
+    int32_t train_windows;   /* windows recorded for training (>= 1024)     */
+    int32_t epochs;          /* >= 1                                        */
+    int32_t batch;           /* >= 128 (rounded down to a multiple of 128)  */
+    float lr;                /* Adam learning rate, cosine decay            */
+    uint64_t seed;
+    float I_min, I_max;      /* uA/cm^2 range of the training neurons       */
+    float gbar_sigma;        /* lognormal spread of their maximal conductances */
+    float V0_min, V0_max;    /* initial V range (gates at steady state)     */
+} hh_surrogate_desc;
+
+typedef struct {
+    int64_t train_windows;   /* windows used                                  */
+    float train_loss;        /* mean squared error of the scaled increments   */
+    float val_loss;          /* same on 5 % held-out windows                  */
+    float out_scale_V;       /* std of the V increment over a window (mV)     */
+} hh_surrogate_report;
+
+/* Train a surrogate for model 0 of `net` (its dt and precision) and keep it
+ * in the network.  Requires a network of independent neurons (no synapses,
+ * no background) with a single model and HH_KERNELS_SPECIALISED, precision
+ * FAST or ACCURATE.  Synchronous.  Errors: HH_EINVAL, HH_EUNSUPPORTED,
+ * HH_ESTATE (model 0 not installed), HH_ENOMEM, HH_ECUDA. */
+hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surrogate_report* rep);
+
+/* Use (1) or stop using (0) the trained surrogate in hh_step_n: whole
+ * windows go through the MLP or the plain kernel as described above; the
+ * steps left over after the last whole window are plain.  V traces and
+ * per-step currents are not supported while it is enabled (HH_EUNSUPPORTED).  HH_READ_SURROGATE reads
+ * the counts of accepted and declined neuron-windows. */
+hh_status hh_surrogate_enable(hh_net* net, int32_t enable);
+
+/* ------------------------------------------------------------------ */
 /* Dense projections on the tensor cores                                */
 /* ------------------------------------------------------------------ */
 
@@ -383,7 +437,8 @@ enum {
     HH_READ_STATUS = 4,  /* int32: OR of HH_STATUS_* bits since the last reset */
     HH_READ_TIME = 5,    /* int64: steps advanced since creation / reset    */
     HH_READ_N_OUT = 6,   /* int64 [N+1] out-CSR row pointer (rows = pre)    */
-    HH_READ_PROFILE = 7  /* hh_kernel_time [HH_KERNEL_COUNT] since hh_profile(net, 1) */
+    HH_READ_PROFILE = 7, /* hh_kernel_time [HH_KERNEL_COUNT] since hh_profile(net, 1) */
+    HH_READ_SURROGATE = 8 /* uint64 [2]: neuron-windows taken from the surrogate, declined */
 };
 enum { HH_STATUS_SPIKE_OVERFLOW = 1, HH_STATUS_NONFINITE = 2 };
 

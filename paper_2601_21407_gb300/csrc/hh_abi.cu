@@ -82,6 +82,10 @@ struct hh_net {
 
     hh::SpikeList list{};
 
+    // learned surrogate
+    hh::Surrogate* sur = nullptr;
+    bool sur_on = false;
+
     // kernel timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -136,6 +140,10 @@ struct hh_net {
             cudaStreamSynchronize(st);
         else
             cudaDeviceSynchronize();
+        if (sur) {
+            hh::surrogate_free(sur);
+            sur = nullptr;
+        }
         for (void* p : allocs)
             cudaFree(p);
         allocs.clear();
@@ -718,6 +726,31 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         net->jit_ready = true;
     }
     const bool spec = net->kernels == HH_KERNELS_SPECIALISED;
+    if (net->sur_on) {
+        if (R.V_trace)
+            return fail(HH_EUNSUPPORTED, "V traces are not recorded while the surrogate is enabled");
+        if (I_steps)
+            return fail(HH_EUNSUPPORTED, "per-step currents are not supported while the surrogate is enabled");
+        const int W = hh::surrogate_window_steps(net->sur);
+        const int n_win = n_steps / W, rem = n_steps % W;
+        for (int w = 0; w < n_win; ++w) {
+            const int64_t t0 = net->t + (int64_t)w * W;
+            HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
+                return hh::surrogate_window(net->models, net->sur, p, net->precision, net->st);
+            }));
+            HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
+                return hh::jit_launch_indexed(net->jit, p, hh::surrogate_fb_list(net->sur),
+                                              hh::surrogate_fb_count(net->sur), net->N, t0, W, R, net->st);
+            }));
+        }
+        if (rem)
+            HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
+                return hh::jit_launch_independent(net->jit, p, net->t + (int64_t)n_win * W, rem, I_steps, R,
+                                                  net->st);
+            }));
+        net->t += n_steps;
+        return HH_OK;
+    }
     if (!net->has_syn && !net->has_bg) {
         if (spec)
             HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
@@ -822,6 +855,11 @@ hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap, size_t* n
         need = (N + 1) * sizeof(int64_t);
         break;
     case HH_READ_PROFILE: need = sizeof(net->ktime); break;
+    case HH_READ_SURROGATE:
+        if (!net->sur)
+            return fail(HH_ESTATE, "no surrogate trained");
+        need = 2 * sizeof(uint64_t);
+        break;
     default: return fail(HH_EINVAL, "unknown readout %d", what);
     }
     if (!dst)
@@ -843,6 +881,15 @@ hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap, size_t* n
         break;
     }
     case HH_READ_N_OUT: HH_CUDA(cudaMemcpy(dst, net->out_ptr, need, cudaMemcpyDefault)); break;
+    case HH_READ_SURROGATE: {
+        unsigned long long s2[2];
+        int32_t err = 0;
+        HH_CUDA(hh::surrogate_stats(net->sur, s2, &err));
+        if (err)
+            return fail(HH_ETIMEOUT, "a bounded wait in the surrogate kernel expired (code %d)", err);
+        HH_CUDA(cudaMemcpy(dst, s2, need, cudaMemcpyDefault));
+        break;
+    }
     case HH_READ_PROFILE:
         HH_CUDA(net->harvest());
         HH_CUDA(cudaMemcpy(dst, net->ktime, need, cudaMemcpyDefault));
@@ -873,6 +920,48 @@ hh_status hh_gemm_bf16(const void* A, int32_t lda, const void* Bt, int32_t ldb, 
     if (const char* why = hh::gemm_check(g))
         return fail(HH_EINVAL, "%s", why);
     HH_CUDA(hh::launch_gemm_bf16(g, status, (cudaStream_t)stream));
+    return HH_OK;
+}
+
+hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surrogate_report* rep)
+{
+    if (!net || !d)
+        return fail(HH_EINVAL, "net and descriptor must not be NULL");
+    if (net->has_syn || net->has_bg)
+        return fail(HH_EUNSUPPORTED, "the surrogate is for networks of independent neurons");
+    if (net->model_id)
+        return fail(HH_EUNSUPPORTED, "the surrogate supports a single model (model_id must be NULL)");
+    if (net->kernels != HH_KERNELS_SPECIALISED)
+        return fail(HH_EUNSUPPORTED, "the surrogate needs HH_KERNELS_SPECIALISED");
+    if (net->precision == HH_PREC_COMPENSATED)
+        return fail(HH_EUNSUPPORTED, "the surrogate supports HH_PREC_FAST and HH_PREC_ACCURATE");
+    if (!net->installed[0])
+        return fail(HH_ESTATE, "model 0 is not installed");
+    if (!net->jit_ready) {
+        std::string err;
+        if (!hh::jit_get(net->models, net->installed, net->precision, &net->jit, &err))
+            return fail(HH_ECUDA, "%s", err.c_str());
+        net->jit_ready = true;
+    }
+    hh::Surrogate* s = nullptr;
+    hh_status rc = hh::surrogate_train(net->models, net->precision, net->dt, net->N, d, net->st, &s, rep);
+    if (rc != HH_OK)
+        return rc;
+    if (net->sur)
+        hh::surrogate_free(net->sur);
+    net->sur = s;
+    return HH_OK;
+}
+
+hh_status hh_surrogate_enable(hh_net* net, int32_t enable)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (enable && !net->sur)
+        return fail(HH_ESTATE, "no surrogate trained");
+    net->sur_on = enable != 0;
+    if (net->sur)
+        HH_CUDA(hh::surrogate_reset_stats(net->sur, net->st));
     return HH_OK;
 }
 

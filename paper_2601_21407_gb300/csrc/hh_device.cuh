@@ -520,6 +520,42 @@ __device__ __forceinline__ void independent_body(const Dyn& dyn, const NeuronPar
     }
 }
 
+// Independent neurons named by a device list (the windows the learned
+// surrogate declined): n_steps plain steps for each listed neuron.
+template <int MAXG, int PREC, class Dyn>
+__device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams& P, const int32_t* __restrict__ list,
+                                             const int32_t* __restrict__ n_list, int64_t t0, int32_t n_steps,
+                                             const RecordParams& R)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nl = *n_list;
+    if ((int64_t)blockIdx.x * blockDim.x >= nl)
+        return;  // whole block past the list (uniform per block)
+    const bool valid = gi < nl;
+    const int64_t i = valid ? list[gi] : list[0];
+    const int mid = P.model_id ? P.model_id[i] : 0;
+    State<MAXG, PREC> s;
+    load_state(P, i, s);
+    dyn.template load<MAXG, PREC>(mid, P, i, s);
+    const float Ic = P.I_const ? P.I_const[i] : 0.0f;
+    int32_t cnt = 0;
+    for (int32_t k = 0; k < n_steps; ++k) {
+        const float Vt = s.V;
+        dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, Ic, 0.0f, 0.0f, 0.0f, 0.0f, s);
+        const bool spk = valid && Vt < P.theta && s.V >= P.theta;
+        cnt += spk;
+        const float frac = spk ? (P.theta - Vt) / (s.V - Vt) : 0.0f;
+        record_spikes(spk, (int32_t)(t0 + k), (int32_t)i, frac, R, P.status);
+    }
+    if (valid) {
+        store_state(P, i, s);
+        if (R.counts && cnt)
+            R.counts[i] += cnt;
+        if (!finite(s.V))
+            atomicOr(P.status, HH_STATUS_NONFINITE);
+    }
+}
+
 // Network window: W <= D steps; spikes go to the window list for routing.
 // The input of every step in the window comes from spikes at least D steps
 // earlier, already routed by previous launches, so neurons are independent

@@ -72,10 +72,24 @@ struct GemmArgs {
 const char* gemm_check(const GemmArgs& g);
 cudaError_t launch_gemm_bf16(const GemmArgs& g, int32_t* err, cudaStream_t st);
 
+// learned surrogate (hh_surrogate.cu)
+struct Surrogate;
+hh_status surrogate_train(const DevModels& Ms, int precision, double dt, int64_t N_net,
+                          const hh_surrogate_desc* d, cudaStream_t st, Surrogate** out, hh_surrogate_report* rep);
+void surrogate_free(Surrogate* s);
+cudaError_t surrogate_window(const DevModels& Ms, Surrogate* S, const NeuronParams& P, int precision,
+                             cudaStream_t st);
+int surrogate_window_steps(const Surrogate* S);
+const int32_t* surrogate_fb_list(const Surrogate* S);
+const int32_t* surrogate_fb_count(const Surrogate* S);
+cudaError_t surrogate_stats(const Surrogate* S, unsigned long long* host2, int32_t* err);
+cudaError_t surrogate_reset_stats(Surrogate* S, cudaStream_t st);
+
 // Neuron kernels specialised for a model set, compiled with NVRTC (hh_jit.cu).
 struct JitKernels {
     cudaKernel_t independent = nullptr;
     cudaKernel_t window = nullptr;
+    cudaKernel_t indexed = nullptr;
 };
 // Compile (or take from the process-wide cache) the kernels for the installed
 // models; false with a message in *err on failure.
@@ -83,6 +97,9 @@ bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernel
 cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, int64_t t0,
                                    int32_t n_steps, const float* I_steps, const RecordParams& R,
                                    cudaStream_t st);
+cudaError_t jit_launch_indexed(const JitKernels& K, const NeuronParams& P, const int32_t* list,
+                               const int32_t* n_list, int64_t max_list, int64_t t0, int32_t n_steps,
+                               const RecordParams& R, cudaStream_t st);
 cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_t t0, int32_t W,
                               int32_t parity, const float* I_steps, const RecordParams& R,
                               const SpikeList& L, cudaStream_t st);

@@ -151,7 +151,7 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
          "                                         float gsI, float EI, State<MAXG, PREC>& s) const\n    {\n";
     s += dispatch("neuron_step<MAXG, PREC>(M, dt, v_update, I, gsE, EE, gsI, EI, s)");
     s += "    }\n};\n\n}  // namespace hh\n\n";
-    char b[1024];
+    char b[2048];
     snprintf(b, sizeof(b),
              "constexpr int kJitMaxG = %d;\nconstexpr int kJitPrec = %d;\n\n"
              "extern \"C\" __global__ void __launch_bounds__(128)\n"
@@ -162,7 +162,12 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
              "hh_jit_window(const __grid_constant__ hh::NeuronParams P, long long t0, int W,\n"
              "              const float* __restrict__ I_steps, const __grid_constant__ hh::RecordParams R,\n"
              "              const __grid_constant__ hh::SpikeList L, int parity)\n"
-             "{\n    hh::window_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, t0, W, I_steps, R, L, parity);\n}\n",
+             "{\n    hh::window_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, t0, W, I_steps, R, L, parity);\n}\n\n"
+             "extern \"C\" __global__ void __launch_bounds__(128)\n"
+             "hh_jit_indexed(const __grid_constant__ hh::NeuronParams P, const int* __restrict__ list,\n"
+             "               const int* __restrict__ n_list, long long t0, int n_steps,\n"
+             "               const __grid_constant__ hh::RecordParams R)\n"
+             "{\n    hh::indexed_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, list, n_list, t0, n_steps, R);\n}\n",
              max_gates, precision);
     s += b;
     return s;
@@ -172,6 +177,7 @@ struct Entry {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t independent = nullptr;
     cudaKernel_t window = nullptr;
+    cudaKernel_t indexed = nullptr;
     std::string log;
 };
 
@@ -212,6 +218,8 @@ bool compile(const std::string& src, Entry* e, std::string* err)
         ce = cudaLibraryGetKernel(&e->independent, e->lib, "hh_jit_independent");
     if (ce == cudaSuccess)
         ce = cudaLibraryGetKernel(&e->window, e->lib, "hh_jit_window");
+    if (ce == cudaSuccess)
+        ce = cudaLibraryGetKernel(&e->indexed, e->lib, "hh_jit_indexed");
     if (ce != cudaSuccess) {
         *err = std::string("loading the specialised neuron kernels failed: ") + cudaGetErrorString(ce);
         return false;
@@ -257,6 +265,7 @@ bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernel
     }
     out->independent = it->second.independent;
     out->window = it->second.window;
+    out->indexed = it->second.indexed;
     return true;
 }
 
@@ -287,6 +296,20 @@ cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_
     SpikeList l = L;
     void* args[] = {&p, &t, &w, &I_steps, &r, &l, &par};
     return cudaLaunchKernel((const void*)K.window, grid, block, args, 0, st);
+}
+
+cudaError_t jit_launch_indexed(const JitKernels& K, const NeuronParams& P, const int32_t* list,
+                               const int32_t* n_list, int64_t max_list, int64_t t0, int32_t n_steps,
+                               const RecordParams& R, cudaStream_t st)
+{
+    const int bs = 128;
+    const dim3 grid((unsigned)((max_list + bs - 1) / bs)), block(bs);
+    long long t = t0;
+    int n = n_steps;
+    NeuronParams p = P;
+    RecordParams r = R;
+    void* args[] = {&p, &list, &n_list, &t, &n, &r};
+    return cudaLaunchKernel((const void*)K.indexed, grid, block, args, 0, st);
 }
 
 }  // namespace hh

@@ -29,7 +29,7 @@ HH_PREC_FAST, HH_PREC_ACCURATE, HH_PREC_COMPENSATED = 0, 1, 2
 HH_V_EXP_EULER, HH_V_FWD_EULER = 0, 1
 HH_KERNELS_SPECIALISED, HH_KERNELS_TABLE = 0, 1
 (HH_READ_V, HH_READ_GATES, HH_READ_CA, HH_READ_G_SYN, HH_READ_STATUS, HH_READ_TIME,
- HH_READ_N_OUT, HH_READ_PROFILE) = range(8)
+ HH_READ_N_OUT, HH_READ_PROFILE, HH_READ_SURROGATE) = range(9)
 HH_KERNEL_NEURON, HH_KERNEL_ROUTE, HH_KERNEL_COUNT = 0, 1, 2
 HH_STATUS_SPIKE_OVERFLOW, HH_STATUS_NONFINITE = 1, 2
 
@@ -88,6 +88,18 @@ class hh_neurons_noalloc(C.Structure):
 HH_NOALLOC_MAX_NEURONS = 1 << 20
 
 
+class hh_surrogate_desc(C.Structure):
+    _fields_ = [("window", C.c_int32), ("v_envelope", C.c_float), ("train_neurons", C.c_int32),
+                ("train_windows", C.c_int32), ("epochs", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_float), ("seed", C.c_uint64), ("I_min", C.c_float), ("I_max", C.c_float),
+                ("gbar_sigma", C.c_float), ("V0_min", C.c_float), ("V0_max", C.c_float)]
+
+
+class hh_surrogate_report(C.Structure):
+    _fields_ = [("train_windows", C.c_int64), ("train_loss", C.c_float), ("val_loss", C.c_float),
+                ("out_scale_V", C.c_float)]
+
+
 class hh_layer_desc(C.Structure):
     _fields_ = [("batch", C.c_int32), ("n_in", C.c_int32), ("n_hidden", C.c_int32),
                 ("n_out", C.c_int32), ("n_steps", C.c_int32), ("substeps", C.c_int32),
@@ -117,7 +129,8 @@ class hh_record(C.Structure):
 EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_route_spikes",
            "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
-           "hh_layer_forward", "hh_backward", "hh_layer_readout", "hh_layer_destroy"]
+           "hh_layer_forward", "hh_backward", "hh_layer_readout", "hh_layer_destroy",
+           "hh_surrogate_train", "hh_surrogate_enable"]
 
 
 def lib_path() -> str:
@@ -154,6 +167,10 @@ def lib():
             L.hh_gemm_bf16.restype = C.c_int
             L.hh_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_int32, vp, vp]
+            L.hh_surrogate_train.restype = C.c_int
+            L.hh_surrogate_train.argtypes = [vp, P(hh_surrogate_desc), P(hh_surrogate_report)]
+            L.hh_surrogate_enable.restype = C.c_int
+            L.hh_surrogate_enable.argtypes = [vp, C.c_int32]
             L.hh_layer_create.restype = C.c_int
             L.hh_layer_create.argtypes = [P(hh_layer_desc), P(hh_model_desc), P(vp)]
             L.hh_layer_set_weights.restype = C.c_int
@@ -367,6 +384,24 @@ class Network:
         out = np.zeros(n, dtype=dt)
         hh_readout(self.handle, what, out.ctypes.data, out.nbytes)
         return out
+
+    def train_surrogate(self, window=10, v_envelope=-55.0, train_neurons=16384, train_windows=1_000_000,
+                        epochs=40, batch=8192, lr=2e-3, seed=0, I_min=0.0, I_max=15.0, gbar_sigma=0.3,
+                        V0_min=-80.0, V0_max=-55.0):
+        d = hh_surrogate_desc(window, v_envelope, train_neurons, train_windows, epochs, batch, lr, seed,
+                              I_min, I_max, gbar_sigma, V0_min, V0_max)
+        r = hh_surrogate_report()
+        _check(lib().hh_surrogate_train(self.handle, C.byref(d), C.byref(r)))
+        return {"train_windows": r.train_windows, "train_loss": r.train_loss, "val_loss": r.val_loss,
+                "out_scale_V": r.out_scale_V}
+
+    def enable_surrogate(self, enable: bool):
+        _check(lib().hh_surrogate_enable(self.handle, 1 if enable else 0))
+
+    def surrogate_stats(self):
+        out = np.zeros(2, dtype=np.uint64)
+        hh_readout(self.handle, HH_READ_SURROGATE, out.ctypes.data, out.nbytes)
+        return int(out[0]), int(out[1])
 
     def profile(self, enable: bool):
         hh_profile(self.handle, enable)
