@@ -245,18 +245,47 @@ def run_gpu(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = float(W["n"]) * STEPS_PER_SIM * e2e_steps * world / float(te.item())
 
+    # the same network as one cooperative launch per step (comparison)
+    persistent_ms = None
+    if rank == 0 and not args.no_extras:
+        net2 = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
+                          delay_steps=DELAY, bg=BG, seed=W["seed"] + rank, precision=hh.HH_PREC_FAST,
+                          stream=stream.cuda_stream, kernels=hh.HH_KERNELS_PERSISTENT)
+        net2.set_channels(0, inp.CLASSIC_HH)
+
+        def step2():
+            with torch.cuda.stream(stream):
+                buf["counts"].zero_()
+                buf["n_spikes"].zero_()
+            net2.reset(V0_dev)
+            net2.step(STEPS_PER_SIM, rec=rec)
+
+        step2()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(2):
+            step2()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        persistent_ms = f0.elapsed_time(f1) / 2
+        net2.close()
+
     if rank == 0:
         pk, pk_kind = peaks()
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         n_launch_neuron, neuron_ms = kt["neuron"]
         n_launch_route, route_ms = kt["route"]
         avg_neuron_ms = neuron_ms / max(1, n_launch_neuron)
-        steps_per_launch = DELAY
+        steps_per_launch = STEPS_PER_SIM / max(1, n_launch_neuron)
         mufu = mufu_ops_per_neuron_step(inp.CLASSIC_HH)
+        # one cooperative launch per call (routing inside it) or one neuron
+        # launch per window with routing launches beside it
+        dominant = ("hh_jit_persistent (whole step in one cooperative launch, routing between steps)"
+                    if n_launch_route == 0 else "hh_jit_window (k_net_window specialised by NVRTC)")
         achieved_gops = mufu * W["n"] * steps_per_launch / (avg_neuron_ms * 1e-3) / 1e9
         peak_gops = SM_COUNT * MUFU_PER_SM_CLK * sm_max * 1e6 / 1e9
         cpu = cpu_baseline_sample(cores=os.cpu_count()) if not args.no_cpu_baseline else None
-        windows = STEPS_PER_SIM // DELAY
         line = {
             "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
             "value": value, "unit": "neuron-steps/s", "n_gpus": world, "steps": args.steps,
@@ -267,7 +296,7 @@ def run_gpu(args):
             "status_bits": status,
             "e2e": {"value": e2e_value, "unit": "neuron-steps/s",
                     "h2d_bytes_per_step": W["n"] * 4, "d2h_bytes_per_step": d2h},
-            "gpu_launches": (1 + 2 * windows) * args.steps * world,
+            "gpu_launches": (1 + n_launch_neuron + n_launch_route) * args.steps * world,
             "kernels": {"neuron_window": {"launches_per_step": n_launch_neuron,
                                           "avg_us": avg_neuron_ms * 1e3,
                                           "share_of_step": neuron_ms / max(1e-9, neuron_ms + route_ms)},
@@ -278,13 +307,16 @@ def run_gpu(args):
                          "frac": achieved_gops / peak_gops, "traffic": None,
                          "peak_source": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} SFU ops/clk x "
                                         f"{sm_max:.0f} MHz ({pk_kind} sm_max)",
-                         "ops_per_neuron_step": mufu, "kernel": "hh_jit_window (k_net_window specialised by NVRTC)"},
+                         "ops_per_neuron_step": mufu, "kernel": dominant},
             "clocks": clk,
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
         if not args.no_extras:
             line["extra"] = extras(dev, pk)
+            line["extra"]["network_persistent_cooperative"] = {
+                "ms_per_step": persistent_ms,
+                "neuron_steps_per_s": float(W["n"]) * STEPS_PER_SIM / (persistent_ms * 1e-3)}
         print(json.dumps(line), flush=True)
     net.close()
     if world > 1:
@@ -428,9 +460,12 @@ def run_reference(args):
 
 def ncu_case(name):
     """Small fixed cases for ncu captures.
-    network: the benchmark network, 120 time steps (three delay windows),
-             then one open-loop routing launch of a 40-step raster with 1% of
-             the neurons spiking per step;
+    network: the benchmark network, 120 time steps (six 20-step windows,
+             one neuron and one routing launch each), then one open-loop
+             routing launch of a 40-step raster with 1% of the neurons
+             spiking per step;
+    network-persistent: the same with the 120 steps in one cooperative
+             launch;
     gemm:    the layer's input projection (32000 x 1024 x 704, bf16) twice;
     layer:   the differentiable layer at full width (B=128, 700 inputs, 1,024
              neurons) for T=25 outer steps, forward and backward."""
@@ -467,8 +502,9 @@ def ncu_case(name):
         return
     g = inp.network(n=W["n"], k_in=W["k_in"], exc_frac=W["exc_frac"], seed=W["seed"],
                     mu=W["mu"], sigma=W["sigma"])
+    kernels = hh.HH_KERNELS_PERSISTENT if name == "network-persistent" else hh.HH_KERNELS_SPECIALISED
     net = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
-                     delay_steps=DELAY, bg=BG, seed=W["seed"], precision=hh.HH_PREC_FAST)
+                     delay_steps=DELAY, bg=BG, seed=W["seed"], precision=hh.HH_PREC_FAST, kernels=kernels)
     net.set_channels(0, inp.CLASSIC_HH)
     rec, b = hh.make_record(W["n"], 3 * DELAY, spike_cap=100_000)
     net.step(3 * DELAY, rec=rec)
@@ -493,7 +529,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (single neurons, BPTT layer, 1e6 neurons, GEMM)")
     ap.add_argument("--ncu-case", nargs="?", const="network", default=None,
-                    choices=["network", "gemm", "layer"],
+                    choices=["network", "network-persistent", "gemm", "layer"],
                     help="run a small fixed case used for ncu captures and exit")
     args = ap.parse_args()
     if args.ncu_case:

@@ -142,12 +142,26 @@ enum { HH_V_EXP_EULER = 0, HH_V_FWD_EULER = 1 };
  *                           the first hh_step_n after hh_set_channels (the
  *                           model table becomes compile-time constants;
  *                           about a second per new model set, cached for the
- *                           life of the process);
+ *                           life of the process).  A network runs one neuron
+ *                           launch per window of delay_steps/2 steps (D >= 2)
+ *                           and routes each window on a second stream while
+ *                           the next one integrates;
  *   HH_KERNELS_TABLE        precompiled kernels that read the model table at
- *                           run time (no compilation; slower per step).
- * Both run the same device code and give the same results up to the
- * compiler's instruction selection (FMA contraction).                     */
-enum { HH_KERNELS_SPECIALISED = 0, HH_KERNELS_TABLE = 1 };
+ *                           run time (no compilation; slower per step), one
+ *                           window of delay_steps steps per launch;
+ *   HH_KERNELS_PERSISTENT   the compiled kernels of HH_KERNELS_SPECIALISED,
+ *                           but a network with synapses and delay_steps >= 2
+ *                           whose neurons fit on the GPU at once (128 per
+ *                           block, with 4 routing warps each) runs a whole
+ *                           hh_step_n call as ONE cooperative launch: the
+ *                           routing warps deliver window w - 1 while the
+ *                           neuron threads integrate window w, ordered by
+ *                           device-side progress counters instead of launch
+ *                           boundaries.  Otherwise as HH_KERNELS_SPECIALISED.
+ * All run the same device code and give the same results up to the
+ * compiler's instruction selection (FMA contraction); SPECIALISED and
+ * PERSISTENT give bit-identical results.                                  */
+enum { HH_KERNELS_SPECIALISED = 0, HH_KERNELS_TABLE = 1, HH_KERNELS_PERSISTENT = 2 };
 
 typedef struct {
     int64_t n_neurons;          /* N >= 1 (all networks together)            */
@@ -440,7 +454,7 @@ enum {
     HH_READ_PROFILE = 7, /* hh_kernel_time [HH_KERNEL_COUNT] since hh_profile(net, 1) */
     HH_READ_SURROGATE = 8 /* uint64 [2]: neuron-windows taken from the surrogate, declined */
 };
-enum { HH_STATUS_SPIKE_OVERFLOW = 1, HH_STATUS_NONFINITE = 2 };
+enum { HH_STATUS_SPIKE_OVERFLOW = 1, HH_STATUS_NONFINITE = 2, HH_STATUS_BARRIER_TIMEOUT = 4 };
 
 /* Copy a quantity into dst (any memory) of cap_bytes bytes; *n_bytes (if
  * not NULL) receives the bytes written.  Synchronous: waits for the work

@@ -71,6 +71,7 @@ struct hh_net {
     float* out_w = nullptr;
     int64_t *ringE = nullptr, *ringI = nullptr;
     int32_t D = 1, R = 1;
+    int32_t route_segs = 1;  // most 256-synapse segments in one out-CSR row
     float tau_E = 1.0f, tau_I = 1.0f, E_E = 0.0f, E_I = 0.0f, area = 1.0f;
 
     // background
@@ -81,6 +82,13 @@ struct hh_net {
     unsigned long long thr[hh::kMaxPoisson] = {};
 
     hh::SpikeList list{};
+    // routing stream and events of the pipelined window schedule
+    cudaStream_t st_route = nullptr;
+    cudaEvent_t ev_neuron[hh::kListSlots] = {};
+    cudaEvent_t ev_route[hh::kListSlots] = {};
+    int32_t W_pipe = 0;  // window length when routing overlaps the next window (0: serial)
+    unsigned long long* progress = nullptr;  // persistent kernel: done[4], routed[4]
+    int persistent_cap = -1;      // co-resident blocks of the persistent kernel (-1: not queried)
 
     // learned surrogate
     hh::Surrogate* sur = nullptr;
@@ -155,6 +163,17 @@ struct hh_net {
         for (cudaEvent_t e : ev_pool)
             cudaEventDestroy(e);
         ev_pool.clear();
+        for (int k = 0; k < hh::kListSlots; ++k) {
+            if (ev_neuron[k])
+                cudaEventDestroy(ev_neuron[k]);
+            if (ev_route[k])
+                cudaEventDestroy(ev_route[k]);
+            ev_neuron[k] = ev_route[k] = nullptr;
+        }
+        if (st_route) {
+            cudaStreamDestroy(st_route);
+            st_route = nullptr;
+        }
     }
 
     hh::NeuronParams neuron_params() const
@@ -184,11 +203,16 @@ struct hh_net {
         p.decE = (float)std::exp(-dt / (double)tau_E);
         p.decI = (float)std::exp(-dt / (double)tau_I);
         p.to_mS = (float)(1e-6 / (double)area);
-        p.bg_n = has_bg ? n_thr : 0;
+        // the table ends with 2^32, which no 32-bit word reaches: keep the
+        // entries below it
+        int32_t nb = 0;
+        while (has_bg && nb < n_thr && thr[nb] < (1ull << 32))
+            ++nb;
+        p.bg_n = nb;
         p.bg_w = bg_w;
         p.seed = seed;
         for (int j = 0; j < hh::kMaxPoisson; ++j)
-            p.bg_thr[j] = thr[j];
+            p.bg_thr[j] = thr[j] < (1ull << 32) ? (uint32_t)thr[j] : 0xffffffffu;
         return p;
     }
 
@@ -206,6 +230,7 @@ struct hh_net {
         r.D = D;
         r.open_loop = 0;
         r.n_window = 0;
+        r.segs = route_segs;
         return r;
     }
 };
@@ -503,8 +528,13 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
                 break;
             }
             op[0] = 0;
-            for (int64_t j = 0; j < N; ++j)
+            int32_t max_out = 0;
+            for (int64_t j = 0; j < N; ++j) {
                 op[j + 1] = op[j] + hc[j];
+                max_out = hc[j] > max_out ? hc[j] : max_out;
+            }
+            // 256-synapse segments per row, counted from the row start rounded down to 4
+            n->route_segs = (max_out + 3 + 255) / 256;
             // 4 entries of padding: the routing kernel reads rows as aligned int4/float4
             if ((e = n->alloc(&n->out_ptr, N + 1)) != cudaSuccess ||
                 (e = n->alloc(&n->out_post, S + 4)) != cudaSuccess ||
@@ -551,13 +581,35 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
         HH_CUDA(cudaMemsetAsync(n->ringI, 0, (size_t)n->R * N * sizeof(int64_t), st));
         const int64_t W = n->has_syn ? n->D : 1;
         n->list.cap = N * ((W + 1) / 2) + 32;
-        HH_CUDA(n->alloc(&n->list.step, n->list.cap));
-        HH_CUDA(n->alloc(&n->list.idx, n->list.cap));
-        HH_CUDA(n->alloc(&n->list.counter, 2));
-        HH_CUDA(cudaMemsetAsync(n->list.counter, 0, 2 * sizeof(int32_t), st));
+        HH_CUDA(n->alloc(&n->list.step, (size_t)hh::kListSlots * n->list.cap));
+        HH_CUDA(n->alloc(&n->list.idx, (size_t)hh::kListSlots * n->list.cap));
+        HH_CUDA(n->alloc(&n->list.counter, hh::kListSlots));
+        HH_CUDA(cudaMemsetAsync(n->list.counter, 0, hh::kListSlots * sizeof(int32_t), st));
+        if (n->has_syn && n->D >= 2) {
+            // windows of W <= D/2 steps: the spikes of window w arrive in window
+            // w + 2 at the earliest, so routing window w may overlap window w + 1
+            n->W_pipe = n->D / 2;
+            int lo = 0, hi = 0;
+            HH_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            HH_CUDA(cudaStreamCreateWithPriority(&n->st_route, cudaStreamNonBlocking, lo));
+            for (int k = 0; k < hh::kListSlots; ++k) {
+                HH_CUDA(cudaEventCreateWithFlags(&n->ev_neuron[k], cudaEventDisableTiming));
+                HH_CUDA(cudaEventCreateWithFlags(&n->ev_route[k], cudaEventDisableTiming));
+            }
+            HH_CUDA(n->alloc(&n->progress, 2 * hh::kPhaseSlots));
+        }
     }
     HH_CUDA(cudaStreamSynchronize(st));
     return HH_OK;
+}
+
+// Blocks of the persistent kernel that fit on the GPU at once (queried once
+// per compiled kernel set).
+int persistent_capacity(hh_net* n)
+{
+    if (n->persistent_cap < 0)
+        n->persistent_cap = hh::jit_persistent_capacity(n->jit);
+    return n->persistent_cap;
 }
 
 int max_gates_installed(const hh_net* n)
@@ -599,7 +651,8 @@ hh_status hh_create_network(const hh_net_desc* d, hh_net** out)
         return fail(HH_EINVAL, "unknown v_update %d", d->v_update);
     if (d->precision < HH_PREC_FAST || d->precision > HH_PREC_COMPENSATED)
         return fail(HH_EINVAL, "unknown precision %d", d->precision);
-    if (d->kernels != HH_KERNELS_SPECIALISED && d->kernels != HH_KERNELS_TABLE)
+    if (d->kernels != HH_KERNELS_SPECIALISED && d->kernels != HH_KERNELS_TABLE &&
+        d->kernels != HH_KERNELS_PERSISTENT)
         return fail(HH_EINVAL, "unknown kernels %d", d->kernels);
     if (!d->V0)
         return fail(HH_EINVAL, "V0 is required");
@@ -701,31 +754,33 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         p.trace_slot = net->trace_slot;
     }
     // optional event bracketing of each launch (hh_profile)
-    auto timed = [&](int kind, auto&& launch) -> cudaError_t {
+    auto timed_on = [&](cudaStream_t s, int kind, auto&& launch) -> cudaError_t {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (net->profiling) {
             e0 = net->take_event();
             e1 = net->take_event();
             if (!e0 || !e1)
                 return cudaErrorMemoryAllocation;
-            cudaError_t e = cudaEventRecord(e0, net->st);
+            cudaError_t e = cudaEventRecord(e0, s);
             if (e != cudaSuccess)
                 return e;
         }
         cudaError_t e = launch();
         if (e != cudaSuccess || !net->profiling)
             return e;
-        e = cudaEventRecord(e1, net->st);
+        e = cudaEventRecord(e1, s);
         net->ev_used.push_back({kind, {e0, e1}});
         return e;
     };
-    if (net->kernels == HH_KERNELS_SPECIALISED && !net->jit_ready) {
+    auto timed = [&](int kind, auto&& launch) -> cudaError_t { return timed_on(net->st, kind, launch); };
+    const bool spec = net->kernels != HH_KERNELS_TABLE;
+    if (spec && !net->jit_ready) {
         std::string err;
         if (!hh::jit_get(net->models, net->installed, net->precision, &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
+        net->persistent_cap = -1;
     }
-    const bool spec = net->kernels == HH_KERNELS_SPECIALISED;
     if (net->sur_on) {
         if (R.V_trace)
             return fail(HH_EUNSUPPORTED, "V traces are not recorded while the surrogate is enabled");
@@ -759,29 +814,59 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         else
         HH_CUDA(timed(HH_KERNEL_NEURON, [&] { return hh::launch_independent(net->models, p, net->precision, net->t, n_steps, I_steps, R,
                                        net->st); }));
+    } else if (net->kernels == HH_KERNELS_PERSISTENT && net->W_pipe > 0 &&
+               (int64_t)persistent_capacity(net) * hh::kPersistNeurons >= net->N) {
+        // one cooperative launch for the whole call
+        const hh::RouteParams rp = net->route_params();
+        const int32_t W = net->W_pipe;
+        const int64_t n_win = (n_steps + W - 1) / W;
+        HH_CUDA(cudaMemsetAsync(net->progress, 0, 2 * hh::kPhaseSlots * sizeof(unsigned long long), net->st));
+        HH_CUDA(cudaMemsetAsync(net->list.counter, 0, hh::kListSlots * sizeof(int32_t), net->st));
+        const hh::PhaseCounters pc{net->progress, net->progress + hh::kPhaseSlots};
+        HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
+            return hh::jit_launch_persistent(net->jit, p, rp, net->t, n_steps, W, net->window_index, I_steps, R,
+                                             net->list, pc, net->st);
+        }));
+        net->window_index += n_win;
     } else {
         const hh::RouteParams rp = net->route_params();
-        const int32_t Wmax = net->has_syn ? net->D : (1 << 30);
+        const bool pipe = net->W_pipe > 0;
+        const int32_t Wmax = net->has_syn ? (pipe ? net->W_pipe : net->D) : (1 << 30);
+        int64_t last_route = -1;
         for (int32_t w0 = 0; w0 < n_steps; w0 += Wmax) {
             const int32_t W = (n_steps - w0) < Wmax ? (n_steps - w0) : Wmax;
-            const int32_t parity = (int32_t)(net->window_index & 1);
+            const int64_t gw = net->window_index;
+            const int32_t slot = (int32_t)(gw % hh::kListSlots);
             hh::RecordParams Rw = R;
             if (Rw.V_trace)
                 Rw.V_trace += (int64_t)w0 * Rw.n_trace;
             const float* Iw = I_steps ? I_steps + (int64_t)w0 * net->N : nullptr;
+            // the input of this window was routed by window gw - 2
+            if (pipe && gw >= 2)
+                HH_CUDA(cudaStreamWaitEvent(net->st, net->ev_route[(gw - 2) % hh::kListSlots], 0));
             HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
                 if (spec)
-                    return hh::jit_launch_window(net->jit, p, net->t + w0, W, parity, Iw, Rw, net->list,
-                                                 net->st);
-                return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, parity, Iw,
-                                             Rw, net->list, net->st);
+                    return hh::jit_launch_window(net->jit, p, net->t + w0, W, slot, Iw, Rw, net->list, net->st);
+                return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, slot, Iw, Rw,
+                                             net->list, net->st);
             }));
-            if (net->has_syn)
-                HH_CUDA(timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, parity, net->st); }));
-            else
-                HH_CUDA(cudaMemsetAsync(net->list.counter + parity, 0, sizeof(int32_t), net->st));
+            if (net->has_syn && pipe) {
+                HH_CUDA(cudaEventRecord(net->ev_neuron[slot], net->st));
+                HH_CUDA(cudaStreamWaitEvent(net->st_route, net->ev_neuron[slot], 0));
+                HH_CUDA(timed_on(net->st_route, HH_KERNEL_ROUTE,
+                                 [&] { return hh::launch_route_window(rp, net->list, slot, net->st_route); }));
+                HH_CUDA(cudaEventRecord(net->ev_route[slot], net->st_route));
+                last_route = gw;
+            } else if (net->has_syn) {
+                HH_CUDA(timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, slot, net->st); }));
+            } else {
+                HH_CUDA(cudaMemsetAsync(net->list.counter + slot, 0, sizeof(int32_t), net->st));
+            }
             net->window_index++;
         }
+        // the caller's stream sees every routing launch of this call complete
+        if (last_route >= 0)
+            HH_CUDA(cudaStreamWaitEvent(net->st, net->ev_route[last_route % hh::kListSlots], 0));
     }
     net->t += n_steps;
     return HH_OK;
@@ -802,7 +887,7 @@ hh_status hh_reset(hh_net* net, const float* V0)
     if (net->ringE) {
         HH_CUDA(cudaMemsetAsync(net->ringE, 0, (size_t)net->R * net->N * sizeof(int64_t), st));
         HH_CUDA(cudaMemsetAsync(net->ringI, 0, (size_t)net->R * net->N * sizeof(int64_t), st));
-        HH_CUDA(cudaMemsetAsync(net->list.counter, 0, 2 * sizeof(int32_t), st));
+        HH_CUDA(cudaMemsetAsync(net->list.counter, 0, hh::kListSlots * sizeof(int32_t), st));
     }
     net->t = 0;
     net->window_index = 0;

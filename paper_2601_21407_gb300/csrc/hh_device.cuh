@@ -97,11 +97,15 @@ struct NeuronParams {
     int32_t R;        // ring slots (= delay steps)
     float E_E, E_I, decE, decI, to_mS;
     // background
-    int32_t bg_n;     // number of thresholds (0 = off)
+    int32_t bg_n;     // thresholds below 2^32 (0 = off); the count of a step is
+                      // #{j < bg_n : word >= bg_thr[j]} (nondecreasing table)
     float bg_w;
     uint64_t seed;
-    unsigned long long bg_thr[kMaxPoisson];
+    uint32_t bg_thr[kMaxPoisson];
 };
+// thresholds compared without a loop on every step (the rest only after a
+// word that passes all of them)
+constexpr int kPoissonUnroll = 4;
 
 struct RecordParams {
     float* V_trace;
@@ -112,11 +116,29 @@ struct RecordParams {
     int32_t* counts;
 };
 
-// Window spike list used between the neuron and the routing kernels.
+// Synaptic routing over the out-CSR (rows = presynaptic neuron).
+struct RouteParams {
+    int64_t N;
+    const int64_t* out_ptr;
+    const int32_t* out_post;
+    const float* out_w;
+    const uint8_t* inh;
+    int64_t* ringE;
+    int64_t* ringI;
+    int32_t R;         // slots in the destination (ring: R = D; open loop: unused)
+    int32_t D;
+    int32_t open_loop; // 1: destination is [n_window][N] linear, drop >= n_window
+    int32_t n_window;
+    int32_t segs;      // most 256-synapse segments of a row (route_items)
+};
+// Window spike lists used between the neuron and the routing kernels: three
+// slots (window index mod 3) so that a window's list can be routed while the
+// next window's neurons append to another slot.
+constexpr int kListSlots = 3;
 struct SpikeList {
-    int32_t* step;
-    int32_t* idx;
-    int32_t* counter;   // [2] alternating per window
+    int32_t* step;      // [kListSlots][cap]
+    int32_t* idx;       // [kListSlots][cap]
+    int32_t* counter;   // [kListSlots]
     int64_t cap;
 };
 
@@ -174,15 +196,14 @@ __device__ __forceinline__ float rate(const DevFn& f, float V)
         // a x / (1 - e^{-x/k}) = a k * y/(1 - e^{-y}), y = x/k.  Near y = 0 the
         // SFU path uses the Bernoulli series 1 + y/2 + y^2/12 - y^4/720
         // (truncation < 1e-10 for |y| < 0.1); the accurate path uses expm1f.
+        // Both branches are evaluated and one selected (no divergent branch).
         const float x = V - f.vh;
         if (FAST) {
             const float y = x * f.ik;
-            if (fabsf(y) < 0.1f) {
-                const float y2 = y * y;
-                r = f.a * f.k * (1.0f + 0.5f * y + y2 * (1.0f / 12.0f - y2 * (1.0f / 720.0f)));
-            } else {
-                r = f.a * x * rcpa(1.0f - ex2a(-y * kLog2e));
-            }
+            const float y2 = y * y;
+            const float near0 = f.a * f.k * (1.0f + 0.5f * y + y2 * (1.0f / 12.0f - y2 * (1.0f / 720.0f)));
+            const float far = f.a * x * rcpa(1.0f - ex2a(-y * kLog2e));
+            r = fabsf(y) < 0.1f ? near0 : far;
         } else {
             r = (x == 0.0f) ? f.a * f.k : f.a * x / (-expm1f(-x * f.ik));
         }
@@ -222,21 +243,20 @@ __device__ __forceinline__ void gate_inf_z(const DevGate& g, float V, float Ca, 
 // relaxation rate exact to rounding even when z is small, where
 // p_inf + (p - p_inf) e^{-z} would turn the absolute error of e^{-z} near 1
 // into a relative error of order ulp/z on every step.
+// The SFU path evaluates both forms and selects one (no divergent branch).
 template <bool FAST>
 __device__ __forceinline__ float em1(float z)
 {
     if (FAST) {
-        if (z < 0.5f) {
-            float c = fmaf(z, -1.0f / 40320.0f, 1.0f / 5040.0f);
-            c = fmaf(z, c, -1.0f / 720.0f);
-            c = fmaf(z, c, 1.0f / 120.0f);
-            c = fmaf(z, c, -1.0f / 24.0f);
-            c = fmaf(z, c, 1.0f / 6.0f);
-            c = fmaf(z, c, -0.5f);
-            c = fmaf(z, c, 1.0f);
-            return z * c;
-        }
-        return 1.0f - ex2a(-z * kLog2e);
+        // c(z) = sum_{j<8} (-z)^j/(j+1)! by Estrin's scheme (dependency depth 4)
+        const float z2 = z * z;
+        const float a0 = fmaf(z, -0.5f, 1.0f);
+        const float a1 = fmaf(z, -1.0f / 24.0f, 1.0f / 6.0f);
+        const float a2 = fmaf(z, -1.0f / 720.0f, 1.0f / 120.0f);
+        const float a3 = fmaf(z, -1.0f / 40320.0f, 1.0f / 5040.0f);
+        const float c = fmaf(z2 * z2, fmaf(z2, a3, a2), fmaf(z2, a1, a0));
+        const float far = 1.0f - ex2a(-z * kLog2e);
+        return z < 0.5f ? z * c : far;
     }
     return -expm1f(-z);
 }
@@ -359,11 +379,10 @@ __device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_u
     // I_ion = sum g (V - E) formed term by term (no cancellation near rest);
     // or explicit Euler dV = dt/C (I - I_ion).
     const float Iion = PREC == HH_PREC_COMPENSATED ? Ip + G * s.Vlo : Ip;
-    float dV;
-    if (v_update == HH_V_EXP_EULER)
-        dV = Mt::div(I - Iion, G) * em1<FAST>(dt * G * M.inv_C);
-    else
-        dV = dt * M.inv_C * (I - Iion);
+    // (both forms evaluated, one selected: no branch inside the step)
+    const float dV_exp = Mt::div(I - Iion, G) * em1<FAST>(dt * G * M.inv_C);
+    const float dV_euler = dt * M.inv_C * (I - Iion);
+    const float dV = v_update == HH_V_EXP_EULER ? dV_exp : dV_euler;
     if (PREC == HH_PREC_COMPENSATED)
         two_sum_add(s.V, s.Vlo, dV);
     else
@@ -405,8 +424,9 @@ __device__ __forceinline__ void store_state(const NeuronParams& P, int64_t i, co
 
 // Warp-aggregated append of this step's spikes to the caller's record:
 // one atomic per warp (ballot + popc), each spiking lane writes its slot.
-__device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t idx, float frac,
-                                              const RecordParams& R, int32_t* status)
+// frac = (theta - Vt)/(V - Vt) is formed only by lanes that spiked.
+__device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t idx, float theta, float Vt,
+                                              float V, const RecordParams& R, int32_t* status)
 {
     const unsigned b = __ballot_sync(kFull, spk);
     if (b == 0u || R.n_spikes == nullptr)
@@ -423,7 +443,7 @@ __device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t id
             hh_spike e;
             e.step = step;
             e.neuron = idx;
-            e.frac = frac;
+            e.frac = (theta - Vt) / (V - Vt);
             R.spikes[pos] = e;
         } else {
             atomicOr(status, HH_STATUS_SPIKE_OVERFLOW);
@@ -471,6 +491,130 @@ __device__ __forceinline__ uint32_t pick(const uint4& v, int w)
     return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
+// w (nS, finite, 0 <= w < 65536) as a 64-bit fixed-point count of 2^-32 nS,
+// from the float's bits with integer operations only (the 64-bit float ->
+// integer conversion executes on the FP64 unit).  Exact for w >= 2^-9 nS;
+// below, rounded to nearest with ties up.
+__device__ __forceinline__ unsigned long long nS_to_fixed(float w)
+{
+    const unsigned b = __float_as_uint(w);
+    const int e = (int)(b >> 23);
+    const unsigned m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int sh = (e ? e : 1) - 118;  // w 2^32 = m 2^(e - 150 + 32)
+    if (sh >= 0)
+        return (unsigned long long)m << sh;
+    if (sh < -40)
+        return 0ull;
+    return ((unsigned long long)m + (1ull << (-sh - 1))) >> (-sh);
+}
+
+// Spike routing: one warp per spike.  The out-row is walked in 128-edge
+// chunks aligned to 4 edges: lane l reads the int4 of targets and the float4
+// of weights at chunk + 4l (the arrays carry 4 entries of padding), masks the
+// entries outside the row and issues one RED.ADD.64 per edge.  Two chunks
+// are in flight per iteration.  Warps `warp`, `warp + nw`, ... take spikes
+// `warp`, `warp + nw`, ... of the list.
+__device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_t* __restrict__ st,
+                                             const int32_t* __restrict__ ix, int64_t n, int64_t warp, int64_t nw)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t sp = warp; sp < n; sp += nw) {
+        const int32_t j = __ldcg(ix + sp);
+        const int32_t t = __ldcg(st + sp);
+        if (j < 0 || j >= RP.N || t < 0)
+            continue;
+        int64_t row;
+        if (RP.open_loop) {
+            row = (int64_t)t + RP.D;
+            if (row >= RP.n_window)
+                continue;
+        } else {
+            row = ((int64_t)t + RP.D) % RP.R;
+        }
+        unsigned long long* dst =
+            reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
+        const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
+        for (int64_t base = (e0 & ~(int64_t)3); base < e1; base += 256) {
+            const int64_t ea = base + 4 * lane;
+            const int64_t eb = ea + 128;
+            int4 pa = make_int4(0, 0, 0, 0), pb = pa;
+            float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
+            if (ea < e1) {
+                pa = *reinterpret_cast<const int4*>(RP.out_post + ea);
+                wa = *reinterpret_cast<const float4*>(RP.out_w + ea);
+            }
+            if (eb < e1) {
+                pb = *reinterpret_cast<const int4*>(RP.out_post + eb);
+                wb = *reinterpret_cast<const float4*>(RP.out_w + eb);
+            }
+            const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+            const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t e = (q < 4 ? ea : eb) + (q & 3);
+                if (e >= e0 && e < e1)
+                    atomicAdd(dst + pp[q], nS_to_fixed(ww[q]));
+            }
+        }
+    }
+}
+
+// The same delivery split into items of (spike, 256-synapse segment): item
+// x is segment x mod segs of spike x / segs (segments past the row's end are
+// empty).  Warp r of nR takes items r, r + nR, ...; the split keeps one
+// spike's fan-out from serialising on a single warp.
+__device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t* __restrict__ st,
+                                            const int32_t* __restrict__ ix, int64_t n, int64_t r, int64_t nR)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t S = RP.segs;
+    if (S < 1 || r >= n * S)
+        return;
+    int64_t sp = r / S;
+    int32_t q = (int32_t)(r - sp * S);
+    const int64_t dsp = nR / S;
+    const int32_t dq = (int32_t)(nR - dsp * S);
+    for (; sp < n;) {
+        const int32_t j = __ldcg(ix + sp);
+        const int32_t t = __ldcg(st + sp);
+        if (j >= 0 && j < RP.N && t >= 0) {
+            const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
+            const int64_t base = (e0 & ~(int64_t)3) + 256 * (int64_t)q;
+            const int64_t row = RP.open_loop ? (int64_t)t + RP.D : ((int64_t)t + RP.D) % RP.R;
+            if (base < e1 && (!RP.open_loop || row < RP.n_window)) {
+                unsigned long long* dst = reinterpret_cast<unsigned long long*>(
+                    (RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
+                const int64_t ea = base + 4 * lane;
+                const int64_t eb = ea + 128;
+                int4 pa = make_int4(0, 0, 0, 0), pb = pa;
+                float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
+                if (ea < e1) {
+                    pa = *reinterpret_cast<const int4*>(RP.out_post + ea);
+                    wa = *reinterpret_cast<const float4*>(RP.out_w + ea);
+                }
+                if (eb < e1) {
+                    pb = *reinterpret_cast<const int4*>(RP.out_post + eb);
+                    wb = *reinterpret_cast<const float4*>(RP.out_w + eb);
+                }
+                const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+                const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int64_t e = (k < 4 ? ea : eb) + (k & 3);
+                    if (e >= e0 && e < e1)
+                        atomicAdd(dst + pp[k], nS_to_fixed(ww[k]));
+                }
+            }
+        }
+        sp += dsp;
+        q += dq;
+        if (q >= S) {
+            q -= S;
+            ++sp;
+        }
+    }
+}
+
 // -------------------------------------------------------------------------
 // Kernel bodies.  `Dyn` supplies the neuron model(s):
 //   dyn.template load<MAXG, PREC>(mid, P, i, s)  per-neuron conductances
@@ -506,8 +650,7 @@ __device__ __forceinline__ void independent_body(const Dyn& dyn, const NeuronPar
         dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
         cnt += spk;
-        const float frac = spk ? (P.theta - Vt) / (s.V - Vt) : 0.0f;
-        record_spikes(spk, (int32_t)(t0 + k), (int32_t)i, frac, R, P.status);
+        record_spikes(spk, (int32_t)(t0 + k), (int32_t)i, P.theta, Vt, s.V, R, P.status);
         if (slot >= 0)
             R.V_trace[(int64_t)k * R.n_trace + slot] = s.V;
     }
@@ -544,8 +687,7 @@ __device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams&
         dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, Ic, 0.0f, 0.0f, 0.0f, 0.0f, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
         cnt += spk;
-        const float frac = spk ? (P.theta - Vt) / (s.V - Vt) : 0.0f;
-        record_spikes(spk, (int32_t)(t0 + k), (int32_t)i, frac, R, P.status);
+        record_spikes(spk, (int32_t)(t0 + k), (int32_t)i, P.theta, Vt, s.V, R, P.status);
     }
     if (valid) {
         store_state(P, i, s);
@@ -553,6 +695,85 @@ __device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams&
             R.counts[i] += cnt;
         if (!finite(s.V))
             atomicOr(P.status, HH_STATUS_NONFINITE);
+    }
+}
+
+// W <= D time steps of one network neuron with its state in registers.
+// The delay-line slots of the window were completed by earlier routing;
+// they are read through L2 (.cg: they were written by atomics from other
+// blocks) one step ahead, and cleared after use.  Spikes go to list slot
+// `lslot` (and to the caller's record).
+// `between(k)` runs after step k with the whole warp (all lanes, valid or
+// not): the persistent kernel routes part of the previous window there.
+struct NoWork {
+    __device__ __forceinline__ void operator()(int32_t) const {}
+};
+template <int MAXG, int PREC, class Dyn, class Between>
+__device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
+                                             int64_t i, int64_t t0, int32_t W, const float* __restrict__ I_steps,
+                                             const RecordParams& R, float* V_trace, int32_t slot,
+                                             const SpikeList& L, int32_t lslot, State<MAXG, PREC>& s,
+                                             float& gE, float& gI, float Ic, int32_t& cnt, uint2 key,
+                                             const Between& between)
+{
+    uint4 rnd = make_uint4(0, 0, 0, 0);
+    int32_t ring_slot = (int32_t)(t0 % P.R);
+    long long nE = 0, nI = 0;
+    if (W > 0) {
+        nE = __ldcg(P.ringE + (int64_t)ring_slot * P.N + i);
+        nI = __ldcg(P.ringI + (int64_t)ring_slot * P.N + i);
+    }
+    int32_t* lstep = L.step + lslot * L.cap;
+    int32_t* lidx = L.idx + lslot * L.cap;
+    for (int32_t k = 0; k < W; ++k) {
+        const int64_t t = t0 + k;
+        const long long e = nE, h = nI;
+        const int32_t next_slot = ring_slot + 1 == P.R ? 0 : ring_slot + 1;
+        // prefetch of the next slot without a branch (after the last step it
+        // reads a slot of a later window and is discarded)
+        nE = __ldcg(P.ringE + (int64_t)next_slot * P.N + i);
+        nI = __ldcg(P.ringI + (int64_t)next_slot * P.N + i);
+        // a. delayed synaptic input (fixed point 2^-32 nS) and background
+        // (added unconditionally: + 0 changes no bit, and the step stays
+        // free of branches the scheduler cannot look across)
+        gE += fixed_to_nS(e);
+        gI += fixed_to_nS(h);
+        if (valid) {
+            const int64_t o = (int64_t)ring_slot * P.N + i;
+            if (e)
+                P.ringE[o] = 0;
+            if (h)
+                P.ringI[o] = 0;
+        }
+        if (P.bg_n > 0) {
+            if (k == 0 || (t & 3) == 0) {
+                const uint64_t q = (uint64_t)t >> 2;
+                rnd = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
+            }
+            const uint32_t u = pick(rnd, (int)(t & 3));
+            int32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < kPoissonUnroll; ++j)
+                c += (j < P.bg_n && u >= P.bg_thr[j]) ? 1 : 0;
+            if (c == kPoissonUnroll)
+                for (int j = kPoissonUnroll; j < P.bg_n && u >= P.bg_thr[j]; ++j)
+                    ++c;
+            gE += (float)c * P.bg_w;
+        }
+        const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
+        const float Vt = s.V;
+        dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, gE * P.to_mS, P.E_E, gI * P.to_mS,
+                                      P.E_I, s);
+        const bool spk = valid && Vt < P.theta && s.V >= P.theta;
+        cnt += spk;
+        list_append(spk, (int32_t)t, (int32_t)i, L.counter + lslot, lstep, lidx, L.cap);
+        record_spikes(spk, (int32_t)t, (int32_t)i, P.theta, Vt, s.V, R, P.status);
+        if (slot >= 0)
+            V_trace[(int64_t)k * R.n_trace + slot] = s.V;
+        gE *= P.decE;
+        gI *= P.decI;
+        ring_slot = next_slot;
+        between(k);
     }
 }
 
@@ -567,7 +788,7 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi == 0)
-        L.counter[parity ^ 1] = 0;  // the next window's list (its reader has finished)
+        L.counter[parity + 1 == kListSlots ? 0 : parity + 1] = 0;  // next window's slot (its reader has finished)
     const bool valid = gi < P.N;
     const int64_t i = valid ? gi : 0;
     const int mid = P.model_id ? P.model_id[i] : 0;
@@ -582,64 +803,9 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
     if (!valid)
         slot = -1;
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-    uint4 rnd = make_uint4(0, 0, 0, 0);
     int32_t cnt = 0;
-    int32_t ring_slot = (int32_t)(t0 % P.R);
-    // The delay-line slots of this window were completed by earlier routing
-    // launches: prefetch one step ahead so the L2 latency overlaps compute.
-    long long nE = 0, nI = 0;
-    if (valid && W > 0) {
-        nE = P.ringE[(int64_t)ring_slot * P.N + i];
-        nI = P.ringI[(int64_t)ring_slot * P.N + i];
-    }
-    for (int32_t k = 0; k < W; ++k) {
-        const int64_t t = t0 + k;
-        const long long e = nE, h = nI;
-        const int32_t next_slot = ring_slot + 1 == P.R ? 0 : ring_slot + 1;
-        if (valid && k + 1 < W) {
-            nE = P.ringE[(int64_t)next_slot * P.N + i];
-            nI = P.ringI[(int64_t)next_slot * P.N + i];
-        }
-        // a. delayed synaptic input (fixed point 2^-32 nS) and background
-        if (valid) {
-            const int64_t o = (int64_t)ring_slot * P.N + i;
-            if (e) {
-                gE += fixed_to_nS(e);
-                P.ringE[o] = 0;
-            }
-            if (h) {
-                gI += fixed_to_nS(h);
-                P.ringI[o] = 0;
-            }
-        }
-        if (P.bg_n > 0) {
-            if (k == 0 || (t & 3) == 0) {
-                const uint64_t q = (uint64_t)t >> 2;
-                rnd = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
-            }
-            const unsigned long long u = pick(rnd, (int)(t & 3));
-            int32_t c = 0;
-            while (c < P.bg_n && u >= P.bg_thr[c])
-                ++c;
-            gE += (float)c * P.bg_w;
-        }
-        const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
-        const float Vt = s.V;
-        dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, gE * P.to_mS, P.E_E, gI * P.to_mS,
-                                      P.E_I, s);
-        const bool spk = valid && Vt < P.theta && s.V >= P.theta;
-        cnt += spk;
-        list_append(spk, (int32_t)t, (int32_t)i, L.counter + parity, L.step, L.idx, L.cap);
-        if (R.n_spikes) {
-            const float frac = spk ? (P.theta - Vt) / (s.V - Vt) : 0.0f;
-            record_spikes(spk, (int32_t)t, (int32_t)i, frac, R, P.status);
-        }
-        if (slot >= 0)
-            R.V_trace[(int64_t)k * R.n_trace + slot] = s.V;
-        gE *= P.decE;
-        gI *= P.decI;
-        ring_slot = next_slot;
-    }
+    window_steps<MAXG, PREC>(dyn, mid, P, valid, i, t0, W, I_steps, R, R.V_trace, slot, L, parity, s, gE, gI,
+                             Ic, cnt, key, NoWork{});
     if (valid) {
         store_state(P, i, s);
         P.gE[i] = gE;
@@ -649,6 +815,192 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         if (!finite(s.V))
             atomicOr(P.status, HH_STATUS_NONFINITE);
     }
+}
+
+// Progress counters of the persistent kernel (zeroed before each launch).
+// Window w counts in slot w mod kPhaseSlots of `done` once per neuron block
+// that finished it and of `routed` once per routing warp that delivered it;
+// window w is complete when its slot reaches (w / kPhaseSlots + 1) x the
+// number of blocks or warps.  This is exact because no block or warp gets
+// more than two windows ahead of the slowest one (see persistent_body), so
+// a slot never holds a contribution from a later window than the one
+// waited for.  Waits are bounded by the global timer (kWaitLimitNs); on
+// expiry the waiter records HH_STATUS_BARRIER_TIMEOUT and gives up.
+constexpr int kPhaseSlots = 4;
+struct PhaseCounters {
+    unsigned long long* done;    // [kPhaseSlots]
+    unsigned long long* routed;  // [kPhaseSlots]
+};
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool wait_at_least(const unsigned long long* c, unsigned long long target,
+                                              int32_t* status)
+{
+    const volatile unsigned long long* p = c;
+    if (*p < target) {
+        const unsigned long long t0 = global_ns();
+        while (*p < target) {
+            if (global_ns() - t0 > kWaitLimitNs) {
+                atomicOr(status, HH_STATUS_BARRIER_TIMEOUT);
+                return false;
+            }
+            __nanosleep(32);
+        }
+    }
+    __threadfence();
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long signal_done(unsigned long long* c)
+{
+    __threadfence();
+    return atomicAdd(c, 1ull);
+}
+
+// The persistent kernel's block: kPersistNeurons neuron threads (warps 0-3)
+// and kPersistRouters routing warps.  Barrier 1 spans the neuron threads
+// only (the routing warps never wait on it).
+constexpr int kPersistNeurons = 128;
+constexpr int kPersistRouters = 4;
+constexpr int kPersistThreads = kPersistNeurons + 32 * kPersistRouters;
+constexpr int kPersistWarps = kPersistThreads / 32;
+
+__device__ __forceinline__ void neuron_bar()
+{
+    asm volatile("barrier.sync 1, %0;" ::"n"(kPersistNeurons) : "memory");
+}
+__device__ __forceinline__ bool neuron_all(bool p)
+{
+    int r;
+    asm volatile("{\n\t.reg .pred a, b;\n\tsetp.ne.s32 a, %1, 0;\n\tbarrier.red.and.pred b, 1, %2, a;\n\t"
+                 "selp.s32 %0, 1, 0, b;\n\t}"
+                 : "=r"(r)
+                 : "r"((int)p), "n"(kPersistNeurons)
+                 : "memory");
+    return r != 0;
+}
+
+// The whole n_steps of a network in one cooperative launch (windows of
+// W <= D/2 steps, call-local window w in list slot (w_index0 + w) mod 3).
+// Dataflow instead of a grid barrier:
+//  - a neuron block integrates window w once every routing warp has routed
+//    window w - 2 (the input of window w comes from spikes at least
+//    D >= 2W steps earlier, i.e. from windows <= w - 2; warps route in
+//    order), then counts itself done with w;
+//  - a routing warp delivers window w once every neuron block is done with
+//    it, then counts itself.  Its targets lie in windows >= w + 2, whose
+//    delay-line slots are disjoint from those of the windows integrated
+//    meanwhile (w + 1 at most: a block in w + 2 waits for w to be routed);
+//  - the last window is routed by every warp of the grid once all blocks
+//    are done with it.
+// So a block in window k implies all blocks done with k - 2, and a warp
+// routing window k implies all warps done routing k - 2: nothing runs more
+// than two windows ahead of the slowest block or warp.
+// The three list counters are zero at launch; the last routing warp to
+// finish window w clears its slot, which window w + 3 reuses: a block
+// starting w + 3 has waited for window w + 1 to be routed, which that warp
+// signals after the clear.
+template <int MAXG, int PREC, class Dyn>
+__device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronParams& P, const RouteParams& RP,
+                                                int64_t t0, int32_t n_steps, int32_t W, int64_t w_index0,
+                                                const float* __restrict__ I_steps, const RecordParams& R,
+                                                const SpikeList& L, const PhaseCounters& pc)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t n_win = (n_steps + W - 1) / W;
+    const unsigned long long n_blocks = gridDim.x;
+    const unsigned long long nR = (unsigned long long)gridDim.x * kPersistRouters;
+    auto list_count = [&](int32_t w) -> int64_t {
+        const int64_t n = __ldcg(L.counter + (int32_t)((w_index0 + w) % kListSlots));
+        return n > L.cap ? L.cap : n;
+    };
+    auto list_step = [&](int32_t w) { return L.step + (int32_t)((w_index0 + w) % kListSlots) * L.cap; };
+    auto list_idx = [&](int32_t w) { return L.idx + (int32_t)((w_index0 + w) % kListSlots) * L.cap; };
+    auto window_done = [&](int32_t w, unsigned long long* c, unsigned long long per) {
+        return wait_at_least(c + w % kPhaseSlots, (unsigned long long)(w / kPhaseSlots + 1) * per, P.status);
+    };
+    bool ok = true;
+    if (threadIdx.x >= kPersistNeurons) {
+        const int64_t r = (int64_t)blockIdx.x * kPersistRouters + (warp - kPersistNeurons / 32);
+        for (int32_t w = 0; w + 1 < n_win; ++w) {
+            int go = 1;
+            if (lane == 0)
+                go = window_done(w, pc.done, n_blocks);
+            if (!__shfl_sync(0xffffffffu, go, 0))
+                return;
+            route_items(RP, list_step(w), list_idx(w), list_count(w), r, (int64_t)nR);
+            __syncwarp();
+            // the last warp to finish window w frees its list slot for window w + 3
+            if (lane == 0 && signal_done(pc.routed + w % kPhaseSlots) + 1 ==
+                                 (unsigned long long)(w / kPhaseSlots + 1) * nR)
+                L.counter[(int32_t)((w_index0 + w) % kListSlots)] = 0;
+        }
+        int go = 1;
+        if (lane == 0 && n_win >= 1)
+            go = window_done(n_win - 1, pc.done, n_blocks);
+        ok = __shfl_sync(0xffffffffu, go, 0) != 0;
+    } else {
+        const int64_t gi = (int64_t)blockIdx.x * kPersistNeurons + threadIdx.x;
+        const bool valid = gi < P.N;
+        const int64_t i = valid ? gi : 0;
+        const int mid = P.model_id ? P.model_id[i] : 0;
+        State<MAXG, PREC> s;
+        load_state(P, i, s);
+        dyn.template load<MAXG, PREC>(mid, P, i, s);
+        float gE = P.gE[i], gI = P.gI[i];
+        const float Ic = P.I_const ? P.I_const[i] : 0.0f;
+        int32_t slot = -1;
+        if (R.V_trace && valid)
+            slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
+        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+        int32_t cnt = 0;
+        for (int32_t w = 0; w < n_win; ++w) {
+            if (w >= 2) {
+                bool go = true;
+                if (threadIdx.x == 0)
+                    go = window_done(w - 2, pc.routed, nR);
+                if (!neuron_all(go)) {
+                    ok = false;
+                    break;
+                }
+            }
+            const int32_t Ww = min(W, n_steps - w * W);
+            window_steps<MAXG, PREC>(dyn, mid, P, valid, i, t0 + (int64_t)w * W, Ww,
+                                     I_steps ? I_steps + (int64_t)w * W * P.N : nullptr, R,
+                                     R.V_trace ? R.V_trace + (int64_t)w * W * R.n_trace : nullptr, slot, L,
+                                     (int32_t)((w_index0 + w) % kListSlots), s, gE, gI, Ic, cnt, key, NoWork{});
+            neuron_bar();
+            if (threadIdx.x == 0)
+                signal_done(pc.done + w % kPhaseSlots);
+        }
+        if (valid) {
+            store_state(P, i, s);
+            P.gE[i] = gE;
+            P.gI[i] = gI;
+            if (R.counts && cnt)
+                R.counts[i] += cnt;
+            if (!finite(s.V))
+                atomicOr(P.status, HH_STATUS_NONFINITE);
+        }
+        if (!ok)
+            return;
+        bool go = true;
+        if (threadIdx.x == 0 && n_win >= 1)
+            go = window_done(n_win - 1, pc.done, n_blocks);
+        ok = neuron_all(go);
+    }
+    if (!ok || n_win < 1)
+        return;
+    // the last window, with every warp of the grid
+    route_items(RP, list_step(n_win - 1), list_idx(n_win - 1), list_count(n_win - 1),
+                (int64_t)blockIdx.x * kPersistWarps + warp, (int64_t)gridDim.x * kPersistWarps);
 }
 
 #endif  // __CUDACC__ || __CUDACC_RTC__

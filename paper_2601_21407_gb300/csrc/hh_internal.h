@@ -12,19 +12,6 @@
 
 namespace hh {
 
-struct RouteParams {
-    int64_t N;
-    const int64_t* out_ptr;
-    const int32_t* out_post;
-    const float* out_w;
-    const uint8_t* inh;
-    int64_t* ringE;
-    int64_t* ringI;
-    int32_t R;         // slots in the destination (ring: R = D; open loop: unused)
-    int32_t D;
-    int32_t open_loop; // 1: destination is [n_window][N] linear, drop >= n_window
-    int32_t n_window;
-};
 
 // error reporting into the thread-local hh_last_error() message (hh_abi.cu)
 hh_status fail(hh_status s, const char* fmt, ...);
@@ -90,7 +77,13 @@ struct JitKernels {
     cudaKernel_t independent = nullptr;
     cudaKernel_t window = nullptr;
     cudaKernel_t indexed = nullptr;
+    cudaKernel_t persistent = nullptr;
 };
+int jit_persistent_capacity(const JitKernels& K);
+cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, const RouteParams& RP, int64_t t0,
+                                  int32_t n_steps, int32_t W, int64_t w_index0, const float* I_steps,
+                                  const RecordParams& R, const SpikeList& L, const PhaseCounters& pc,
+                                  cudaStream_t st);
 // Compile (or take from the process-wide cache) the kernels for the installed
 // models; false with a message in *err on failure.
 bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernels* out, std::string* err);

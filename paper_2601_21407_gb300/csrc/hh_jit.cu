@@ -102,7 +102,7 @@ std::string abi_constants()
         {"HH_PREC_FAST", HH_PREC_FAST}, {"HH_PREC_ACCURATE", HH_PREC_ACCURATE},
         {"HH_PREC_COMPENSATED", HH_PREC_COMPENSATED}, {"HH_V_EXP_EULER", HH_V_EXP_EULER},
         {"HH_V_FWD_EULER", HH_V_FWD_EULER}, {"HH_STATUS_SPIKE_OVERFLOW", HH_STATUS_SPIKE_OVERFLOW},
-        {"HH_STATUS_NONFINITE", HH_STATUS_NONFINITE}};
+        {"HH_STATUS_NONFINITE", HH_STATUS_NONFINITE}, {"HH_STATUS_BARRIER_TIMEOUT", HH_STATUS_BARRIER_TIMEOUT}};
     for (const auto& x : c) {
         snprintf(b, sizeof(b), "#define %s %d\n", x.n, x.v);
         s += b;
@@ -167,7 +167,13 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
              "hh_jit_indexed(const __grid_constant__ hh::NeuronParams P, const int* __restrict__ list,\n"
              "               const int* __restrict__ n_list, long long t0, int n_steps,\n"
              "               const __grid_constant__ hh::RecordParams R)\n"
-             "{\n    hh::indexed_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, list, n_list, t0, n_steps, R);\n}\n",
+             "{\n    hh::indexed_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, list, n_list, t0, n_steps, R);\n}\n\n"
+             "extern \"C\" __global__ void __launch_bounds__(hh::kPersistThreads)\n"
+             "hh_jit_persistent(const __grid_constant__ hh::NeuronParams P, const __grid_constant__ hh::RouteParams RP,\n"
+             "                  long long t0, int n_steps, int W, long long w_index0, const float* __restrict__ I_steps,\n"
+             "                  const __grid_constant__ hh::RecordParams R, const __grid_constant__ hh::SpikeList L,\n"
+             "                  const __grid_constant__ hh::PhaseCounters pc)\n"
+             "{\n    hh::persistent_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, RP, t0, n_steps, W, w_index0, I_steps, R, L, pc);\n}\n",
              max_gates, precision);
     s += b;
     return s;
@@ -178,6 +184,7 @@ struct Entry {
     cudaKernel_t independent = nullptr;
     cudaKernel_t window = nullptr;
     cudaKernel_t indexed = nullptr;
+    cudaKernel_t persistent = nullptr;
     std::string log;
 };
 
@@ -220,6 +227,8 @@ bool compile(const std::string& src, Entry* e, std::string* err)
         ce = cudaLibraryGetKernel(&e->window, e->lib, "hh_jit_window");
     if (ce == cudaSuccess)
         ce = cudaLibraryGetKernel(&e->indexed, e->lib, "hh_jit_indexed");
+    if (ce == cudaSuccess)
+        ce = cudaLibraryGetKernel(&e->persistent, e->lib, "hh_jit_persistent");
     if (ce != cudaSuccess) {
         *err = std::string("loading the specialised neuron kernels failed: ") + cudaGetErrorString(ce);
         return false;
@@ -266,6 +275,7 @@ bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernel
     out->independent = it->second.independent;
     out->window = it->second.window;
     out->indexed = it->second.indexed;
+    out->persistent = it->second.persistent;
     return true;
 }
 
@@ -296,6 +306,44 @@ cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_
     SpikeList l = L;
     void* args[] = {&p, &t, &w, &I_steps, &r, &l, &par};
     return cudaLaunchKernel((const void*)K.window, grid, block, args, 0, st);
+}
+
+// Blocks of the persistent kernel (kPersistNeurons neurons each) that can
+// be resident at once (0 if the query fails).
+int jit_persistent_capacity(const JitKernels& K)
+{
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)K.persistent, kPersistThreads, 0) !=
+            cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, const RouteParams& RP, int64_t t0,
+                                  int32_t n_steps, int32_t W, int64_t w_index0, const float* I_steps,
+                                  const RecordParams& R, const SpikeList& L, const PhaseCounters& pc,
+                                  cudaStream_t st)
+{
+    NeuronParams p = P;
+    RouteParams rp = RP;
+    RecordParams r = R;
+    SpikeList l = L;
+    PhaseCounters g = pc;
+    long long t = t0, wi = w_index0;
+    int n = n_steps, w = W;
+    void* args[] = {&p, &rp, &t, &n, &w, &wi, &I_steps, &r, &l, &g};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((P.N + kPersistNeurons - 1) / kPersistNeurons));
+    cfg.blockDim = dim3(kPersistThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)K.persistent, args);
 }
 
 cudaError_t jit_launch_indexed(const JitKernels& K, const NeuronParams& P, const int32_t* list,

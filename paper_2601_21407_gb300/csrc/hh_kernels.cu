@@ -59,30 +59,7 @@ __global__ void __launch_bounds__(128) k_net_window(const __grid_constant__ DevM
     window_body<MAXG, PREC>(TableDyn{Ms}, P, t0, W, I_steps, R, L, parity);
 }
 
-// w (nS, finite, 0 <= w < 65536) as a 64-bit fixed-point count of 2^-32 nS,
-// from the float's bits with integer operations only (the 64-bit float ->
-// integer conversion executes on the FP64 unit).  Exact for w >= 2^-9 nS;
-// below, rounded to nearest with ties up.
-__device__ __forceinline__ unsigned long long nS_to_fixed(float w)
-{
-    const unsigned b = __float_as_uint(w);
-    const int e = (int)(b >> 23);
-    const unsigned m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
-    const int sh = (e ? e : 1) - 118;  // w 2^32 = m 2^(e - 150 + 32)
-    if (sh >= 0)
-        return (unsigned long long)m << sh;
-    if (sh < -40)
-        return 0ull;
-    return ((unsigned long long)m + (1ull << (-sh - 1))) >> (-sh);
-}
-
-// -------------------------------------------------------------------------
-// Spike routing: one warp per spike.  The out-row is walked in 128-edge
-// chunks aligned to 4 edges: lane l reads the int4 of targets and the float4
-// of weights at chunk + 4l (the arrays carry 4 entries of padding), masks the
-// entries outside the row and issues one RED.ADD.64 per edge.  Two chunks
-// are in flight per iteration.  The spike count is read on the device.
-// -------------------------------------------------------------------------
+// Spike routing of a list whose length is read on the device.
 __global__ void __launch_bounds__(256) k_route(const __grid_constant__ RouteParams RP,
                                                const int32_t* __restrict__ st,
                                                const int32_t* __restrict__ ix,
@@ -92,48 +69,9 @@ __global__ void __launch_bounds__(256) k_route(const __grid_constant__ RoutePara
     int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     if (n > cap)
         n = cap;
-    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t sp = warp; sp < n; sp += nw) {
-        const int32_t j = ix[sp];
-        const int32_t t = st[sp];
-        if (j < 0 || j >= RP.N || t < 0)
-            continue;
-        int64_t row;
-        if (RP.open_loop) {
-            row = (int64_t)t + RP.D;
-            if (row >= RP.n_window)
-                continue;
-        } else {
-            row = ((int64_t)t + RP.D) % RP.R;
-        }
-        unsigned long long* dst =
-            reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
-        const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
-        for (int64_t base = (e0 & ~(int64_t)3); base < e1; base += 256) {
-            const int64_t ea = base + 4 * lane;
-            const int64_t eb = ea + 128;
-            int4 pa = make_int4(0, 0, 0, 0), pb = pa;
-            float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
-            if (ea < e1) {
-                pa = *reinterpret_cast<const int4*>(RP.out_post + ea);
-                wa = *reinterpret_cast<const float4*>(RP.out_w + ea);
-            }
-            if (eb < e1) {
-                pb = *reinterpret_cast<const int4*>(RP.out_post + eb);
-                wb = *reinterpret_cast<const float4*>(RP.out_w + eb);
-            }
-            const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
-            const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int64_t e = (q < 4 ? ea : eb) + (q & 3);
-                if (e >= e0 && e < e1)
-                    atomicAdd(dst + pp[q], nS_to_fixed(ww[q]));
-            }
-        }
-    }
+    route_spikes(RP, st, ix, n, warp, nw);
 }
 
 // -------------------------------------------------------------------------
@@ -293,7 +231,11 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
 cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity,
                                 cudaStream_t st)
 {
-    k_route<<<152 * 8, 256, 0, st>>>(RP, L.step, L.idx, L.counter + parity, 0, L.cap);
+    // two resident blocks per SM whose warps loop over the window's spikes:
+    // routing overlaps the next window's neuron kernel, whose blocks must
+    // still find registers on every SM
+    k_route<<<152 * 2, 256, 0, st>>>(RP, L.step + parity * L.cap, L.idx + parity * L.cap, L.counter + parity, 0,
+                                     L.cap);
     return cudaGetLastError();
 }
 

@@ -27,11 +27,11 @@ HH_GATE = {"ab": 0, "inftau": 1, "ca": 2}
 HH_MAX_CHANNELS, HH_MAX_GATES_PER_CHANNEL, HH_MAX_GATES, HH_MAX_MODELS = 8, 3, 8, 4
 HH_PREC_FAST, HH_PREC_ACCURATE, HH_PREC_COMPENSATED = 0, 1, 2
 HH_V_EXP_EULER, HH_V_FWD_EULER = 0, 1
-HH_KERNELS_SPECIALISED, HH_KERNELS_TABLE = 0, 1
+HH_KERNELS_SPECIALISED, HH_KERNELS_TABLE, HH_KERNELS_PERSISTENT = 0, 1, 2
 (HH_READ_V, HH_READ_GATES, HH_READ_CA, HH_READ_G_SYN, HH_READ_STATUS, HH_READ_TIME,
  HH_READ_N_OUT, HH_READ_PROFILE, HH_READ_SURROGATE) = range(9)
 HH_KERNEL_NEURON, HH_KERNEL_ROUTE, HH_KERNEL_COUNT = 0, 1, 2
-HH_STATUS_SPIKE_OVERFLOW, HH_STATUS_NONFINITE = 1, 2
+HH_STATUS_SPIKE_OVERFLOW, HH_STATUS_NONFINITE, HH_STATUS_BARRIER_TIMEOUT = 1, 2, 4
 
 
 class HHError(RuntimeError):

@@ -111,6 +111,7 @@ def test_background_counts_bit_exact():
 @pytest.mark.parametrize("prec,kernels", [(hh.HH_PREC_FAST, hh.HH_KERNELS_SPECIALISED),
                                           (hh.HH_PREC_ACCURATE, hh.HH_KERNELS_SPECIALISED),
                                           (hh.HH_PREC_COMPENSATED, hh.HH_KERNELS_SPECIALISED),
+                                          (hh.HH_PREC_FAST, hh.HH_KERNELS_PERSISTENT),
                                           (hh.HH_PREC_FAST, hh.HH_KERNELS_TABLE)])
 def test_closed_loop_small_network(prec, kernels):
     """1,000 neurons, in-degree 100, background, 200 ms closed loop: every
@@ -178,30 +179,65 @@ def test_batched_networks_mixed_models():
 
 def test_deterministic_and_resumable():
     """Two runs from the same state give bit-identical rasters (fixed-point
-    delivery is order independent), and splitting a run across calls at
-    points that do not align with the delay windows changes no bit."""
+    delivery is order independent), splitting a run across calls at points
+    that do not align with the delay windows changes no bit, and the
+    single-launch persistent schedule equals the launch-per-window one."""
     torch = _torch()
     g = inp.network(n=3000, k_in=300, seed=5, mu=0.0)
     bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
 
-    def run(chunks):
-        net = make_net(g, bg=bg, seed=1)
+    def run(chunks, kernels=hh.HH_KERNELS_SPECIALISED):
+        net = make_net(g, bg=bg, seed=1, kernels=kernels)
         rec, b = hh.make_record(3000, sum(chunks), spike_cap=500_000)
         for c in chunks:
             net.step(c, rec=rec)
         torch.cuda.synchronize()
         v = net.readout(hh.HH_READ_V)
         s = hh.spikes_to_numpy(b)
+        assert int(net.readout(hh.HH_READ_STATUS)[0]) == 0
         net.close()
         return v, s
 
     a = run([2000])
     b = run([2000])
     c = run([13, 401, 999, 587])
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[0], c[0])
-    for k in range(3):
-        assert np.array_equal(a[1][k], b[1][k]) and np.array_equal(a[1][k], c[1][k])
+    d = run([2000], hh.HH_KERNELS_PERSISTENT)
+    e = run([13, 401, 999, 587], hh.HH_KERNELS_PERSISTENT)
+    for x in (b, c, d, e):
+        assert np.array_equal(a[0], x[0])
+        for k in range(3):
+            assert np.array_equal(a[1][k], x[1][k])
     assert len(a[1][0]) > 100
+
+
+@pytest.mark.parametrize("D,chunks", [(2, [1, 300, 99]), (7, [400]), (13, [5, 6, 389]), (40, [1000])])
+def test_persistent_matches_launches(D, chunks):
+    """The single cooperative launch (windows of D/2 steps, routing warps
+    delivering the previous window while the neuron threads integrate the
+    next) gives bit-identical V and rasters to one launch per window, for
+    odd and minimal delays and calls of any length."""
+    torch = _torch()
+    g = inp.network(n=2000, k_in=150, seed=11, mu=0.3)
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
+    out = []
+    for kernels in (hh.HH_KERNELS_PERSISTENT, hh.HH_KERNELS_SPECIALISED):
+        net = make_net(g, D=D, bg=bg, seed=4, kernels=kernels)
+        net.profile(True)
+        rec, b = hh.make_record(2000, sum(chunks), trace=16, spike_cap=400_000)
+        for c in chunks:
+            net.step(c, rec=rec)
+        torch.cuda.synchronize()
+        kt = net.kernel_times()
+        out.append((net.readout(hh.HH_READ_V), hh.spikes_to_numpy(b), b["V_trace"].cpu().numpy(),
+                    int(net.readout(hh.HH_READ_STATUS)[0]), kt))
+        net.close()
+    (va, sa, ta, sta, kta), (vb, sb, tb, stb, ktb) = out
+    assert sta == 0 and stb == 0
+    assert kta["neuron"][0] == len(chunks) and kta["route"][0] == 0
+    assert np.array_equal(va, vb) and np.array_equal(ta, tb)
+    for k in range(3):
+        assert np.array_equal(sa[k], sb[k])
+    assert len(sa[0]) > 50
 
 
 def test_reset_restores_initial_state():
@@ -239,12 +275,29 @@ def test_invalid_csr_rejected(what):
 
 
 def test_profile_counts_launches():
+    """D = 40: windows of D/2 steps, so 400 steps are 20 neuron and 20
+    routing launches (routing overlaps the next window on a second stream);
+    the persistent mode makes it one cooperative launch per call; D = 1
+    keeps one launch pair per step."""
     g = inp.network(n=500, k_in=20, seed=8)
-    net = make_net(g, bg={"rate_hz": 5.0, "K": 500, "w": 1.0})
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.0}
+    net = make_net(g, bg=bg)
     net.profile(True)
     net.step(400)
     kt = net.kernel_times()
     net.profile(False)
-    assert kt["neuron"][0] == 10 and kt["route"][0] == 10
+    assert kt["neuron"][0] == 20 and kt["route"][0] == 20
     assert kt["neuron"][1] > 0
+    net.close()
+    net = make_net(g, bg=bg, kernels=hh.HH_KERNELS_PERSISTENT)
+    net.profile(True)
+    net.step(400)
+    kt = net.kernel_times()
+    assert kt["neuron"][0] == 1 and kt["route"][0] == 0
+    net.close()
+    net = make_net(g, D=1)
+    net.profile(True)
+    net.step(30)
+    kt = net.kernel_times()
+    assert kt["neuron"][0] == 30 and kt["route"][0] == 30
     net.close()
