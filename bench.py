@@ -115,18 +115,22 @@ def peaks():
 
 
 def mufu_ops_per_neuron_step(model):
-    """Algorithmic transcendental work of one exponential-Euler neuron step:
-    one exponential per exp/sigmoid/linoid rate (two for bell), one division
-    per sigmoid/linoid rate, per gate one division (p_inf) and one
-    exponential (the relaxation factor), and for V one division (V_inf) and
-    one exponential."""
-    n = 0
+    """Algorithmic transcendental work of one exponential-Euler neuron step,
+    as (exponentials, divisions): one exponential per exp/sigmoid/linoid
+    rate (two for bell), one division per sigmoid/linoid/bell rate, per gate
+    one division (p_inf) and one exponential (the relaxation factor), and for
+    V one division (V_inf) and one exponential.  Classic HH: (10, 7)."""
+    n_exp = n_div = 0
     for ch in model["channels"]:
         for g in ch["gates"]:
             for f in (g["f1"], g["f2"]):
-                n += {"const": 0, "exp": 1, "sigmoid": 2, "linoid": 2, "bell": 3}[f[0]]
-            n += 2
-    return n + 2
+                e, d = {"const": (0, 0), "exp": (1, 0), "sigmoid": (1, 1), "linoid": (1, 1),
+                        "bell": (2, 1)}[f[0]]
+                n_exp += e
+                n_div += d
+            n_exp += 1
+            n_div += 1
+    return n_exp + 1, n_div + 1
 
 
 def run_gpu(args):
@@ -167,6 +171,9 @@ def run_gpu(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # SFU and FMA issue rates of this GPU (the roofline denominator of the
+    # neuron kernel), measured before the timed region
+    sfu_peaks = hh.hh_measure_peaks(stream.cuda_stream)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -278,13 +285,20 @@ def run_gpu(args):
         n_launch_route, route_ms = kt["route"]
         avg_neuron_ms = neuron_ms / max(1, n_launch_neuron)
         steps_per_launch = STEPS_PER_SIM / max(1, n_launch_neuron)
-        mufu = mufu_ops_per_neuron_step(inp.CLASSIC_HH)
+        n_exp, n_div = mufu_ops_per_neuron_step(inp.CLASSIC_HH)
+        mufu = n_exp + n_div
         # one cooperative launch per call (routing inside it) or one neuron
         # launch per window with routing launches beside it
         dominant = ("hh_jit_persistent (whole step in one cooperative launch, routing between steps)"
                     if n_launch_route == 0 else "hh_jit_window (k_net_window specialised by NVRTC)")
         achieved_gops = mufu * W["n"] * steps_per_launch / (avg_neuron_ms * 1e-3) / 1e9
-        peak_gops = SM_COUNT * MUFU_PER_SM_CLK * sm_max * 1e6 / 1e9
+        # SFU bound of one neuron-step from the measured rates: n_exp
+        # ex2.approx and n_div rcp.approx results; the peak is the op count
+        # over that time.  The nominal 16 results/clk/SM x sm_max stays in the
+        # line for context.
+        t_sfu = n_exp / sfu_peaks["ex2_per_s"] + n_div / sfu_peaks["rcp_per_s"]
+        peak_gops = mufu / t_sfu / 1e9
+        nominal_gops = SM_COUNT * MUFU_PER_SM_CLK * sm_max * 1e6 / 1e9
         cpu = cpu_baseline_sample(cores=os.cpu_count()) if not args.no_cpu_baseline else None
         line = {
             "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
@@ -305,10 +319,14 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops,
                          "unit": "Gop/s (SFU-class: exp + div)",
                          "frac": achieved_gops / peak_gops, "traffic": None,
-                         "peak_source": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} SFU ops/clk x "
-                                        f"{sm_max:.0f} MHz ({pk_kind} sm_max)",
-                         "ops_per_neuron_step": mufu, "kernel": dominant},
+                         "peak_source": f"measured (hh_measure_peaks, all SMs, CUDA events): {n_exp} ex2.approx "
+                                        f"+ {n_div} rcp.approx per neuron-step at the measured rates",
+                         "nominal_peak": nominal_gops,
+                         "nominal_source": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} SFU ops/clk x "
+                                           f"{sm_max:.0f} MHz ({pk_kind} sm_max)",
+                         "ops_per_neuron_step": {"exp": n_exp, "div": n_div}, "kernel": dominant},
             "clocks": clk,
+            "peaks_measured": {k: v / 1e9 for k, v in sfu_peaks.items()} | {"unit": "G results/s"},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

@@ -229,6 +229,23 @@ hh_status hh_set_channels(hh_net* net, int32_t model_index, const hh_model_desc*
                           const float* gbar);
 
 /* ------------------------------------------------------------------ */
+/* Issue-rate peaks (the denominators of the neuron kernels' roofline)   */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double ffma_per_s;  /* FP32 fused multiply-adds per second, whole GPU   */
+    double ex2_per_s;   /* ex2.approx.ftz.f32 results per second            */
+    double rcp_per_s;   /* rcp.approx.ftz.f32 results per second            */
+} hh_peaks;
+
+/* Measure the three rates on the current device: 8 blocks of 256 threads
+ * per SM, 8 independent unrolled dependency chains per thread, one warm-up
+ * launch, CUDA events on `stream` (cudaStream_t, NULL = legacy).  Takes a
+ * few milliseconds; allocates and frees a small scratch buffer on the
+ * stream.  Synchronous.  Errors: HH_EINVAL (out NULL), HH_ECUDA. */
+hh_status hh_measure_peaks(hh_peaks* out, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Stepping                                                             */
 /* ------------------------------------------------------------------ */
 

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhh.so")
-SOURCES = ["hh_kernels.cu", "hh_abi.cu", "hh_jit.cu", "hh_gemm.cu", "hh_layer.cu", "hh_surrogate.cu"]
+SOURCES = ["hh_kernels.cu", "hh_abi.cu", "hh_jit.cu", "hh_gemm.cu", "hh_layer.cu", "hh_surrogate.cu",
+           "hh_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -872,6 +872,15 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
     return HH_OK;
 }
 
+hh_status hh_measure_peaks(hh_peaks* out, void* stream)
+{
+    if (!out)
+        return fail(HH_EINVAL, "out is NULL");
+    *out = hh_peaks{};
+    HH_CUDA(hh::measure_peaks(&out->ffma_per_s, &out->ex2_per_s, &out->rcp_per_s, (cudaStream_t)stream));
+    return HH_OK;
+}
+
 hh_status hh_reset(hh_net* net, const float* V0)
 {
     if (!net)

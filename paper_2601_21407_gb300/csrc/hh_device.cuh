@@ -330,19 +330,16 @@ __device__ __forceinline__ void load_conductances(const DevModel& M, const float
     }
 }
 
-// One exponential-Euler step of one neuron (order: rates at V_t, gates,
-// conductances with the new gates, V, Ca).  gsE/gsI in mS/cm^2.
-template <int MAXG, int PREC>
-__device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_update, float I,
-                                            float gsE, float EE, float gsI, float EI,
-                                            State<MAXG, PREC>& s)
+// Gate part of one exponential-Euler step: the gates q with q % 2 == ROLE
+// (ROLE < 0: every gate) from the rates at V_t = s.V.
+template <int MAXG, int PREC, int ROLE>
+__device__ __forceinline__ void neuron_gates(const DevModel& M, float dt, State<MAXG, PREC>& s)
 {
     constexpr bool FAST = PREC == HH_PREC_FAST;
-    using Mt = Mth<FAST>;
     const float V = s.V;
 #pragma unroll
     for (int q = 0; q < MAXG; ++q) {
-        if (q < M.n_gates) {
+        if (q < M.n_gates && (ROLE < 0 || (q & 1) == ROLE)) {
             float inf, z;
             gate_inf_z<FAST>(M.g[q], V, s.Ca, dt, inf, z);
             if (PREC == HH_PREC_COMPENSATED) {
@@ -353,6 +350,17 @@ __device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_u
             }
         }
     }
+}
+
+// Membrane part: conductances with the new gates, V, Ca.  gsE/gsI in
+// mS/cm^2.
+template <int MAXG, int PREC>
+__device__ __forceinline__ void neuron_vstep(const DevModel& M, float dt, int v_update, float I, float gsE,
+                                             float EE, float gsI, float EI, State<MAXG, PREC>& s)
+{
+    constexpr bool FAST = PREC == HH_PREC_FAST;
+    using Mt = Mth<FAST>;
+    const float V = s.V;
     float G = gsE + gsI + s.gconst;
     float Ip = gsE * (V - EE) + gsI * (V - EI) + (s.gconst * V - s.gconstE);
     float gCa = 0.0f, ECa = 0.0f;
@@ -392,6 +400,17 @@ __device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_u
         const float Cainf = M.ca_rest - M.ca_k * M.ca_tau * ICa;
         s.Ca = fmaf(s.Ca - Cainf, M.ca_decay, Cainf);
     }
+}
+
+// One exponential-Euler step of one neuron (order: rates at V_t, gates,
+// conductances with the new gates, V, Ca).  gsE/gsI in mS/cm^2.
+template <int MAXG, int PREC>
+__device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_update, float I,
+                                            float gsE, float EE, float gsI, float EI,
+                                            State<MAXG, PREC>& s)
+{
+    neuron_gates<MAXG, PREC, -1>(M, dt, s);
+    neuron_vstep<MAXG, PREC>(M, dt, v_update, I, gsE, EE, gsI, EI, s);
 }
 
 template <int MAXG, int PREC>
@@ -491,6 +510,21 @@ __device__ __forceinline__ uint32_t pick(const uint4& v, int w)
     return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
+// Inverse-CDF Poisson count of a uniform 32-bit word: #{j < n : u >= thr[j]}
+// for a nondecreasing table (the first kPoissonUnroll compares without a
+// loop, the rest only after a word that passed all of them).
+__device__ __forceinline__ int32_t poisson_count(uint32_t u, const uint32_t* thr, int32_t n)
+{
+    int32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kPoissonUnroll; ++j)
+        c += (j < n && u >= thr[j]) ? 1 : 0;
+    if (c == kPoissonUnroll)
+        for (int j = kPoissonUnroll; j < n && u >= thr[j]; ++j)
+            ++c;
+    return c;
+}
+
 // w (nS, finite, 0 <= w < 65536) as a 64-bit fixed-point count of 2^-32 nS,
 // from the float's bits with integer operations only (the 64-bit float ->
 // integer conversion executes on the FP64 unit).  Exact for w >= 2^-9 nS;
@@ -534,18 +568,20 @@ __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_
         unsigned long long* dst =
             reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
         const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
+        // synapse rows are read once per spike: streaming (evict-first) loads,
+        // so that they do not push the delay line out of L2
         for (int64_t base = (e0 & ~(int64_t)3); base < e1; base += 256) {
             const int64_t ea = base + 4 * lane;
             const int64_t eb = ea + 128;
             int4 pa = make_int4(0, 0, 0, 0), pb = pa;
             float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
             if (ea < e1) {
-                pa = *reinterpret_cast<const int4*>(RP.out_post + ea);
-                wa = *reinterpret_cast<const float4*>(RP.out_w + ea);
+                pa = __ldcs(reinterpret_cast<const int4*>(RP.out_post + ea));
+                wa = __ldcs(reinterpret_cast<const float4*>(RP.out_w + ea));
             }
             if (eb < e1) {
-                pb = *reinterpret_cast<const int4*>(RP.out_post + eb);
-                wb = *reinterpret_cast<const float4*>(RP.out_w + eb);
+                pb = __ldcs(reinterpret_cast<const int4*>(RP.out_post + eb));
+                wb = __ldcs(reinterpret_cast<const float4*>(RP.out_w + eb));
             }
             const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
             const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -589,12 +625,12 @@ __device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t
                 int4 pa = make_int4(0, 0, 0, 0), pb = pa;
                 float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
                 if (ea < e1) {
-                    pa = *reinterpret_cast<const int4*>(RP.out_post + ea);
-                    wa = *reinterpret_cast<const float4*>(RP.out_w + ea);
+                    pa = __ldcs(reinterpret_cast<const int4*>(RP.out_post + ea));
+                    wa = __ldcs(reinterpret_cast<const float4*>(RP.out_w + ea));
                 }
                 if (eb < e1) {
-                    pb = *reinterpret_cast<const int4*>(RP.out_post + eb);
-                    wb = *reinterpret_cast<const float4*>(RP.out_w + eb);
+                    pb = __ldcs(reinterpret_cast<const int4*>(RP.out_post + eb));
+                    wb = __ldcs(reinterpret_cast<const float4*>(RP.out_w + eb));
                 }
                 const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
                 const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -750,14 +786,7 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
                 const uint64_t q = (uint64_t)t >> 2;
                 rnd = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
             }
-            const uint32_t u = pick(rnd, (int)(t & 3));
-            int32_t c = 0;
-#pragma unroll
-            for (int j = 0; j < kPoissonUnroll; ++j)
-                c += (j < P.bg_n && u >= P.bg_thr[j]) ? 1 : 0;
-            if (c == kPoissonUnroll)
-                for (int j = kPoissonUnroll; j < P.bg_n && u >= P.bg_thr[j]; ++j)
-                    ++c;
+            const int32_t c = poisson_count(pick(rnd, (int)(t & 3)), P.bg_thr, P.bg_n);
             gE += (float)c * P.bg_w;
         }
         const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);

@@ -73,6 +73,9 @@ cudaError_t surrogate_stats(const Surrogate* S, unsigned long long* host2, int32
 cudaError_t surrogate_reset_stats(Surrogate* S, cudaStream_t st);
 
 // Neuron kernels specialised for a model set, compiled with NVRTC (hh_jit.cu).
+// FP32 FMA, ex2.approx and rcp.approx results per second on the current device.
+cudaError_t measure_peaks(double* ffma, double* ex2, double* rcp, cudaStream_t st);
+
 struct JitKernels {
     cudaKernel_t independent = nullptr;
     cudaKernel_t window = nullptr;

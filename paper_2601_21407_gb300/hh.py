@@ -120,6 +120,10 @@ class hh_kernel_time(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
+class hh_peaks(C.Structure):
+    _fields_ = [("ffma_per_s", C.c_double), ("ex2_per_s", C.c_double), ("rcp_per_s", C.c_double)]
+
+
 class hh_record(C.Structure):
     _fields_ = [("V_trace", C.c_void_p), ("trace_idx", C.c_void_p), ("n_trace", C.c_int32),
                 ("spikes", C.c_void_p), ("spike_cap", C.c_int64), ("n_spikes", C.c_void_p),
@@ -130,7 +134,7 @@ EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_
            "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
            "hh_layer_forward", "hh_backward", "hh_layer_readout", "hh_layer_destroy",
-           "hh_surrogate_train", "hh_surrogate_enable"]
+           "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks"]
 
 
 def lib_path() -> str:
@@ -188,6 +192,8 @@ def lib():
             L.hh_last_error.restype = C.c_char_p
             L.hh_last_error.argtypes = []
             L.hh_version.restype = C.c_int32
+            L.hh_measure_peaks.restype = C.c_int
+            L.hh_measure_peaks.argtypes = [P(hh_peaks), vp]
             _lib = L
     return _lib
 
@@ -250,6 +256,14 @@ def hh_gemm_bf16(A, Bt, C, M, N, K, splits=1, status=None, stream=None):
 
 def hh_destroy(net: int):
     lib().hh_destroy(net)
+
+
+def hh_measure_peaks(stream=None) -> dict:
+    """FP32 FMA, ex2.approx and rcp.approx results per second on the current
+    device (microbenchmarks of the library, CUDA-event timed)."""
+    out = hh_peaks()
+    _check(lib().hh_measure_peaks(C.byref(out), stream))
+    return {"ffma_per_s": out.ffma_per_s, "ex2_per_s": out.ex2_per_s, "rcp_per_s": out.rcp_per_s}
 
 
 # ---------------------------------------------------------------------------

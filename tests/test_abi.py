@@ -48,6 +48,7 @@ int main(void){
  printf("%zu %zu %zu %zu %zu\\n", offsetof(hh_net_desc, dt_ms), offsetof(hh_net_desc, n_synapses),
    offsetof(hh_net_desc, seed), offsetof(hh_net_desc, stream), offsetof(hh_model_desc, ca_tau));
  printf("%zu\\n", offsetof(hh_net_desc, V0));
+ printf("%zu %zu\\n", sizeof(hh_peaks), offsetof(hh_peaks, rcp_per_s));
  return 0; }
 """)
     exe = tmp_path / "probe"
@@ -60,7 +61,8 @@ int main(void){
             C.sizeof(hh.hh_spike), C.sizeof(hh.hh_neurons_noalloc),
             hh.hh_neurons_noalloc.status.offset, hh.hh_net_desc.dt_ms.offset, hh.hh_net_desc.n_synapses.offset,
             hh.hh_net_desc.seed.offset, hh.hh_net_desc.stream.offset,
-            hh.hh_model_desc.ca_tau.offset, hh.hh_net_desc.V0.offset]
+            hh.hh_model_desc.ca_tau.offset, hh.hh_net_desc.V0.offset,
+            C.sizeof(hh.hh_peaks), hh.hh_peaks.rcp_per_s.offset]
     assert got == want
 
 
@@ -105,3 +107,8 @@ def test_model_marshalling_roundtrip():
     assert m.channels[0].gates[0].f1.form == hh.HH_FN["linoid"]
     assert m.channels[2].gates[1].f2.form == hh.HH_FN["bell"]
     assert m.channels[0].gates[0].power == 3
+
+
+def test_measure_peaks_rejects_null():
+    assert hh.lib().hh_measure_peaks(None, None) == hh.HH_EINVAL
+    assert "NULL" in hh.hh_last_error()

@@ -108,6 +108,36 @@ def test_background_counts_bit_exact():
     net.close()
 
 
+@pytest.mark.parametrize("kernels", [hh.HH_KERNELS_SPECIALISED, hh.HH_KERNELS_PERSISTENT, hh.HH_KERNELS_TABLE])
+def test_background_counts_in_network_bit_exact(kernels):
+    """The background of a network with synapses (delay line, routing and
+    list machinery active, every kernel schedule): with zero synaptic
+    weights, g_E after each step reveals every neuron's count, and it equals
+    the oracle's draw for every neuron and step."""
+    N = 4096
+    rng = np.random.default_rng(5)
+    csr = (np.arange(0, 4 * N + 1, 4, dtype=np.int64), rng.integers(0, N, 4 * N).astype(np.int32),
+           np.zeros(4 * N, np.float32))
+    bg = {"rate_hz": 5.0, "K": 2106, "w": 0.5}
+    net = hh.Network(np.full(N, -65.0, np.float32), 0.025, csr=csr, inh=np.zeros(N, np.uint8), syn=SYN,
+                     delay_steps=6, bg=bg, seed=321, kernels=kernels)
+    net.set_channels(0, inp.CLASSIC_HH)
+    thr = oracle.poisson_table(oracle.background_lambda(2106, 5.0, 0.025))
+    dec = np.float32(np.exp(-0.025 / 5.0))
+    prev = np.zeros(N, np.float32)
+    total = 0
+    for t in range(9):
+        net.step(1)
+        gsyn = net.readout(hh.HH_READ_G_SYN)[:N]
+        k = np.rint((gsyn / dec - prev) / np.float32(0.5)).astype(int)
+        kr = np.array([oracle.poisson_sample(oracle.background_word(321, t, i), thr) for i in range(N)])
+        assert np.array_equal(k, kr), t
+        total += kr.sum()
+        prev = gsyn
+    assert total > 0
+    net.close()
+
+
 @pytest.mark.parametrize("prec,kernels", [(hh.HH_PREC_FAST, hh.HH_KERNELS_SPECIALISED),
                                           (hh.HH_PREC_ACCURATE, hh.HH_KERNELS_SPECIALISED),
                                           (hh.HH_PREC_COMPENSATED, hh.HH_KERNELS_SPECIALISED),

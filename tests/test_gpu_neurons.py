@@ -246,3 +246,16 @@ def test_bad_model_rejected():
         net.step(10)     # model 0 never installed
     assert e.value.status == hh.HH_ESTATE
     net.close()
+
+
+def test_measure_peaks_plausible():
+    """The issue-rate microbenchmarks behind the neuron kernels' roofline:
+    positive, FMA faster than the SFU approximations, and the SFU rates
+    within a factor of 8 of 16 results per clock per SM at 1-2.1 GHz."""
+    import torch
+    p = hh.hh_measure_peaks()
+    torch.cuda.synchronize()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lo, hi = sms * 16 * 1.0e9 / 8, sms * 16 * 2.1e9 * 8
+    assert p["ffma_per_s"] > p["ex2_per_s"] > 0 and p["ffma_per_s"] > p["rcp_per_s"] > 0
+    assert lo < p["ex2_per_s"] < hi and lo < p["rcp_per_s"] < hi
