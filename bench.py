@@ -331,7 +331,9 @@ def run_gpu(args):
         if cpu is not None:
             line["cpu_baseline"] = cpu
         if not args.no_extras:
-            line["extra"] = extras(dev, pk)
+            line["extra"] = extras(dev, dict(pk, sfu=sfu_peaks))
+            if args.batched:
+                line["extra"]["batched_64_networks_200ms"] = extra_batched(dev, sfu_peaks)
             line["extra"]["network_persistent_cooperative"] = {
                 "ms_per_step": persistent_ms,
                 "neuron_steps_per_s": float(W["n"]) * STEPS_PER_SIM / (persistent_ms * 1e-3)}
@@ -339,6 +341,68 @@ def run_gpu(args):
     net.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def sfu_roofline_frac(model, neuron_steps_per_s, peaks):
+    """Fraction of the SFU bound of `model` (its exponentials at the measured
+    ex2.approx rate plus its divisions at the measured rcp.approx rate)."""
+    n_exp, n_div = mufu_ops_per_neuron_step(model)
+    return neuron_steps_per_s * (n_exp / peaks["ex2_per_s"] + n_div / peaks["rcp_per_s"])
+
+
+def extra_batched(dev, peaks):
+    """The 64 batched heterogeneous networks: sizes LogUniform(1e3, 5e4),
+    in-degree U{100..1000}, lognormal weights, half classic and half
+    multi-channel networks (7.9e5 neurons, 4.5e8 synapses at seed 0), 1 ms
+    delay, background 600 sources x 5 Hz x 1.2 nS, 200 ms (8,000 steps) from
+    reset per repetition, launch per 20-step window."""
+    import torch
+
+    from paper_2601_21407_gb300 import hh
+    t_gen = time.perf_counter()
+    bn = inp.batched_networks(n_nets=64, seed=0)
+    t_gen = time.perf_counter() - t_gen
+    N = int(bn["offsets"][-1])
+    T = 8_000
+    net = hh.Network(bn["V0"], 0.025, csr=(bn["row_ptr"], bn["col"], bn["w"]), inh=bn["inh"], syn=SYN,
+                     delay_steps=DELAY, bg={"rate_hz": 5.0, "K": 600, "w": 1.2}, seed=3,
+                     precision=hh.HH_PREC_FAST, model_id=bn["model_id"])
+    net.set_channels(0, inp.CLASSIC_HH)
+    net.set_channels(1, inp.MULTI_CHANNEL)
+    V0 = torch.as_tensor(bn["V0"], device=dev)
+    out_deg = torch.as_tensor(np.diff(net.readout(hh.HH_READ_N_OUT)), device=dev)
+    rec, b = hh.make_record(N, T, spike_cap=0)
+
+    def run():
+        b["counts"].zero_()
+        net.reset(V0)
+        net.step(T, rec=rec)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    counts = b["counts"]
+    events = float((counts.to(torch.int64) * out_deg).sum().item())
+    nc = int((bn["model_id"] == 0).sum())
+    frac_c = nc / N
+    rate = N * T / (ms * 1e-3)
+    # SFU bound of the mix: per-neuron-step time weighted by model share
+    t_c = sfu_roofline_frac(inp.CLASSIC_HH, 1.0, peaks)
+    t_m = sfu_roofline_frac(inp.MULTI_CHANNEL, 1.0, peaks)
+    res = {"neurons": N, "synapses": int(bn["col"].size), "ms_per_200ms_sim": ms,
+           "neuron_steps_per_s": rate, "synaptic_events_per_s": events / (ms * 1e-3),
+           "mean_rate_hz": float(counts.sum().item()) / N / 0.2,
+           "sfu_roofline_frac": rate * (frac_c * t_c + (1 - frac_c) * t_m),
+           "graph_generation_s": t_gen, "status": int(net.readout(hh.HH_READ_STATUS)[0])}
+    net.close()
+    return res
 
 
 def extras(dev, pk):
@@ -380,7 +444,10 @@ def extras(dev, pk):
     rec, b = hh.make_record(1_000_000, 20_000, spike_cap=0)
     ms = timed(lambda: net.step(20_000, rec=rec))
     out["multichannel_1e6_500ms"] = {"neuron_steps_per_s": 1e6 * 20_000 / (ms * 1e-3), "ms": ms,
-                                     "mean_rate_hz": float(b["counts"].sum().item()) / 1e6 / 0.5}
+                                     "mean_rate_hz": float(b["counts"].sum().item()) / 1e6 / 0.5,
+                                     "sfu_roofline_frac": sfu_roofline_frac(inp.MULTI_CHANNEL,
+                                                                            1e6 * 20_000 / (ms * 1e-3),
+                                                                            pk["sfu"])}
     net.close()
     del y
 
@@ -544,6 +611,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="also run the 64 batched heterogeneous networks (about a minute more)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (single neurons, BPTT layer, 1e6 neurons, GEMM)")
     ap.add_argument("--ncu-case", nargs="?", const="network", default=None,

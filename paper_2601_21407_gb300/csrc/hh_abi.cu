@@ -87,7 +87,7 @@ struct hh_net {
     cudaEvent_t ev_neuron[hh::kListSlots] = {};
     cudaEvent_t ev_route[hh::kListSlots] = {};
     int32_t W_pipe = 0;  // window length when routing overlaps the next window (0: serial)
-    unsigned long long* progress = nullptr;  // persistent kernel: done[4], routed[4]
+    unsigned long long* progress = nullptr;  // persistent kernel: done[4] at 0, routed[4] at 16 (own lines)
     int persistent_cap = -1;      // co-resident blocks of the persistent kernel (-1: not queried)
 
     // learned surrogate
@@ -596,7 +596,7 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
                 HH_CUDA(cudaEventCreateWithFlags(&n->ev_neuron[k], cudaEventDisableTiming));
                 HH_CUDA(cudaEventCreateWithFlags(&n->ev_route[k], cudaEventDisableTiming));
             }
-            HH_CUDA(n->alloc(&n->progress, 2 * hh::kPhaseSlots));
+            HH_CUDA(n->alloc(&n->progress, 32));
         }
     }
     HH_CUDA(cudaStreamSynchronize(st));
@@ -820,9 +820,9 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         const hh::RouteParams rp = net->route_params();
         const int32_t W = net->W_pipe;
         const int64_t n_win = (n_steps + W - 1) / W;
-        HH_CUDA(cudaMemsetAsync(net->progress, 0, 2 * hh::kPhaseSlots * sizeof(unsigned long long), net->st));
+        HH_CUDA(cudaMemsetAsync(net->progress, 0, 32 * sizeof(unsigned long long), net->st));
         HH_CUDA(cudaMemsetAsync(net->list.counter, 0, hh::kListSlots * sizeof(int32_t), net->st));
-        const hh::PhaseCounters pc{net->progress, net->progress + hh::kPhaseSlots};
+        const hh::PhaseCounters pc{net->progress, net->progress + 16};
         HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
             return hh::jit_launch_persistent(net->jit, p, rp, net->t, n_steps, W, net->window_index, I_steps, R,
                                              net->list, pc, net->st);

@@ -548,6 +548,41 @@ __device__ __forceinline__ unsigned long long nS_to_fixed(float w)
 // entries outside the row and issues one RED.ADD.64 per edge.  Two chunks
 // are in flight per iteration.  Warps `warp`, `warp + nw`, ... take spikes
 // `warp`, `warp + nw`, ... of the list.
+// Lane part of one 256-synapse chunk of an out-row: entries ea..ea+3 and
+// ea+128..ea+131 (zeros past e1; rows are padded by 4 entries).
+__device__ __forceinline__ void load_chunk(const RouteParams& RP, int64_t ea, int64_t e1, int4& pa, int4& pb,
+                                           float4& wa, float4& wb)
+{
+    const int64_t eb = ea + 128;
+    pa = make_int4(0, 0, 0, 0);
+    pb = pa;
+    wa = make_float4(0.f, 0.f, 0.f, 0.f);
+    wb = wa;
+    if (ea < e1) {
+        pa = __ldcs(reinterpret_cast<const int4*>(RP.out_post + ea));
+        wa = __ldcs(reinterpret_cast<const float4*>(RP.out_w + ea));
+    }
+    if (eb < e1) {
+        pb = __ldcs(reinterpret_cast<const int4*>(RP.out_post + eb));
+        wb = __ldcs(reinterpret_cast<const float4*>(RP.out_w + eb));
+    }
+}
+
+// The atomics of one loaded chunk (entries outside [e0, e1) skipped).
+__device__ __forceinline__ void deliver_chunk(unsigned long long* dst, int64_t ea, int64_t e0, int64_t e1,
+                                              const int4& pa, const int4& pb, const float4& wa, const float4& wb)
+{
+    const int64_t eb = ea + 128;
+    const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+    const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int64_t e = (q < 4 ? ea : eb) + (q & 3);
+        if (e >= e0 && e < e1)
+            atomicAdd(dst + pp[q], nS_to_fixed(ww[q]));
+    }
+}
+
 __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_t* __restrict__ st,
                                              const int32_t* __restrict__ ix, int64_t n, int64_t warp, int64_t nw)
 {
@@ -568,29 +603,26 @@ __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_
         unsigned long long* dst =
             reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
         const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
-        // synapse rows are read once per spike: streaming (evict-first) loads,
-        // so that they do not push the delay line out of L2
-        for (int64_t base = (e0 & ~(int64_t)3); base < e1; base += 256) {
-            const int64_t ea = base + 4 * lane;
-            const int64_t eb = ea + 128;
-            int4 pa = make_int4(0, 0, 0, 0), pb = pa;
-            float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
-            if (ea < e1) {
-                pa = __ldcs(reinterpret_cast<const int4*>(RP.out_post + ea));
-                wa = __ldcs(reinterpret_cast<const float4*>(RP.out_w + ea));
-            }
-            if (eb < e1) {
-                pb = __ldcs(reinterpret_cast<const int4*>(RP.out_post + eb));
-                wb = __ldcs(reinterpret_cast<const float4*>(RP.out_w + eb));
-            }
-            const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
-            const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int64_t e = (q < 4 ? ea : eb) + (q & 3);
-                if (e >= e0 && e < e1)
-                    atomicAdd(dst + pp[q], nS_to_fixed(ww[q]));
-            }
+        // 256 synapses per warp iteration, software-pipelined: the next
+        // chunk's (target, weight) loads are issued before this chunk's
+        // atomics, so two chunks are in flight per warp (the loop is
+        // latency-bound otherwise).  Streaming (evict-first) loads: the rows
+        // are read once per spike and must not push the delay line out of L2.
+        int64_t base = e0 & ~(int64_t)3;
+        if (base >= e1)
+            continue;
+        int4 pa, pb;
+        float4 wa, wb;
+        load_chunk(RP, base + 4 * lane, e1, pa, pb, wa, wb);
+        for (; base < e1; base += 256) {
+            int4 qa, qb;
+            float4 va, vb;
+            load_chunk(RP, base + 256 + 4 * lane, e1, qa, qb, va, vb);
+            deliver_chunk(dst, base + 4 * lane, e0, e1, pa, pb, wa, wb);
+            pa = qa;
+            pb = qb;
+            wa = va;
+            wb = vb;
         }
     }
 }
@@ -620,26 +652,10 @@ __device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t
             if (base < e1 && (!RP.open_loop || row < RP.n_window)) {
                 unsigned long long* dst = reinterpret_cast<unsigned long long*>(
                     (RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
-                const int64_t ea = base + 4 * lane;
-                const int64_t eb = ea + 128;
-                int4 pa = make_int4(0, 0, 0, 0), pb = pa;
-                float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
-                if (ea < e1) {
-                    pa = __ldcs(reinterpret_cast<const int4*>(RP.out_post + ea));
-                    wa = __ldcs(reinterpret_cast<const float4*>(RP.out_w + ea));
-                }
-                if (eb < e1) {
-                    pb = __ldcs(reinterpret_cast<const int4*>(RP.out_post + eb));
-                    wb = __ldcs(reinterpret_cast<const float4*>(RP.out_w + eb));
-                }
-                const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
-                const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int64_t e = (k < 4 ? ea : eb) + (k & 3);
-                    if (e >= e0 && e < e1)
-                        atomicAdd(dst + pp[k], nS_to_fixed(ww[k]));
-                }
+                int4 pa, pb;
+                float4 wa, wb;
+                load_chunk(RP, base + 4 * lane, e1, pa, pb, wa, wb);
+                deliver_chunk(dst, base + 4 * lane, e0, e1, pa, pb, wa, wb);
             }
         }
         sp += dsp;
@@ -848,7 +864,8 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
 
 // Progress counters of the persistent kernel (zeroed before each launch).
 // Window w counts in slot w mod kPhaseSlots of `done` once per neuron block
-// that finished it and of `routed` once per routing warp that delivered it;
+// that finished it and of `routed` once per block whose routing warps
+// delivered their share of it;
 // window w is complete when its slot reaches (w / kPhaseSlots + 1) x the
 // number of blocks or warps.  This is exact because no block or warp gets
 // more than two windows ahead of the slowest one (see persistent_body), so
@@ -857,8 +874,8 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
 // expiry the waiter records HH_STATUS_BARRIER_TIMEOUT and gives up.
 constexpr int kPhaseSlots = 4;
 struct PhaseCounters {
-    unsigned long long* done;    // [kPhaseSlots]
-    unsigned long long* routed;  // [kPhaseSlots]
+    unsigned long long* done;    // [kPhaseSlots], one count per neuron block
+    unsigned long long* routed;  // [kPhaseSlots], one count per block's routing warps (own 128-B line)
 };
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
@@ -875,12 +892,14 @@ __device__ __forceinline__ bool wait_at_least(const unsigned long long* c, unsig
     const volatile unsigned long long* p = c;
     if (*p < target) {
         const unsigned long long t0 = global_ns();
+        unsigned ns = 32;  // back-off: few pollers on a line every other SM reads
         while (*p < target) {
             if (global_ns() - t0 > kWaitLimitNs) {
                 atomicOr(status, HH_STATUS_BARRIER_TIMEOUT);
                 return false;
             }
-            __nanosleep(32);
+            __nanosleep(ns);
+            ns = ns < 1024 ? 2 * ns : ns;
         }
     }
     __threadfence();
@@ -905,6 +924,21 @@ __device__ __forceinline__ void neuron_bar()
 {
     asm volatile("barrier.sync 1, %0;" ::"n"(kPersistNeurons) : "memory");
 }
+// Barrier 2 spans the block's routing warps.
+__device__ __forceinline__ void router_bar()
+{
+    asm volatile("barrier.sync 2, %0;" ::"n"(32 * kPersistRouters) : "memory");
+}
+__device__ __forceinline__ bool router_all(bool p)
+{
+    int r;
+    asm volatile("{\n\t.reg .pred a, b;\n\tsetp.ne.s32 a, %1, 0;\n\tbarrier.red.and.pred b, 2, %2, a;\n\t"
+                 "selp.s32 %0, 1, 0, b;\n\t}"
+                 : "=r"(r)
+                 : "r"((int)p), "n"(32 * kPersistRouters)
+                 : "memory");
+    return r != 0;
+}
 __device__ __forceinline__ bool neuron_all(bool p)
 {
     int r;
@@ -919,22 +953,23 @@ __device__ __forceinline__ bool neuron_all(bool p)
 // The whole n_steps of a network in one cooperative launch (windows of
 // W <= D/2 steps, call-local window w in list slot (w_index0 + w) mod 3).
 // Dataflow instead of a grid barrier:
-//  - a neuron block integrates window w once every routing warp has routed
-//    window w - 2 (the input of window w comes from spikes at least
-//    D >= 2W steps earlier, i.e. from windows <= w - 2; warps route in
-//    order), then counts itself done with w;
-//  - a routing warp delivers window w once every neuron block is done with
-//    it, then counts itself.  Its targets lie in windows >= w + 2, whose
-//    delay-line slots are disjoint from those of the windows integrated
-//    meanwhile (w + 1 at most: a block in w + 2 waits for w to be routed);
+//  - a neuron block integrates window w once the routing warps of every
+//    block have routed window w - 2 (the input of window w comes from spikes
+//    at least D >= 2W steps earlier, i.e. from windows <= w - 2; routing
+//    goes in window order), then counts itself done with w;
+//  - a block's routing warps deliver their share of window w once every
+//    neuron block is done with it, then the block counts itself.  The
+//    targets lie in windows >= w + 2, whose delay-line slots are disjoint
+//    from those of the windows integrated meanwhile (w + 1 at most: a block
+//    in w + 2 waits for w to be routed);
 //  - the last window is routed by every warp of the grid once all blocks
 //    are done with it.
-// So a block in window k implies all blocks done with k - 2, and a warp
-// routing window k implies all warps done routing k - 2: nothing runs more
-// than two windows ahead of the slowest block or warp.
-// The three list counters are zero at launch; the last routing warp to
-// finish window w clears its slot, which window w + 3 reuses: a block
-// starting w + 3 has waited for window w + 1 to be routed, which that warp
+// So a block in window k implies all blocks done with k - 2, and routing of
+// window k implies all blocks done routing k - 2: nothing runs more than two
+// windows ahead of the slowest block.
+// The three list counters are zero at launch; the last block to finish
+// routing window w clears its slot, which window w + 3 reuses: a block
+// starting w + 3 has waited for window w + 1 to be routed, which that block
 // signals after the clear.
 template <int MAXG, int PREC, class Dyn>
 __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronParams& P, const RouteParams& RP,
@@ -957,24 +992,27 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
     };
     bool ok = true;
     if (threadIdx.x >= kPersistNeurons) {
+        // the block's routing warps wait and signal together: one poller and
+        // one count per block
+        const bool lead = threadIdx.x == kPersistNeurons;
         const int64_t r = (int64_t)blockIdx.x * kPersistRouters + (warp - kPersistNeurons / 32);
         for (int32_t w = 0; w + 1 < n_win; ++w) {
-            int go = 1;
-            if (lane == 0)
+            bool go = true;
+            if (lead)
                 go = window_done(w, pc.done, n_blocks);
-            if (!__shfl_sync(0xffffffffu, go, 0))
+            if (!router_all(go))
                 return;
             route_items(RP, list_step(w), list_idx(w), list_count(w), r, (int64_t)nR);
-            __syncwarp();
-            // the last warp to finish window w frees its list slot for window w + 3
-            if (lane == 0 && signal_done(pc.routed + w % kPhaseSlots) + 1 ==
-                                 (unsigned long long)(w / kPhaseSlots + 1) * nR)
+            router_bar();
+            // the last block to finish window w frees its list slot for window w + 3
+            if (lead && signal_done(pc.routed + w % kPhaseSlots) + 1 ==
+                            (unsigned long long)(w / kPhaseSlots + 1) * n_blocks)
                 L.counter[(int32_t)((w_index0 + w) % kListSlots)] = 0;
         }
-        int go = 1;
-        if (lane == 0 && n_win >= 1)
+        bool go = true;
+        if (lead && n_win >= 1)
             go = window_done(n_win - 1, pc.done, n_blocks);
-        ok = __shfl_sync(0xffffffffu, go, 0) != 0;
+        ok = router_all(go);
     } else {
         const int64_t gi = (int64_t)blockIdx.x * kPersistNeurons + threadIdx.x;
         const bool valid = gi < P.N;
@@ -994,7 +1032,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
             if (w >= 2) {
                 bool go = true;
                 if (threadIdx.x == 0)
-                    go = window_done(w - 2, pc.routed, nR);
+                    go = window_done(w - 2, pc.routed, n_blocks);
                 if (!neuron_all(go)) {
                     ok = false;
                     break;
