@@ -44,6 +44,8 @@ SYN = {"tau_E": W["tau_E"], "tau_I": W["tau_I"], "E_E": W["E_E"], "E_I": W["E_I"
        "area_cm2": W["area_cm2"]}
 BG = {"rate_hz": W["bg_rate_hz"], "K": W["bg_K"], "w": W["bg_w_nS"]}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes of one 20-step window launch of the 38k network (ncu, cold L2)
+WINDOW_TRAFFIC_BYTES = 13_850_368
 # SFU (MUFU) issue rate per SM per clock for ex2/rcp on this architecture and
 # the SM count / maximum clock of the part.
 SM_COUNT, MUFU_PER_SM_CLK, FP32_PER_SM_CLK = 152, 16, 128
@@ -318,7 +320,12 @@ def run_gpu(args):
                                   "avg_us": route_ms / max(1, n_launch_route) * 1e3}},
             "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops,
                          "unit": "Gop/s (SFU-class: exp + div)",
-                         "frac": achieved_gops / peak_gops, "traffic": None,
+                         "frac": achieved_gops / peak_gops,
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one hh_jit_window
+                         # launch (20 steps, cold L2) in an ncu capture of this kernel: the 16 B
+                         # of delay line per neuron-step plus the state, nothing re-read
+                         "traffic": WINDOW_TRAFFIC_BYTES if n_launch_route > 0 else None,
+                         "traffic_unit": "bytes per launch (ncu, cold L2)",
                          "peak_source": f"measured (hh_measure_peaks, all SMs, CUDA events): {n_exp} ex2.approx "
                                         f"+ {n_div} rcp.approx per neuron-step at the measured rates",
                          "nominal_peak": nominal_gops,
@@ -551,6 +558,7 @@ def ncu_case(name):
              spiking per step;
     network-persistent: the same with the 120 steps in one cooperative
              launch;
+    multichannel: 1e6 multi-channel neurons, two launches of 200 steps;
     gemm:    the layer's input projection (32000 x 1024 x 704, bf16) twice;
     layer:   the differentiable layer at full width (B=128, 700 inputs, 1,024
              neurons) for T=25 outer steps, forward and backward."""
@@ -558,6 +566,17 @@ def ncu_case(name):
 
     from paper_2601_21407_gb300 import hh
     torch.cuda.set_device(0)
+    if name == "multichannel":
+        y = inp.multi_channel_neurons(1_000_000, seed=0)
+        net = hh.Network(y["V0"], 0.025, I_const=y["I"], precision=hh.HH_PREC_FAST)
+        net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
+        rec, b = hh.make_record(1_000_000, 200, spike_cap=0)
+        for _ in range(2):
+            net.step(200, rec=rec)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "multichannel", "status": int(net.readout(hh.HH_READ_STATUS)[0])}))
+        net.close()
+        return
     if name == "gemm":
         M, N, K = 32000, 1024, 704
         A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
@@ -616,7 +635,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (single neurons, BPTT layer, 1e6 neurons, GEMM)")
     ap.add_argument("--ncu-case", nargs="?", const="network", default=None,
-                    choices=["network", "network-persistent", "gemm", "layer"],
+                    choices=["network", "network-persistent", "multichannel", "gemm", "layer"],
                     help="run a small fixed case used for ncu captures and exit")
     args = ap.parse_args()
     if args.ncu_case:

@@ -88,6 +88,13 @@ struct hh_net {
     cudaEvent_t ev_route[hh::kListSlots] = {};
     int32_t W_pipe = 0;  // window length when routing overlaps the next window (0: serial)
     unsigned long long* progress = nullptr;  // persistent kernel: done[4] at 0, routed[4] at 16 (own lines)
+    // the window schedule of a call as a CUDA graph: two executables used in
+    // turn (each updated in place when the next call has the same shape)
+    cudaGraphExec_t gexec[2] = {};
+    cudaEvent_t gdone[2] = {};
+    int gnext = 0;
+    cudaStream_t st_own = nullptr;  // capture stream when the caller's is the legacy default stream
+    cudaEvent_t ev_enter = nullptr, ev_leave = nullptr;
     int persistent_cap = -1;      // co-resident blocks of the persistent kernel (-1: not queried)
 
     // learned surrogate
@@ -174,6 +181,52 @@ struct hh_net {
             cudaStreamDestroy(st_route);
             st_route = nullptr;
         }
+        if (st_own) {
+            cudaStreamDestroy(st_own);
+            st_own = nullptr;
+        }
+        if (ev_enter)
+            cudaEventDestroy(ev_enter);
+        if (ev_leave)
+            cudaEventDestroy(ev_leave);
+        ev_enter = ev_leave = nullptr;
+        for (int k = 0; k < 2; ++k) {
+            if (gexec[k])
+                cudaGraphExecDestroy(gexec[k]);
+            if (gdone[k])
+                cudaEventDestroy(gdone[k]);
+            gexec[k] = nullptr;
+            gdone[k] = nullptr;
+        }
+    }
+
+    // Launch a captured window schedule on stream s: update the executable
+    // used two calls ago in place when the shape matches (after its launch
+    // has finished), else instantiate it anew.
+    cudaError_t launch_graph(cudaGraph_t g, cudaStream_t s)
+    {
+        const int k = gnext;
+        gnext ^= 1;
+        cudaError_t e = cudaSuccess;
+        if (!gdone[k] && (e = cudaEventCreateWithFlags(&gdone[k], cudaEventDisableTiming)) != cudaSuccess)
+            return e;
+        if (gexec[k]) {
+            if ((e = cudaEventSynchronize(gdone[k])) != cudaSuccess)
+                return e;
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(gexec[k], g, &info) != cudaSuccess) {
+                cudaGetLastError();  // the failed update is not sticky; instantiate instead
+                cudaGraphExecDestroy(gexec[k]);
+                gexec[k] = nullptr;
+            }
+        }
+        if (!gexec[k] && (e = cudaGraphInstantiate(&gexec[k], g, 0)) != cudaSuccess) {
+            gexec[k] = nullptr;
+            return e;
+        }
+        if ((e = cudaGraphLaunch(gexec[k], s)) != cudaSuccess)
+            return e;
+        return cudaEventRecord(gdone[k], s);
     }
 
     hh::NeuronParams neuron_params() const
@@ -592,6 +645,13 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
             int lo = 0, hi = 0;
             HH_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
             HH_CUDA(cudaStreamCreateWithPriority(&n->st_route, cudaStreamNonBlocking, lo));
+            if (!n->st) {
+                // the legacy default stream cannot be captured: calls on it run
+                // their schedule on a stream of the library, ordered by events
+                HH_CUDA(cudaStreamCreateWithFlags(&n->st_own, cudaStreamNonBlocking));
+                HH_CUDA(cudaEventCreateWithFlags(&n->ev_enter, cudaEventDisableTiming));
+                HH_CUDA(cudaEventCreateWithFlags(&n->ev_leave, cudaEventDisableTiming));
+            }
             for (int k = 0; k < hh::kListSlots; ++k) {
                 HH_CUDA(cudaEventCreateWithFlags(&n->ev_neuron[k], cudaEventDisableTiming));
                 HH_CUDA(cudaEventCreateWithFlags(&n->ev_route[k], cudaEventDisableTiming));
@@ -832,41 +892,91 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         const hh::RouteParams rp = net->route_params();
         const bool pipe = net->W_pipe > 0;
         const int32_t Wmax = net->has_syn ? (pipe ? net->W_pipe : net->D) : (1 << 30);
-        int64_t last_route = -1;
-        for (int32_t w0 = 0; w0 < n_steps; w0 += Wmax) {
-            const int32_t W = (n_steps - w0) < Wmax ? (n_steps - w0) : Wmax;
-            const int64_t gw = net->window_index;
-            const int32_t slot = (int32_t)(gw % hh::kListSlots);
-            hh::RecordParams Rw = R;
-            if (Rw.V_trace)
-                Rw.V_trace += (int64_t)w0 * Rw.n_trace;
-            const float* Iw = I_steps ? I_steps + (int64_t)w0 * net->N : nullptr;
-            // the input of this window was routed by window gw - 2
-            if (pipe && gw >= 2)
-                HH_CUDA(cudaStreamWaitEvent(net->st, net->ev_route[(gw - 2) % hh::kListSlots], 0));
-            HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
-                if (spec)
-                    return hh::jit_launch_window(net->jit, p, net->t + w0, W, slot, Iw, Rw, net->list, net->st);
-                return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, slot, Iw, Rw,
-                                             net->list, net->st);
-            }));
-            if (net->has_syn && pipe) {
-                HH_CUDA(cudaEventRecord(net->ev_neuron[slot], net->st));
-                HH_CUDA(cudaStreamWaitEvent(net->st_route, net->ev_neuron[slot], 0));
-                HH_CUDA(timed_on(net->st_route, HH_KERNEL_ROUTE,
-                                 [&] { return hh::launch_route_window(rp, net->list, slot, net->st_route); }));
-                HH_CUDA(cudaEventRecord(net->ev_route[slot], net->st_route));
-                last_route = gw;
-            } else if (net->has_syn) {
-                HH_CUDA(timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, slot, net->st); }));
-            } else {
-                HH_CUDA(cudaMemsetAsync(net->list.counter + slot, 0, sizeof(int32_t), net->st));
+        // Window schedule.  Waits on routing events of the previous call are
+        // not needed: the caller's stream waited for its last routing launch.
+        const int64_t gw_first = net->window_index;
+        auto enqueue = [&]() -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            int64_t last_route = -1;
+            for (int32_t w0 = 0; w0 < n_steps; w0 += Wmax) {
+                const int32_t W = (n_steps - w0) < Wmax ? (n_steps - w0) : Wmax;
+                const int64_t gw = net->window_index;
+                const int32_t slot = (int32_t)(gw % hh::kListSlots);
+                hh::RecordParams Rw = R;
+                if (Rw.V_trace)
+                    Rw.V_trace += (int64_t)w0 * Rw.n_trace;
+                const float* Iw = I_steps ? I_steps + (int64_t)w0 * net->N : nullptr;
+                // the input of this window was routed by window gw - 2
+                if (pipe && gw - 2 >= gw_first &&
+                    (e = cudaStreamWaitEvent(net->st, net->ev_route[(gw - 2) % hh::kListSlots], 0)) != cudaSuccess)
+                    return e;
+                e = timed(HH_KERNEL_NEURON, [&] {
+                    if (spec)
+                        return hh::jit_launch_window(net->jit, p, net->t + w0, W, slot, Iw, Rw, net->list, net->st);
+                    return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, slot, Iw, Rw,
+                                                 net->list, net->st);
+                });
+                if (e != cudaSuccess)
+                    return e;
+                if (net->has_syn && pipe) {
+                    if ((e = cudaEventRecord(net->ev_neuron[slot], net->st)) != cudaSuccess ||
+                        (e = cudaStreamWaitEvent(net->st_route, net->ev_neuron[slot], 0)) != cudaSuccess ||
+                        (e = timed_on(net->st_route, HH_KERNEL_ROUTE, [&] {
+                             return hh::launch_route_window(rp, net->list, slot, net->st_route);
+                         })) != cudaSuccess ||
+                        (e = cudaEventRecord(net->ev_route[slot], net->st_route)) != cudaSuccess)
+                        return e;
+                    last_route = gw;
+                } else if (net->has_syn) {
+                    e = timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, slot, net->st); });
+                } else {
+                    e = cudaMemsetAsync(net->list.counter + slot, 0, sizeof(int32_t), net->st);
+                }
+                if (e != cudaSuccess)
+                    return e;
+                net->window_index++;
             }
-            net->window_index++;
+            // the caller's stream sees every routing launch of this call complete
+            if (last_route >= 0)
+                e = cudaStreamWaitEvent(net->st, net->ev_route[last_route % hh::kListSlots], 0);
+            return e;
+        };
+        // With routing on a second stream the schedule is captured into a CUDA
+        // graph and launched as one (dependencies resolved on the device,
+        // without per-launch stream and event work); not while profiling.  On
+        // the legacy default stream, which cannot be captured, the capture and
+        // the graph use the library's own stream, entered and left through
+        // events so that the call stays ordered on the caller's stream.
+        if (pipe && net->has_syn && !net->profiling) {
+            const cudaStream_t user = net->st;
+            if (!user) {
+                HH_CUDA(cudaEventRecord(net->ev_enter, user));
+                HH_CUDA(cudaStreamWaitEvent(net->st_own, net->ev_enter, 0));
+                net->st = net->st_own;
+            }
+            cudaError_t e = cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                e = enqueue();
+                cudaGraph_t g = nullptr;
+                const cudaError_t e_end = cudaStreamEndCapture(net->st, &g);
+                if (e == cudaSuccess)
+                    e = e_end;
+                if (e == cudaSuccess)
+                    e = net->launch_graph(g, net->st);
+                if (g)
+                    cudaGraphDestroy(g);
+            }
+            if (!user) {
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(net->ev_leave, net->st);
+                if (e == cudaSuccess)
+                    e = cudaStreamWaitEvent(user, net->ev_leave, 0);
+                net->st = user;
+            }
+            HH_CUDA(e);
+        } else {
+            HH_CUDA(enqueue());
         }
-        // the caller's stream sees every routing launch of this call complete
-        if (last_route >= 0)
-            HH_CUDA(cudaStreamWaitEvent(net->st, net->ev_route[last_route % hh::kListSlots], 0));
     }
     net->t += n_steps;
     return HH_OK;

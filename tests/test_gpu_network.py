@@ -20,10 +20,10 @@ def _torch():
 
 
 def make_net(g, dt=0.025, D=40, bg=None, seed=0, precision=hh.HH_PREC_FAST, models=(inp.CLASSIC_HH,),
-             model_id=None, I=None, kernels=hh.HH_KERNELS_SPECIALISED):
+             model_id=None, I=None, kernels=hh.HH_KERNELS_SPECIALISED, stream=None):
     net = hh.Network(g["V0"], dt, csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
                      delay_steps=D, bg=bg, seed=seed, precision=precision, model_id=model_id,
-                     I_const=I, kernels=kernels)
+                     I_const=I, kernels=kernels, stream=stream)
     for k, m in enumerate(models):
         net.set_channels(k, m)
     return net
@@ -268,6 +268,43 @@ def test_persistent_matches_launches(D, chunks):
     for k in range(3):
         assert np.array_equal(sa[k], sb[k])
     assert len(sa[0]) > 50
+
+
+@pytest.mark.parametrize("kernels", [hh.HH_KERNELS_SPECIALISED, hh.HH_KERNELS_TABLE])
+def test_graph_schedule_matches_stream_schedule(kernels):
+    """On a caller stream the window schedule of each call is captured into
+    a CUDA graph (executables reused when a call has the same shape); with
+    profiling on it is enqueued launch by launch.  Both give bit-identical V,
+    rasters and traces over calls of repeated and changing lengths."""
+    torch = _torch()
+    g = inp.network(n=3000, k_in=300, seed=5, mu=0.0)
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
+    chunks = [400, 400, 400, 13, 400, 787, 400]
+    s = torch.cuda.Stream()
+
+    def run(profile):
+        net = make_net(g, bg=bg, seed=1, kernels=kernels, stream=s.cuda_stream)
+        net.profile(profile)
+        rec, b = hh.make_record(3000, max(chunks), trace=8, spike_cap=500_000)
+        traces = []
+        for c in chunks:
+            net.step(c, rec=rec)
+            s.synchronize()
+            traces.append(b["V_trace"][:c].cpu().numpy().copy())
+        s.synchronize()
+        out = (net.readout(hh.HH_READ_V), hh.spikes_to_numpy(b), traces,
+               int(net.readout(hh.HH_READ_STATUS)[0]))
+        net.close()
+        return out
+
+    a, p = run(False), run(True)
+    assert a[3] == 0 and p[3] == 0
+    assert np.array_equal(a[0], p[0])
+    for k in range(3):
+        assert np.array_equal(a[1][k], p[1][k])
+    for x, y in zip(a[2], p[2]):
+        assert np.array_equal(x, y)
+    assert len(a[1][0]) > 100
 
 
 def test_reset_restores_initial_state():
