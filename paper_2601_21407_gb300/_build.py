@@ -47,11 +47,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     # the shared device code is compiled into the library and also embedded
-    # verbatim for the run-time (NVRTC) specialisation of the neuron kernels
-    src = open(os.path.join(CSRC, "hh_device.cuh")).read()
-    assert ')HHSRC"' not in src
-    with open(os.path.join(BUILD, "hh_device_src.inc"), "w") as f:
-        f.write('R"HHSRC(' + src + ')HHSRC"\n')
+    # verbatim for the run-time (NVRTC) specialisation of the neuron and
+    # layer kernels
+    for name in ("hh_device", "hh_layer_device"):
+        src = open(os.path.join(CSRC, name + ".cuh")).read()
+        assert ')HHSRC"' not in src
+        with open(os.path.join(BUILD, name + "_src.inc"), "w") as f:
+            f.write('R"HHSRC(' + src + ')HHSRC"\n')
     cc = nvcc()
     cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(cc)))
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

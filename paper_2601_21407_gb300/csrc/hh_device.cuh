@@ -19,6 +19,7 @@ typedef long long int64_t;
 typedef unsigned long long uint64_t;
 typedef int int32_t;
 typedef unsigned int uint32_t;
+typedef unsigned short uint16_t;
 typedef unsigned char uint8_t;
 #else
 #include <cstdint>

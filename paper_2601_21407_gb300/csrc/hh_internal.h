@@ -73,6 +73,19 @@ cudaError_t surrogate_stats(const Surrogate* S, unsigned long long* host2, int32
 cudaError_t surrogate_reset_stats(Surrogate* S, cudaStream_t st);
 
 // Neuron kernels specialised for a model set, compiled with NVRTC (hh_jit.cu).
+// The differentiable layer's kernels compiled for its model (hh_jit.cu).
+struct LayerKernels {
+    cudaKernel_t fwd = nullptr;
+    cudaKernel_t recompute = nullptr;
+    cudaKernel_t bwd = nullptr;
+};
+struct LayerParams;
+bool jit_get_layer(const DevModels& M, int precision, LayerKernels* out, std::string* err);
+// Launch k(L, arg) with one thread per neuron-sample (n of them), blocks of
+// 128, `smem` bytes of dynamic shared memory.
+cudaError_t jit_launch_layer(cudaKernel_t k, const LayerParams& L, int arg, int64_t n, size_t smem,
+                             cudaStream_t st);
+
 // FP32 FMA, ex2.approx and rcp.approx results per second on the current device.
 cudaError_t measure_peaks(double* ffma, double* ex2, double* rcp, cudaStream_t st);
 

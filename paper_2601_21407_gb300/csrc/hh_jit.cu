@@ -20,11 +20,15 @@
 #include <nvrtc.h>
 
 #include "hh_internal.h"
+#include "hh_layer_device.cuh"
 
 namespace {
 
 const char kDeviceSrc[] =
 #include "hh_device_src.inc"
+    ;
+const char kLayerDeviceSrc[] =
+#include "hh_layer_device_src.inc"
     ;
 
 std::string flt(float x)
@@ -181,17 +185,14 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
 
 struct Entry {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t independent = nullptr;
-    cudaKernel_t window = nullptr;
-    cudaKernel_t indexed = nullptr;
-    cudaKernel_t persistent = nullptr;
+    std::vector<cudaKernel_t> kernels;  // in the order of the names compiled
     std::string log;
 };
 
 std::mutex g_mu;
 std::map<std::string, Entry>* g_cache = nullptr;
 
-bool compile(const std::string& src, Entry* e, std::string* err)
+bool compile(const std::string& src, const std::vector<const char*>& names, Entry* e, std::string* err)
 {
     nvrtcProgram prog;
     if (nvrtcCreateProgram(&prog, src.c_str(), "hh_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
@@ -221,18 +222,35 @@ bool compile(const std::string& src, Entry* e, std::string* err)
     if (getenv("HH_JIT_VERBOSE"))
         fprintf(stderr, "[libhh jit] %zu-byte cubin\n%s\n", n, log.c_str());
     cudaError_t ce = cudaLibraryLoadData(&e->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (ce == cudaSuccess)
-        ce = cudaLibraryGetKernel(&e->independent, e->lib, "hh_jit_independent");
-    if (ce == cudaSuccess)
-        ce = cudaLibraryGetKernel(&e->window, e->lib, "hh_jit_window");
-    if (ce == cudaSuccess)
-        ce = cudaLibraryGetKernel(&e->indexed, e->lib, "hh_jit_indexed");
-    if (ce == cudaSuccess)
-        ce = cudaLibraryGetKernel(&e->persistent, e->lib, "hh_jit_persistent");
+    for (const char* name : names) {
+        cudaKernel_t k = nullptr;
+        if (ce == cudaSuccess)
+            ce = cudaLibraryGetKernel(&k, e->lib, name);
+        e->kernels.push_back(k);
+    }
     if (ce != cudaSuccess) {
-        *err = std::string("loading the specialised neuron kernels failed: ") + cudaGetErrorString(ce);
+        *err = std::string("loading the specialised kernels failed: ") + cudaGetErrorString(ce);
         return false;
     }
+    return true;
+}
+
+// Compile (once per distinct source, for the life of the process) and look
+// up the named kernels.
+bool cached_compile(const std::string& src, const std::vector<const char*>& names, const Entry** out,
+                    std::string* err)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_cache)
+        g_cache = new std::map<std::string, Entry>();
+    auto it = g_cache->find(src);
+    if (it == g_cache->end()) {
+        Entry e;
+        if (!compile(src, names, &e, err))
+            return false;
+        it = g_cache->emplace(src, e).first;
+    }
+    *out = &it->second;
     return true;
 }
 
@@ -262,21 +280,67 @@ bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernel
             fclose(f);
         }
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_cache)
-        g_cache = new std::map<std::string, Entry>();
-    auto it = g_cache->find(src);
-    if (it == g_cache->end()) {
-        Entry e;
-        if (!compile(src, &e, err))
-            return false;
-        it = g_cache->emplace(src, e).first;
-    }
-    out->independent = it->second.independent;
-    out->window = it->second.window;
-    out->indexed = it->second.indexed;
-    out->persistent = it->second.persistent;
+    const Entry* e = nullptr;
+    if (!cached_compile(src, {"hh_jit_independent", "hh_jit_window", "hh_jit_indexed", "hh_jit_persistent"}, &e,
+                        err))
+        return false;
+    out->independent = e->kernels[0];
+    out->window = e->kernels[1];
+    out->indexed = e->kernels[2];
+    out->persistent = e->kernels[3];
     return true;
+}
+
+// The layer kernels for one model (model index 0 of M), compiled in as
+// constants like the network kernels.
+bool jit_get_layer(const DevModels& M, int precision, LayerKernels* out, std::string* err)
+{
+    std::string s = "// generated by libhh: differentiable-layer kernels specialised for one model\n";
+    s += abi_constants();
+    s += kDeviceSrc;
+    s += kLayerDeviceSrc;
+    s += "\nnamespace hh {\n\n";
+    s += model_function(M.m[0], 0);
+    s += "}  // namespace hh\n\n";
+    char b[2048];
+    snprintf(b, sizeof(b),
+             "constexpr int kJitMaxG = %d;\nconstexpr int kJitPrec = %d;\n\n"
+             "extern \"C\" __global__ void __launch_bounds__(128)\n"
+             "hh_jit_layer_fwd(const __grid_constant__ hh::LayerParams L, int t)\n"
+             "{\n    const hh::DevModel M = hh::jit_model_0();\n"
+             "    hh::layer_fwd_body<kJitMaxG, kJitPrec>(M, L, t);\n}\n\n"
+             "extern \"C\" __global__ void __launch_bounds__(128)\n"
+             "hh_jit_layer_recompute(const __grid_constant__ hh::LayerParams L, int g)\n"
+             "{\n    const hh::DevModel M = hh::jit_model_0();\n"
+             "    hh::layer_recompute_body<kJitMaxG, kJitPrec>(M, L, g);\n}\n\n"
+             "extern \"C\" __global__ void __launch_bounds__(128)\n"
+             "hh_jit_layer_bwd(const __grid_constant__ hh::LayerParams L, int t)\n"
+             "{\n    const hh::DevModel M = hh::jit_model_0();\n"
+             "    hh::layer_bwd_body<kJitMaxG, kJitPrec>(M, L, t);\n}\n",
+             M.m[0].n_gates > 0 ? M.m[0].n_gates : 1, precision);
+    s += b;
+    if (const char* path = getenv("HH_JIT_DUMP_LAYER")) {
+        if (FILE* f = fopen(path, "w")) {
+            fwrite(s.data(), 1, s.size(), f);
+            fclose(f);
+        }
+    }
+    const Entry* e = nullptr;
+    if (!cached_compile(s, {"hh_jit_layer_fwd", "hh_jit_layer_recompute", "hh_jit_layer_bwd"}, &e, err))
+        return false;
+    out->fwd = e->kernels[0];
+    out->recompute = e->kernels[1];
+    out->bwd = e->kernels[2];
+    return true;
+}
+
+cudaError_t jit_launch_layer(cudaKernel_t k, const LayerParams& L, int arg, int64_t n, size_t smem,
+                             cudaStream_t st)
+{
+    LayerParams l = L;
+    int a = arg;
+    void* args[] = {&l, &a};
+    return cudaLaunchKernel((const void*)k, dim3((unsigned)((n + 127) / 128)), dim3(128), args, smem, st);
 }
 
 cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, int64_t t0,
