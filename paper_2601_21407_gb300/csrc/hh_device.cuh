@@ -832,6 +832,12 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
                                             int32_t W, const float* __restrict__ I_steps,
                                             const RecordParams& R, const SpikeList& L, int32_t parity)
 {
+    // Programmatic dependent launch (when the launch asks for it; no-ops
+    // otherwise): the next window's blocks may be scheduled now, and this
+    // window waits for the previous kernel of the stream to complete before
+    // it touches the state that kernel wrote.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi == 0)
         L.counter[parity + 1 == kListSlots ? 0 : parity + 1] = 0;  // next window's slot (its reader has finished)

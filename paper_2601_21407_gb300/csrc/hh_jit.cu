@@ -369,7 +369,18 @@ cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_
     RecordParams r = R;
     SpikeList l = L;
     void* args[] = {&p, &t, &w, &I_steps, &r, &l, &par};
-    return cudaLaunchKernel((const void*)K.window, grid, block, args, 0, st);
+    // programmatic dependent launch: scheduled while the previous window
+    // runs, released by its completion (griddepcontrol in the kernel)
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)K.window, args);
 }
 
 // Blocks of the persistent kernel (kPersistNeurons neurons each) that can
