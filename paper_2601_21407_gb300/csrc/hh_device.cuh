@@ -107,6 +107,8 @@ struct NeuronParams {
 // thresholds compared without a loop on every step (the rest only after a
 // word that passes all of them)
 constexpr int kPoissonUnroll = 4;
+// steps of delay-line reads kept in flight by the window kernels
+constexpr int kRingAhead = 2;
 
 struct RecordParams {
     float* V_trace;
@@ -770,22 +772,36 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
                                              const Between& between)
 {
     uint4 rnd = make_uint4(0, 0, 0, 0);
+    // The delay-line slots of the next kRingAhead steps are in flight in a
+    // register queue: the step itself is shorter than an L2 round trip.
+    // (Slots past the window are read and discarded; inside it the slots are
+    // distinct, W <= R, and only cleared after their own step.)
     int32_t ring_slot = (int32_t)(t0 % P.R);
-    long long nE = 0, nI = 0;
-    if (W > 0) {
-        nE = __ldcg(P.ringE + (int64_t)ring_slot * P.N + i);
-        nI = __ldcg(P.ringI + (int64_t)ring_slot * P.N + i);
+    int32_t far_slot = ring_slot;
+    long long qE[kRingAhead], qI[kRingAhead];
+#pragma unroll
+    for (int a = 0; a < kRingAhead; ++a) {
+        qE[a] = __ldcg(P.ringE + (int64_t)far_slot * P.N + i);
+        qI[a] = __ldcg(P.ringI + (int64_t)far_slot * P.N + i);
+        far_slot = far_slot + 1 == P.R ? 0 : far_slot + 1;
     }
     int32_t* lstep = L.step + lslot * L.cap;
     int32_t* lidx = L.idx + lslot * L.cap;
+    // unrolled by the queue depth, so that the queue rotates by renaming
+    // registers instead of moving values whose loads are still in flight
+#pragma unroll kRingAhead
     for (int32_t k = 0; k < W; ++k) {
         const int64_t t = t0 + k;
-        const long long e = nE, h = nI;
+        const long long e = qE[0], h = qI[0];
+#pragma unroll
+        for (int a = 0; a + 1 < kRingAhead; ++a) {
+            qE[a] = qE[a + 1];
+            qI[a] = qI[a + 1];
+        }
+        qE[kRingAhead - 1] = __ldcg(P.ringE + (int64_t)far_slot * P.N + i);
+        qI[kRingAhead - 1] = __ldcg(P.ringI + (int64_t)far_slot * P.N + i);
+        far_slot = far_slot + 1 == P.R ? 0 : far_slot + 1;
         const int32_t next_slot = ring_slot + 1 == P.R ? 0 : ring_slot + 1;
-        // prefetch of the next slot without a branch (after the last step it
-        // reads a slot of a later window and is discarded)
-        nE = __ldcg(P.ringE + (int64_t)next_slot * P.N + i);
-        nI = __ldcg(P.ringI + (int64_t)next_slot * P.N + i);
         // a. delayed synaptic input (fixed point 2^-32 nS) and background
         // (added unconditionally: + 0 changes no bit, and the step stays
         // free of branches the scheduler cannot look across)
