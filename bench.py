@@ -135,6 +135,30 @@ def mufu_ops_per_neuron_step(model):
     return n_exp + 1, n_div + 1
 
 
+def reduce_over_ranks(ms, spikes, events, world, dev):
+    """Replicas only: the job's time is the slowest rank's (MAX), its spikes
+    and synaptic events the sum over ranks.  Single process: unchanged."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    tot = torch.tensor([spikes, events], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(tot[0].item()), float(tot[1].item())
+
+
+def aggregate_rates(ms_max, spikes_all, events_all, steps, world):
+    """Whole-job rates of `world` replicas of the network, each simulating
+    `steps` steps of STEPS_PER_SIM time steps (weak scaling): neuron-steps/s,
+    synaptic events/s and the mean firing rate in Hz."""
+    neuron_steps = float(W["n"]) * STEPS_PER_SIM * steps * world
+    value = neuron_steps / (ms_max * 1e-3)
+    events_per_s = events_all / (ms_max * 1e-3)
+    mean_rate = spikes_all / (W["n"] * world * steps * W["T_ms"] * 1e-3)
+    return value, events_per_s, mean_rate
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -201,17 +225,8 @@ def run_gpu(args):
     events_total = int((counts.to(torch.int64) * out_deg_t).sum().item()) * args.steps
     status = int(net.readout(hh.HH_READ_STATUS)[0])
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    tot = torch.tensor([spikes_total, events_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    neuron_steps = float(W["n"]) * STEPS_PER_SIM * args.steps * world
-    value = neuron_steps / (ms_max * 1e-3)
-    events_per_s = float(tot[1].item()) / (ms_max * 1e-3)
-    mean_rate = float(tot[0].item()) / (W["n"] * world * args.steps * W["T_ms"] * 1e-3)
+    ms_max, spikes_all, events_all = reduce_over_ranks(ms, spikes_total, events_total, world, dev)
+    value, events_per_s, mean_rate = aggregate_rates(ms_max, spikes_all, events_all, args.steps, world)
 
     # kernel timing pass (hh_profile brackets each launch with CUDA events on
     # the network's stream); not part of the timed region above

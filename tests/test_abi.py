@@ -80,7 +80,7 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("field,value", [("n_neurons", 0), ("dt_ms", 0.0), ("dt_ms", -1.0),
                                          ("n_nets", 0), ("precision", 7), ("v_update", 3),
-                                         ("V0", None)])
+                                         ("kernels", 3), ("kernels", -1), ("V0", None)])
 def test_create_rejects_bad_descriptor(field, value):
     d, keep = _desc(**{field: value})
     h = C.c_void_p()
