@@ -756,22 +756,21 @@ __device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams&
 // W <= D time steps of one network neuron with its state in registers.
 // The delay-line slots of the window were completed by earlier routing;
 // they are read through L2 (.cg: they were written by atomics from other
-// blocks) one step ahead, and cleared after use.  Spikes go to list slot
+// blocks) kRingAhead steps ahead, and cleared after use.  Spikes go to list slot
 // `lslot` (and to the caller's record).
 // `between(k)` runs after step k with the whole warp (all lanes, valid or
 // not): the persistent kernel routes part of the previous window there.
 struct NoWork {
     __device__ __forceinline__ void operator()(int32_t) const {}
 };
-template <int MAXG, int PREC, class Dyn, class Between>
-__device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
-                                             int64_t i, int64_t t0, int32_t W, const float* __restrict__ I_steps,
-                                             const RecordParams& R, float* V_trace, int32_t slot,
-                                             const SpikeList& L, int32_t lslot, State<MAXG, PREC>& s,
-                                             float& gE, float& gI, float Ic, int32_t& cnt, uint2 key,
-                                             const Between& between)
+template <int MAXG, int PREC, bool BG, class Dyn, class Between>
+__device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
+                                                int64_t i, int64_t t0, int32_t W,
+                                                const float* __restrict__ I_steps, const RecordParams& R,
+                                                float* V_trace, int32_t slot, const SpikeList& L, int32_t lslot,
+                                                State<MAXG, PREC>& s, float& gE, float& gI, float Ic,
+                                                int32_t& cnt, uint2 key, const Between& between)
 {
-    uint4 rnd = make_uint4(0, 0, 0, 0);
     // The delay-line slots of the next kRingAhead steps are in flight in a
     // register queue: the step itself is shorter than an L2 round trip.
     // (Slots past the window are read and discarded; inside it the slots are
@@ -787,10 +786,8 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
     }
     int32_t* lstep = L.step + lslot * L.cap;
     int32_t* lidx = L.idx + lslot * L.cap;
-    // unrolled by the queue depth, so that the queue rotates by renaming
-    // registers instead of moving values whose loads are still in flight
-#pragma unroll kRingAhead
-    for (int32_t k = 0; k < W; ++k) {
+    // one step; `word` is the background word of step t0 + k
+    auto step = [&](int32_t k, uint32_t word) {
         const int64_t t = t0 + k;
         const long long e = qE[0], h = qI[0];
 #pragma unroll
@@ -804,9 +801,12 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
         const int32_t next_slot = ring_slot + 1 == P.R ? 0 : ring_slot + 1;
         // a. delayed synaptic input (fixed point 2^-32 nS) and background
         // (added unconditionally: + 0 changes no bit, and the step stays
-        // free of branches the scheduler cannot look across)
-        gE += fixed_to_nS(e);
-        gI += fixed_to_nS(h);
+        // free of branches the scheduler cannot look across).  The
+        // conductance arithmetic that crosses steps is written with explicit
+        // rounding, so that no copy of the step fuses the previous step's
+        // decay into this addition: every copy gives the same bits.
+        gE = __fadd_rn(gE, fixed_to_nS(e));
+        gI = __fadd_rn(gI, fixed_to_nS(h));
         if (valid) {
             const int64_t o = (int64_t)ring_slot * P.N + i;
             if (e)
@@ -814,29 +814,74 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
             if (h)
                 P.ringI[o] = 0;
         }
-        if (P.bg_n > 0) {
-            if (k == 0 || (t & 3) == 0) {
-                const uint64_t q = (uint64_t)t >> 2;
-                rnd = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
-            }
-            const int32_t c = poisson_count(pick(rnd, (int)(t & 3)), P.bg_thr, P.bg_n);
-            gE += (float)c * P.bg_w;
-        }
+        if (BG)
+            gE = fmaf((float)poisson_count(word, P.bg_thr, P.bg_n), P.bg_w, gE);
         const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
         const float Vt = s.V;
-        dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, gE * P.to_mS, P.E_E, gI * P.to_mS,
-                                      P.E_I, s);
+        dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, __fmul_rn(gE, P.to_mS), P.E_E,
+                                      __fmul_rn(gI, P.to_mS), P.E_I, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
         cnt += spk;
         list_append(spk, (int32_t)t, (int32_t)i, L.counter + lslot, lstep, lidx, L.cap);
         record_spikes(spk, (int32_t)t, (int32_t)i, P.theta, Vt, s.V, R, P.status);
         if (slot >= 0)
             V_trace[(int64_t)k * R.n_trace + slot] = s.V;
-        gE *= P.decE;
-        gI *= P.decI;
+        gE = __fmul_rn(gE, P.decE);
+        gI = __fmul_rn(gI, P.decI);
         ring_slot = next_slot;
         between(k);
+    };
+    // The background words of steps 4q..4q+3 come from one Philox block
+    // (counter q).  Steps are grouped by those blocks, so inside a group the
+    // draw is not behind a branch and overlaps the first step's gates.
+    auto draw = [&](int64_t t) {
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (BG) {
+            const uint64_t q = (uint64_t)t >> 2;
+            r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
+        }
+        return r;
+    };
+    int32_t k = 0;
+    const int32_t head = min(W, (int32_t)((4 - (t0 & 3)) & 3));
+    if (head > 0) {
+        const uint4 r = draw(t0);
+        for (; k < head; ++k)
+            step(k, pick(r, (int)((t0 + k) & 3)));
     }
+    // unrolled by four steps, a multiple of the queue depth, so that the
+    // queue rotates by renaming registers instead of moving values whose
+    // loads are still in flight
+    static_assert(4 % kRingAhead == 0, "group of four steps");
+#pragma unroll 1
+    for (; k + 4 <= W; k += 4) {
+        const uint4 r = draw(t0 + k);
+        step(k, r.x);
+        step(k + 1, r.y);
+        step(k + 2, r.z);
+        step(k + 3, r.w);
+    }
+    if (k < W) {
+        const uint4 r = draw(t0 + k);
+        for (; k < W; ++k)
+            step(k, pick(r, (int)((t0 + k) & 3)));
+    }
+}
+
+template <int MAXG, int PREC, class Dyn, class Between>
+__device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
+                                             int64_t i, int64_t t0, int32_t W, const float* __restrict__ I_steps,
+                                             const RecordParams& R, float* V_trace, int32_t slot,
+                                             const SpikeList& L, int32_t lslot, State<MAXG, PREC>& s,
+                                             float& gE, float& gI, float Ic, int32_t& cnt, uint2 key,
+                                             const Between& between)
+{
+    if (P.bg_n > 0)
+        window_steps_bg<MAXG, PREC, true>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L, lslot, s,
+                                          gE, gI, Ic, cnt, key, between);
+    else
+        window_steps_bg<MAXG, PREC, false>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L, lslot,
+                                           s, gE, gI, Ic, cnt, key, between);
 }
 
 // Network window: W <= D steps; spikes go to the window list for routing.
