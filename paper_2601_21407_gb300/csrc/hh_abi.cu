@@ -93,6 +93,10 @@ struct hh_net {
     cudaGraphExec_t gexec[2] = {};
     cudaEvent_t gdone[2] = {};
     int gnext = 0;
+    // the call each executable was captured from (its kernel arguments and
+    // launch shape); a call identical to the last one relaunches it as is
+    std::string gsig[2];
+    int glast = -1;
     cudaStream_t st_own = nullptr;  // capture stream when the caller's is the legacy default stream
     cudaEvent_t ev_enter = nullptr, ev_leave = nullptr;
     int persistent_cap = -1;      // co-resident blocks of the persistent kernel (-1: not queried)
@@ -203,10 +207,12 @@ struct hh_net {
     // Launch a captured window schedule on stream s: update the executable
     // used two calls ago in place when the shape matches (after its launch
     // has finished), else instantiate it anew.
-    cudaError_t launch_graph(cudaGraph_t g, cudaStream_t s)
+    cudaError_t launch_graph(cudaGraph_t g, cudaStream_t s, const std::string& sig)
     {
         const int k = gnext;
         gnext ^= 1;
+        gsig[k].clear();
+        glast = -1;
         cudaError_t e = cudaSuccess;
         if (!gdone[k] && (e = cudaEventCreateWithFlags(&gdone[k], cudaEventDisableTiming)) != cudaSuccess)
             return e;
@@ -226,7 +232,21 @@ struct hh_net {
         }
         if ((e = cudaGraphLaunch(gexec[k], s)) != cudaSuccess)
             return e;
+        gsig[k] = sig;
+        glast = k;
         return cudaEventRecord(gdone[k], s);
+    }
+
+    // Launch the last executable again when this call's schedule is the one
+    // it was captured from (false: capture anew).  Launches of one
+    // executable on one stream run in order.
+    bool relaunch_graph(const std::string& sig, cudaStream_t s, cudaError_t* e)
+    {
+        if (glast < 0 || !gexec[glast] || gsig[glast] != sig)
+            return false;
+        if ((*e = cudaGraphLaunch(gexec[glast], s)) == cudaSuccess)
+            *e = cudaEventRecord(gdone[glast], s);
+        return true;
     }
 
     hh::NeuronParams neuron_params() const
@@ -954,17 +974,41 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
                 HH_CUDA(cudaStreamWaitEvent(net->st_own, net->ev_enter, 0));
                 net->st = net->st_own;
             }
-            cudaError_t e = cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                e = enqueue();
-                cudaGraph_t g = nullptr;
-                const cudaError_t e_end = cudaStreamEndCapture(net->st, &g);
-                if (e == cudaSuccess)
-                    e = e_end;
-                if (e == cudaSuccess)
-                    e = net->launch_graph(g, net->st);
-                if (g)
-                    cudaGraphDestroy(g);
+            // everything the captured schedule depends on: repeated calls
+            // with the same arguments from the same state (a reset, then
+            // the same run) skip the capture and the executable update
+            std::string sig;
+            auto put = [&sig](const void* x, size_t n) { sig.append(static_cast<const char*>(x), n); };
+            const int64_t wmod = net->window_index % hh::kListSlots;
+            const void* kw = spec ? (const void*)net->jit.window : nullptr;
+            const cudaStream_t cs = net->st;
+            put(&n_steps, sizeof n_steps);
+            put(&net->t, sizeof net->t);
+            put(&wmod, sizeof wmod);
+            put(&p, sizeof p);
+            put(&R, sizeof R);
+            put(&rp, sizeof rp);
+            put(&I_steps, sizeof I_steps);
+            put(&kw, sizeof kw);
+            put(&cs, sizeof cs);
+            put(&net->precision, sizeof net->precision);
+            put(&net->models, sizeof net->models);
+            cudaError_t e = cudaSuccess;
+            if (!net->relaunch_graph(sig, net->st, &e)) {
+                e = cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    e = enqueue();
+                    cudaGraph_t g = nullptr;
+                    const cudaError_t e_end = cudaStreamEndCapture(net->st, &g);
+                    if (e == cudaSuccess)
+                        e = e_end;
+                    if (e == cudaSuccess)
+                        e = net->launch_graph(g, net->st, sig);
+                    if (g)
+                        cudaGraphDestroy(g);
+                }
+            } else {
+                net->window_index += (n_steps + Wmax - 1) / Wmax;
             }
             if (!user) {
                 if (e == cudaSuccess)

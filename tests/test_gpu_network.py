@@ -307,6 +307,46 @@ def test_graph_schedule_matches_stream_schedule(kernels):
     assert len(a[1][0]) > 100
 
 
+def test_repeated_call_relaunches_same_schedule():
+    """A call identical to the previous one (same state after a reset, same
+    arguments) relaunches the captured schedule; a call that differs only in
+    its record buffers or its length is captured anew and writes where it
+    is told."""
+    torch = _torch()
+    g = inp.network(n=3000, k_in=300, seed=5, mu=0.0)
+    bg = {"rate_hz": 5.0, "K": 500, "w": 1.5}
+    s = torch.cuda.Stream()
+    net = make_net(g, bg=bg, seed=1, stream=s.cuda_stream)
+    V0 = torch.as_tensor(g["V0"], device="cuda")
+    recs = [hh.make_record(3000, 600, trace=4, spike_cap=200_000) for _ in range(2)]
+
+    def run(k, n):
+        rec, b = recs[k]
+        with torch.cuda.stream(s):
+            b["counts"].zero_()
+            b["n_spikes"].zero_()
+            b["V_trace"].zero_()
+        net.reset(V0)
+        net.step(n, rec=rec)
+        s.synchronize()
+        return (net.readout(hh.HH_READ_V), b["counts"].cpu().numpy().copy(), b["V_trace"][:n].cpu().numpy().copy())
+
+    a = run(0, 600)
+    b = run(0, 600)
+    with torch.cuda.stream(s):
+        recs[0][1]["counts"].fill_(-7)
+    c = run(1, 600)
+    assert (recs[0][1]["counts"].cpu().numpy() == -7).all()
+    d = run(1, 450)
+    e = run(1, 600)
+    assert a[1].sum() > 100
+    for x in (b, c, e):
+        assert np.array_equal(a[0], x[0]) and np.array_equal(a[1], x[1]) and np.array_equal(a[2], x[2])
+    assert np.array_equal(a[2][:450], d[2])
+    assert int(net.readout(hh.HH_READ_STATUS)[0]) == 0
+    net.close()
+
+
 def test_reset_restores_initial_state():
     torch = _torch()
     g = inp.network(n=800, k_in=80, seed=6, mu=0.5)
