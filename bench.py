@@ -79,8 +79,18 @@ class ClockSampler:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # the timed region starts once the sampler is producing rows; the
+            # rows written before it are not counted
+            t_end = time.time() + 3.0
+            self.skip = 0
+            while time.time() < t_end:
+                with open(self.path) as f:
+                    self.skip = sum(1 for _ in f)
+                if self.skip > 0 or self.proc.poll() is not None:
+                    break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -101,6 +111,8 @@ class ClockSampler:
                 except ValueError:
                     pass
         os.unlink(self.path)
+        if len(rows) > getattr(self, "skip", 0):
+            rows = rows[self.skip:]
         if not rows:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -641,7 +653,7 @@ def ncu_case(name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
