@@ -763,7 +763,7 @@ __device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams&
 struct NoWork {
     __device__ __forceinline__ void operator()(int32_t) const {}
 };
-template <int MAXG, int PREC, bool BG, class Dyn, class Between>
+template <int MAXG, int PREC, bool BG, int GROUP, class Dyn, class Between>
 __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
                                                 int64_t i, int64_t t0, int32_t W,
                                                 const float* __restrict__ I_steps, const RecordParams& R,
@@ -832,8 +832,7 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         between(k);
     };
     // The background words of steps 4q..4q+3 come from one Philox block
-    // (counter q).  Steps are grouped by those blocks, so inside a group the
-    // draw is not behind a branch and overlaps the first step's gates.
+    // (counter q).
     auto draw = [&](int64_t t) {
         uint4 r = make_uint4(0, 0, 0, 0);
         if (BG) {
@@ -842,6 +841,21 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         }
         return r;
     };
+    if (GROUP != 4) {
+        // one step per iteration, the block drawn at its first step (the
+        // smaller loop body, for models whose step is long)
+        uint4 r = make_uint4(0, 0, 0, 0);
+#pragma unroll kRingAhead
+        for (int32_t k = 0; k < W; ++k) {
+            const int64_t t = t0 + k;
+            if (BG && (k == 0 || (t & 3) == 0))
+                r = draw(t);
+            step(k, pick(r, (int)(t & 3)));
+        }
+        return;
+    }
+    // GROUP == 4: steps grouped by Philox block, so inside a group the draw
+    // is not behind a branch and overlaps the first step's gates.
     int32_t k = 0;
     const int32_t head = min(W, (int32_t)((4 - (t0 & 3)) & 3));
     if (head > 0) {
@@ -868,7 +882,10 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
     }
 }
 
-template <int MAXG, int PREC, class Dyn, class Between>
+// GROUP: 4 = steps grouped by background block (short model steps), 1 = one
+// step per iteration (long model steps: the four-step body would not stay in
+// the instruction cache).  Both run the same step arithmetic.
+template <int MAXG, int PREC, int GROUP, class Dyn, class Between>
 __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
                                              int64_t i, int64_t t0, int32_t W, const float* __restrict__ I_steps,
                                              const RecordParams& R, float* V_trace, int32_t slot,
@@ -877,18 +894,18 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
                                              const Between& between)
 {
     if (P.bg_n > 0)
-        window_steps_bg<MAXG, PREC, true>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L, lslot, s,
-                                          gE, gI, Ic, cnt, key, between);
+        window_steps_bg<MAXG, PREC, true, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
+                                                 lslot, s, gE, gI, Ic, cnt, key, between);
     else
-        window_steps_bg<MAXG, PREC, false>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L, lslot,
-                                           s, gE, gI, Ic, cnt, key, between);
+        window_steps_bg<MAXG, PREC, false, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
+                                                  lslot, s, gE, gI, Ic, cnt, key, between);
 }
 
 // Network window: W <= D steps; spikes go to the window list for routing.
 // The input of every step in the window comes from spikes at least D steps
 // earlier, already routed by previous launches, so neurons are independent
 // inside the window.
-template <int MAXG, int PREC, class Dyn>
+template <int MAXG, int PREC, int GROUP, class Dyn>
 __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& P, int64_t t0,
                                             int32_t W, const float* __restrict__ I_steps,
                                             const RecordParams& R, const SpikeList& L, int32_t parity)
@@ -917,7 +934,7 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         slot = -1;
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     int32_t cnt = 0;
-    window_steps<MAXG, PREC>(dyn, mid, P, valid, i, t0, W, I_steps, R, R.V_trace, slot, L, parity, s, gE, gI,
+    window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, R.V_trace, slot, L, parity, s, gE, gI,
                              Ic, cnt, key, NoWork{});
     if (valid) {
         store_state(P, i, s);
@@ -1039,7 +1056,7 @@ __device__ __forceinline__ bool neuron_all(bool p)
 // routing window w clears its slot, which window w + 3 reuses: a block
 // starting w + 3 has waited for window w + 1 to be routed, which that block
 // signals after the clear.
-template <int MAXG, int PREC, class Dyn>
+template <int MAXG, int PREC, int GROUP, class Dyn>
 __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronParams& P, const RouteParams& RP,
                                                 int64_t t0, int32_t n_steps, int32_t W, int64_t w_index0,
                                                 const float* __restrict__ I_steps, const RecordParams& R,
@@ -1107,7 +1124,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
                 }
             }
             const int32_t Ww = min(W, n_steps - w * W);
-            window_steps<MAXG, PREC>(dyn, mid, P, valid, i, t0 + (int64_t)w * W, Ww,
+            window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0 + (int64_t)w * W, Ww,
                                      I_steps ? I_steps + (int64_t)w * W * P.N : nullptr, R,
                                      R.V_trace ? R.V_trace + (int64_t)w * W * R.n_trace : nullptr, slot, L,
                                      (int32_t)((w_index0 + w) % kListSlots), s, gE, gI, Ic, cnt, key, NoWork{});

@@ -155,18 +155,27 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
          "                                         float gsI, float EI, State<MAXG, PREC>& s) const\n    {\n";
     s += dispatch("neuron_step<MAXG, PREC>(M, dt, v_update, I, gsE, EE, gsI, EI, s)");
     s += "    }\n};\n\n}  // namespace hh\n\n";
-    char b[2048];
+    // Window steps grouped by background block (four steps unrolled) for one
+    // installed model with a short step; one step per iteration otherwise,
+    // where four unrolled copies of the dispatch would leave the
+    // instruction cache.
+    const int group = (n_inst == 1 && max_gates <= 4) ? 4 : 1;
+    // With long model steps the window kernel is held to 64 registers (8
+    // blocks of 128 per SM): their networks are large and throughput-bound,
+    // and need the resident warps.
+    const char* window_bounds = group == 4 ? "128" : "128, 8";
+    char b[4096];
     snprintf(b, sizeof(b),
-             "constexpr int kJitMaxG = %d;\nconstexpr int kJitPrec = %d;\n\n"
+             "constexpr int kJitMaxG = %d;\nconstexpr int kJitPrec = %d;\nconstexpr int kJitGroup = %d;\n\n"
              "extern \"C\" __global__ void __launch_bounds__(128)\n"
              "hh_jit_independent(const __grid_constant__ hh::NeuronParams P, long long t0, int n_steps,\n"
              "                   const float* __restrict__ I_steps, const __grid_constant__ hh::RecordParams R)\n"
              "{\n    hh::independent_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, t0, n_steps, I_steps, R);\n}\n\n"
-             "extern \"C\" __global__ void __launch_bounds__(128)\n"
+             "extern \"C\" __global__ void __launch_bounds__(%s)\n"
              "hh_jit_window(const __grid_constant__ hh::NeuronParams P, long long t0, int W,\n"
              "              const float* __restrict__ I_steps, const __grid_constant__ hh::RecordParams R,\n"
              "              const __grid_constant__ hh::SpikeList L, int parity)\n"
-             "{\n    hh::window_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, t0, W, I_steps, R, L, parity);\n}\n\n"
+             "{\n    hh::window_body<kJitMaxG, kJitPrec, kJitGroup>(hh::JitDyn{}, P, t0, W, I_steps, R, L, parity);\n}\n\n"
              "extern \"C\" __global__ void __launch_bounds__(128)\n"
              "hh_jit_indexed(const __grid_constant__ hh::NeuronParams P, const int* __restrict__ list,\n"
              "               const int* __restrict__ n_list, long long t0, int n_steps,\n"
@@ -177,8 +186,8 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
              "                  long long t0, int n_steps, int W, long long w_index0, const float* __restrict__ I_steps,\n"
              "                  const __grid_constant__ hh::RecordParams R, const __grid_constant__ hh::SpikeList L,\n"
              "                  const __grid_constant__ hh::PhaseCounters pc)\n"
-             "{\n    hh::persistent_body<kJitMaxG, kJitPrec>(hh::JitDyn{}, P, RP, t0, n_steps, W, w_index0, I_steps, R, L, pc);\n}\n",
-             max_gates, precision);
+             "{\n    hh::persistent_body<kJitMaxG, kJitPrec, kJitGroup>(hh::JitDyn{}, P, RP, t0, n_steps, W, w_index0, I_steps, R, L, pc);\n}\n",
+             max_gates, precision, group, window_bounds);
     s += b;
     return s;
 }
