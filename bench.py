@@ -130,21 +130,33 @@ def peaks():
 
 
 def mufu_ops_per_neuron_step(model):
-    """Algorithmic transcendental work of one exponential-Euler neuron step,
-    as (exponentials, divisions): one exponential per exp/sigmoid/linoid
-    rate (two for bell), one division per sigmoid/linoid/bell rate, per gate
-    one division (p_inf) and one exponential (the relaxation factor), and for
-    V one division (V_inf) and one exponential.  Classic HH: (10, 7)."""
+    """Transcendental work of one exponential-Euler neuron step in the SFU
+    formulation, as (exponentials, divisions).  A rate takes one exponential
+    per exp/sigmoid/linoid (two for bell) and one division per
+    sigmoid/linoid/bell.  An alpha-beta gate adds one division (p_inf); an
+    inf-tau or calcium gate's dt/tau takes none for a constant tau, one
+    exponential pair and one division for a bell-shaped tau with an offset
+    (none without), else the rate's work and one division; a calcium gate's
+    p_inf is one division.  Every gate adds one exponential (the relaxation
+    factor), and V one division and one exponential.  Classic HH: (10, 7)."""
+    work = {"const": (0, 0), "exp": (1, 0), "sigmoid": (1, 1), "linoid": (1, 1), "bell": (2, 1)}
     n_exp = n_div = 0
     for ch in model["channels"]:
         for g in ch["gates"]:
-            for f in (g["f1"], g["f2"]):
-                e, d = {"const": (0, 0), "exp": (1, 0), "sigmoid": (1, 1), "linoid": (1, 1),
-                        "bell": (2, 1)}[f[0]]
-                n_exp += e
-                n_div += d
-            n_exp += 1
-            n_div += 1
+            f1, f2 = g["f1"], g["f2"]
+            if g["kind"] == "ab":
+                e = work[f1[0]][0] + work[f2[0]][0]
+                v = work[f1[0]][1] + work[f2[0]][1] + 1
+            else:
+                e, v = (0, 1) if g["kind"] == "ca" else work[f1[0]]
+                if f2[0] == "bell":
+                    e += 2
+                    v += 1 if f2[6] != 0.0 else 0
+                elif f2[0] != "const":
+                    e += work[f2[0]][0]
+                    v += work[f2[0]][1] + 1
+            n_exp += e + 1
+            n_div += v
     return n_exp + 1, n_div + 1
 
 

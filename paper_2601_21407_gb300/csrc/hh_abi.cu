@@ -366,6 +366,9 @@ hh::DevFn prep_fn(const hh_fn& f)
     d.ik2 = (float)(1.0 / k2);
     d.s2 = (float)(1.4426950408889634 / k2);
     d.b2 = (float)(-(double)f.vh2 * 1.4426950408889634 / k2);
+    d.ia = f.a != 0.0f ? (float)(1.0 / (double)f.a) : 0.0f;
+    const double ac = (double)f.a + (double)f.c;
+    d.irate = ac != 0.0 ? (float)(1.0 / ac) : 0.0f;
     return d;
 }
 

@@ -42,6 +42,8 @@ struct DevFn {
     float a, c;
     float vh, k, ik, s, b;     // first exponential
     float vh2, ik2, s2, b2;    // second exponential (bell)
+    float ia;                  // 1/a (0 when a = 0)
+    float irate;               // 1/(a + c) (0 when a + c = 0): a constant rate's reciprocal
 };
 
 struct DevGate {
@@ -219,6 +221,23 @@ __device__ __forceinline__ float rate(const DevFn& f, float V)
     return r + f.c;
 }
 
+// dt/tau for a time constant tau = c + form(V).  The SFU path takes a
+// constant tau's reciprocal from the model table, and writes a bell-shaped
+// tau = a/(e1 + e2) + c as dt (e1 + e2)/(a + c (e1 + e2)): one division
+// instead of two, none when c = 0.
+template <bool FAST>
+__device__ __forceinline__ float dt_over_tau(const DevFn& f, float V, float dt)
+{
+    using M = Mth<FAST>;
+    if (FAST && f.form == HH_FN_CONST)
+        return dt * f.irate;
+    if (FAST && f.form == HH_FN_BELL) {
+        const float e = M::expv(f, V) + M::expv2(f, V);
+        return f.c == 0.0f ? (dt * f.ia) * e : M::div(dt * e, fmaf(f.c, e, f.a));
+    }
+    return M::div(dt, rate<FAST>(f, V));
+}
+
 // Steady-state value and dt/tau of one gate at (V, Ca).
 template <bool FAST>
 __device__ __forceinline__ void gate_inf_z(const DevGate& g, float V, float Ca, float dt, float& inf,
@@ -232,10 +251,10 @@ __device__ __forceinline__ void gate_inf_z(const DevGate& g, float V, float Ca, 
         z = dt * s;
     } else if (g.kind == HH_GATE_INFTAU) {
         inf = rate<FAST>(g.f1, V);
-        z = M::div(dt, rate<FAST>(g.f2, V));
+        z = dt_over_tau<FAST>(g.f2, V, dt);
     } else {
         inf = M::div(Ca, Ca + g.f1.a);
-        z = M::div(dt, rate<FAST>(g.f2, V));
+        z = dt_over_tau<FAST>(g.f2, V, dt);
     }
 }
 

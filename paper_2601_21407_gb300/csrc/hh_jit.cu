@@ -45,7 +45,7 @@ void emit_fn(std::string& s, const char* path, const hh::DevFn& f)
     s += b;
     const struct { const char* n; float v; } fields[] = {
         {"a", f.a}, {"c", f.c}, {"vh", f.vh}, {"k", f.k}, {"ik", f.ik}, {"s", f.s}, {"b", f.b},
-        {"vh2", f.vh2}, {"ik2", f.ik2}, {"s2", f.s2}, {"b2", f.b2}};
+        {"vh2", f.vh2}, {"ik2", f.ik2}, {"s2", f.s2}, {"b2", f.b2}, {"ia", f.ia}, {"irate", f.irate}};
     for (const auto& fl : fields)
         s += std::string("    ") + path + "." + fl.n + " = " + flt(fl.v) + ";\n";
 }
