@@ -128,7 +128,7 @@ typedef struct {
  * divisions are evaluated:
  *   HH_PREC_FAST        FP32 on the SFU: ex2.approx for the exponentials of
  *                       the rate functions, rcp.approx for divisions, and a
- *                       degree-8 Taylor polynomial of 1 - e^{-z} for z < 0.5;
+ *                       degree-5 Taylor polynomial of 1 - e^{-z} for z < 0.125;
  *   HH_PREC_ACCURATE    FP32 with IEEE division, expf and expm1f;
  *   HH_PREC_COMPENSATED as ACCURATE, on a two-float (hi + lo) state: each
  *                       increment is added by an error-free two-sum, so the
