@@ -45,8 +45,8 @@ SYN = {"tau_E": W["tau_E"], "tau_I": W["tau_I"], "E_E": W["E_E"], "E_I": W["E_I"
 BG = {"rate_hz": W["bg_rate_hz"], "K": W["bg_K"], "w": W["bg_w_nS"]}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) of one 20-step window launch of the 38k network
-# (ncu, cold L2; the kernel with steps grouped by background block)
-WINDOW_TRAFFIC_BYTES = 14_507_520
+# (ncu, cold L2; the current window kernel)
+WINDOW_TRAFFIC_BYTES = 14_508_544
 # SFU (MUFU) issue rate per SM per clock for ex2/rcp on this architecture and
 # the SM count / maximum clock of the part.
 SM_COUNT, MUFU_PER_SM_CLK, FP32_PER_SM_CLK = 152, 16, 128
