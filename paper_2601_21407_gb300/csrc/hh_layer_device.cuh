@@ -32,23 +32,38 @@ __device__ __forceinline__ float smooth_d(float x, float beta)
     return 0.5f * beta / (d * d);
 }
 
-// value (without the offset c) and derivative d/dV of a rate form, accurate FP32
+// 1 - e^{-y} for either sign of y on the SFU path: the Taylor polynomial of
+// -expm1(-y) up to y^5 for |y| < 0.125 (truncation < 4.3e-8 relative),
+// 1 - 2^{-y log2 e} beyond (no cancellation there).
+__device__ __forceinline__ float em1_signed(float y)
+{
+    const float y2 = y * y;
+    const float c = fmaf(y2, fmaf(y2, 1.0f / 120.0f, fmaf(y, -1.0f / 24.0f, 1.0f / 6.0f)), fmaf(y, -0.5f, 1.0f));
+    const float far = 1.0f - ex2a(-y * kLog2e);
+    return fabsf(y) < 0.125f ? y * c : far;
+}
+
+// Value (with the offset c) and derivative d/dV of a rate form.  FAST: the
+// SFU exponential and reciprocal; otherwise IEEE FP32 (expf, expm1f,
+// division).
+template <bool FAST>
 __device__ __forceinline__ void rate_vd(const DevFn& f, float V, float& r, float& dr)
 {
+    using M = Mth<FAST>;
     switch (f.form) {
     case HH_FN_CONST:
         r = f.a;
         dr = 0.0f;
         break;
     case HH_FN_EXP: {
-        const float e = expf((V - f.vh) * f.ik);
+        const float e = M::expv(f, V);
         r = f.a * e;
         dr = r * f.ik;
         break;
     }
     case HH_FN_SIGMOID: {
-        const float e = expf((V - f.vh) * f.ik);
-        const float q = 1.0f / (1.0f + e);
+        const float e = M::expv(f, V);
+        const float q = M::div(1.0f, 1.0f + e);
         r = f.a * q;
         dr = -f.a * e * q * q * f.ik;
         break;
@@ -60,18 +75,18 @@ __device__ __forceinline__ void rate_vd(const DevFn& f, float V, float& r, float
             r = f.a * f.k * (1.0f + 0.5f * y + y * y * (1.0f / 12.0f));
             dr = f.a * (0.5f + y * (1.0f / 6.0f));
         } else {
-            const float em = -expm1f(-y);  // 1 - e^{-y}
-            const float g = y / em;
-            r = f.a * f.k * g;
-            dr = f.a * (em - y * (1.0f - em)) / (em * em);
+            const float em = FAST ? em1_signed(y) : -expm1f(-y);  // 1 - e^{-y}
+            const float ie = M::div(1.0f, em);
+            r = f.a * f.k * (y * ie);
+            dr = f.a * (em - y * (1.0f - em)) * (ie * ie);
         }
         break;
     }
     default: {  // bell
-        const float e1 = expf((V - f.vh) * f.ik), e2 = expf((V - f.vh2) * f.ik2);
-        const float den = e1 + e2;
-        r = f.a / den;
-        dr = -f.a * (e1 * f.ik + e2 * f.ik2) / (den * den);
+        const float e1 = M::expv(f, V), e2 = M::expv2(f, V);
+        const float id = M::div(1.0f, e1 + e2);
+        r = f.a * id;
+        dr = -f.a * (e1 * f.ik + e2 * f.ik2) * (id * id);
         break;
     }
     }
@@ -80,11 +95,13 @@ __device__ __forceinline__ void rate_vd(const DevFn& f, float V, float& r, float
 
 // Reverse of one substep (state V, p before it, current I): on entry lamV,
 // lamP hold the adjoints of the state after the substep; on exit those of
-// the state before it; lamI accumulates dL/dI.
-template <int MAXG>
+// the state before it; lamI accumulates dL/dI.  FAST: SFU exponentials,
+// reciprocals and 1 - e^{-z}, as in the forward substep of that precision.
+template <int MAXG, bool FAST>
 __device__ __forceinline__ void substep_adjoint(const DevModel& M, const State<MAXG, 1>& s0, float dt, float I,
                                                 float& lamV, float* lamP, float& lamI)
 {
+    using Mt = Mth<FAST>;
     const float V = s0.V;
     float pn[MAXG], Eq[MAXG], dpdV[MAXG];
 #pragma unroll
@@ -98,21 +115,23 @@ __device__ __forceinline__ void substep_adjoint(const DevModel& M, const State<M
             float inf, dinf, z, dz;
             if (g.kind == HH_GATE_AB) {
                 float al, dal, be, dbe;
-                rate_vd(g.f1, V, al, dal);
-                rate_vd(g.f2, V, be, dbe);
+                rate_vd<FAST>(g.f1, V, al, dal);
+                rate_vd<FAST>(g.f2, V, be, dbe);
                 const float sum = al + be;
-                inf = al / sum;
-                dinf = (dal * be - al * dbe) / (sum * sum);
+                const float is = Mt::div(1.0f, sum);
+                inf = al * is;
+                dinf = (dal * be - al * dbe) * (is * is);
                 z = dt * sum;
                 dz = dt * (dal + dbe);
             } else {
                 float tau, dtau;
-                rate_vd(g.f1, V, inf, dinf);
-                rate_vd(g.f2, V, tau, dtau);
-                z = dt / tau;
-                dz = -dt * dtau / (tau * tau);
+                rate_vd<FAST>(g.f1, V, inf, dinf);
+                rate_vd<FAST>(g.f2, V, tau, dtau);
+                const float it = Mt::div(1.0f, tau);
+                z = dt * it;
+                dz = -dt * dtau * (it * it);
             }
-            const float E = -expm1f(-z);
+            const float E = em1<FAST>(z);
             Eq[q] = E;
             pn[q] = p + (inf - p) * E;
             dpdV[q] = E * dinf + (inf - p) * (1.0f - E) * dz;
@@ -133,9 +152,10 @@ __device__ __forceinline__ void substep_adjoint(const DevModel& M, const State<M
                 }
             }
     }
-    const float EV = -expm1f(-dt * G * M.inv_C);
-    const float A = (I - Ip) / G;
-    lamI += lamV * EV / G;
+    const float EV = em1<FAST>(dt * G * M.inv_C);
+    const float iG = Mt::div(1.0f, G);
+    const float A = (I - Ip) * iG;
+    lamI += lamV * EV * iG;
     float lamVpre = lamV * (1.0f - EV);
     float lamPn[MAXG];
 #pragma unroll
@@ -147,7 +167,7 @@ __device__ __forceinline__ void substep_adjoint(const DevModel& M, const State<M
         if (q < M.n_gates && M.gate_last[q]) {
             const int c = M.gate_ch[q];
             const int f = M.ch_first[c], ng = M.ch_ng[c];
-            const float dVdg = -EV * ((V - M.gate_E[q]) + A) / G + A * (1.0f - EV) * dt * M.inv_C;
+            const float dVdg = -EV * ((V - M.gate_E[q]) + A) * iG + A * (1.0f - EV) * dt * M.inv_C;
             const float lg = lamV * dVdg * s0.gq[q];
 #pragma unroll
             for (int r = 0; r < MAXG; ++r) {
@@ -346,7 +366,7 @@ __device__ __forceinline__ void layer_bwd_body(const DevModel& M, const LayerPar
 #pragma unroll
         for (int q = 0; q < MAXG; ++q)
             s0.p[q] = Ps[((k - 1) * MAXG + q) * nt + tid];
-        substep_adjoint<MAXG>(M, s0, L.dt, I, lamV, lamP, lamI);
+        substep_adjoint<MAXG, PREC == HH_PREC_FAST>(M, s0, L.dt, I, lamV, lamP, lamI);
         if (L.smooth)
             lamV -= ds * smooth_s(Vk - L.theta, L.beta) * smooth_d(Vp - L.theta, L.beta);
     }
