@@ -477,9 +477,56 @@ def spikes_to_numpy(b):
     return step[o], idx[o], frac[o]
 
 
+_layer_fn = None
+
+
+def layer_function():
+    """torch.autograd.Function over one Layer: the forward sets the weights
+    (hh_layer_set_weights) and runs hh_layer_forward, giving the mean loss
+    and the logits; the backward runs hh_backward (the hand-derived adjoint
+    with recomputation from checkpoints) and scales its weight gradients by
+    the incoming gradient of the loss.  The spike inputs and labels get no
+    gradient; the logits are not differentiable.  The layer's stream must be
+    the current torch stream (the default: both are the legacy stream), and
+    the backward belongs to the layer's last forward: a later forward on the
+    same layer makes an earlier graph's backward raise."""
+    global _layer_fn
+    if _layer_fn is None:
+        import torch
+
+        class _LayerFn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, layer, X, labels, W_in, W_rec, W_out, bias):
+                _, B, _, _, n_out = layer.shape
+                layer.set_weights(W_in.detach(), W_rec.detach(), W_out.detach(), bias.detach())
+                loss = torch.zeros((), dtype=torch.float32, device=X.device)
+                logits = torch.zeros((B, n_out), dtype=torch.float32, device=X.device)
+                layer.forward(X.contiguous(), labels.to(torch.int32).contiguous(), loss, logits)
+                ctx.layer = layer
+                ctx.forward_id = layer._forward_id
+                ctx.shapes = (tuple(W_in.shape), tuple(W_rec.shape), tuple(W_out.shape), tuple(bias.shape))
+                ctx.mark_non_differentiable(logits)
+                return loss, logits
+
+            @staticmethod
+            def backward(ctx, g_loss, g_logits):
+                layer = ctx.layer
+                if layer._forward_id != ctx.forward_id:
+                    raise RuntimeError("the layer ran another forward after this one; its backward is lost")
+                dev = g_loss.device
+                grads = [torch.empty(s, dtype=torch.float32, device=dev) for s in ctx.shapes]
+                layer.backward(*grads)
+                return (None, None, None) + tuple(g * g_loss for g in grads)
+
+        _layer_fn = _LayerFn
+    return _layer_fn
+
+
 class Layer:
     """Owns one hh_layer (differentiable recurrent HH layer).  Device tensors
     are torch tensors; the library does the work."""
+
+    _forward_id = 0
 
     def __init__(self, model: dict, *, batch, n_in, n_hidden, n_out, n_steps, substeps=10,
                  dt=0.01, theta=0.0, v_init=-65.0, beta=0.5, precision=HH_PREC_FAST, smooth=False,
@@ -499,10 +546,16 @@ class Layer:
     def forward(self, X, labels, loss, logits=None):
         _check(lib().hh_layer_forward(self.handle, X.data_ptr(), labels.data_ptr(), loss.data_ptr(),
                                       None if logits is None else logits.data_ptr()))
+        self._forward_id += 1
 
     def backward(self, dW_in, dW_rec, dW_out, dbias):
         g = hh_grads(dW_in.data_ptr(), dW_rec.data_ptr(), dW_out.data_ptr(), dbias.data_ptr())
         _check(lib().hh_backward(self.handle, C.byref(g)))
+
+    def loss(self, X, labels, W_in, W_rec, W_out, bias):
+        """The mean cross-entropy loss as a differentiable torch function of
+        the weights (see layer_function); returns (loss, logits)."""
+        return layer_function().apply(self, X, labels, W_in, W_rec, W_out, bias)
 
     def readout(self, what):
         T, B, _, N, _ = self.shape

@@ -128,3 +128,38 @@ def test_layer_full_size_sampled():
     agree = (g["spikes"][:, idx] == sp).mean()
     assert agree >= 0.9999, agree
     assert np.abs(g["logits"][idx] - aux["logits"].numpy()).max() <= 2e-3
+
+
+def test_layer_autograd_function():
+    """loss.backward() through the torch.autograd.Function gives exactly the
+    gradients of hh_backward (the same kernels), scaled by the incoming
+    gradient; the spike inputs get none; after a second forward the first
+    graph's backward raises."""
+    torch = _torch()
+    T, B, n_in, N, n_out = 20, 3, 16, 32, 4
+    d = small_case(1, T, B, n_in, N, n_out)
+    lay = hh.Layer(HH, batch=B, n_in=n_in, n_hidden=N, n_out=n_out, n_steps=T, substeps=10, dt=0.01,
+                   precision=hh.HH_PREC_FAST, checkpoint_every=7)
+    W = [torch.tensor(d[k], dtype=torch.float32, device="cuda", requires_grad=True)
+         for k in ("W_in", "W_rec", "W_out", "bias")]
+    X = torch.as_tensor(d["X"], device="cuda")
+    y = torch.as_tensor(d["labels"], device="cuda")
+    loss, logits = lay.loss(X, y, *W)
+    assert loss.requires_grad and not logits.requires_grad
+    (2.5 * loss).backward()
+    lay.set_weights(*[w.detach() for w in W])
+    l2 = torch.zeros(1, device="cuda")
+    lay.forward(X, y, l2)
+    g = [torch.zeros_like(w) for w in W]
+    lay.backward(*g)
+    torch.cuda.synchronize()
+    assert float(loss.item()) == float(l2.item())
+    assert all(float(x.abs().max()) > 0 for x in g)
+    for w, gd in zip(W, g):
+        assert torch.equal(w.grad, 2.5 * gd)
+    loss_a, _ = lay.loss(X, y, *W)
+    loss_b, _ = lay.loss(X, y, *W)
+    with pytest.raises(RuntimeError):
+        loss_a.backward()
+    loss_b.backward()
+    lay.close()
