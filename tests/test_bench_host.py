@@ -17,3 +17,28 @@ def test_sfu_work_per_neuron_step():
     constant time constant none."""
     assert bench.mufu_ops_per_neuron_step(inp.CLASSIC_HH) == (10, 7)
     assert bench.mufu_ops_per_neuron_step(inp.MULTI_CHANNEL) == (26, 16)
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The oracle arm prints one JSON line with the contract's keys, on the
+    benchmark's workload and metric, with the oracle's set-up subtracted."""
+    import json
+    monkeypatch.setenv("HH_REF_SAMPLE_STEPS", "4")
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class Args:
+        steps, warmup = 1, 3
+
+    bench.run_reference(Args())
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in r, k
+    assert r["impl"] == "reference" and r["dtype"] == "f64" and r["value"] > 0
+    assert r["config"] == bench.workload_config()
+    assert r["cpu_baseline"]["kind"] == "oracle" and r["cpu_baseline"]["value"] == r["value"]
+    assert r["e2e"]["value"] == r["value"] and r["e2e"]["h2d_bytes_per_step"] == 0
+    assert "subtracted" in r["cpu_baseline"]["sample"]
