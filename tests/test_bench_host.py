@@ -1,4 +1,5 @@
-"""Host-side pieces of bench.py that need no GPU."""
+"""Host-side pieces that need no GPU: the benchmark's work counting and
+oracle arm, and the autograd wrapper's own logic."""
 import os
 import sys
 
@@ -42,3 +43,47 @@ def test_reference_arm_line(monkeypatch, capsys):
     assert r["cpu_baseline"]["kind"] == "oracle" and r["cpu_baseline"]["value"] == r["value"]
     assert r["e2e"]["value"] == r["value"] and r["e2e"]["h2d_bytes_per_step"] == 0
     assert "subtracted" in r["cpu_baseline"]["sample"]
+
+
+def test_layer_function_host_logic():
+    """The autograd wrapper's own logic, on a stand-in for the library layer
+    (CPU tensors): the weights go to set_weights before the forward, the
+    backward's gradients come back scaled by the incoming gradient, the
+    spike inputs and labels get none, and a second forward makes the first
+    graph's backward raise."""
+    import pytest
+    import torch
+
+    from paper_2601_21407_gb300 import hh
+
+    class FakeLayer:
+        shape = (5, 2, 3, 4, 2)  # T, B, n_in, N, n_out
+        _forward_id = 0
+
+        def set_weights(self, *w):
+            self.w = [x.clone() for x in w]
+
+        def forward(self, X, labels, loss, logits):
+            loss.fill_(float(sum(x.sum() for x in self.w)))
+            logits.fill_(1.0)
+            self._forward_id += 1
+
+        def backward(self, *g):
+            for k, x in enumerate(g):
+                x.fill_(k + 1.0)
+
+    lay = FakeLayer()
+    W = [torch.randn(s, requires_grad=True) for s in ((3, 4), (4, 4), (2, 4), (4,))]
+    X = torch.zeros((5, 2, 3))
+    y = torch.zeros(2, dtype=torch.int32)
+    loss, logits = hh.layer_function().apply(lay, X, y, *W)
+    assert torch.equal(lay.w[1], W[1].detach())
+    assert loss.requires_grad and not logits.requires_grad
+    (3.0 * loss).backward()
+    for k, w in enumerate(W):
+        assert torch.equal(w.grad, torch.full_like(w, 3.0 * (k + 1)))
+    a, _ = hh.layer_function().apply(lay, X, y, *W)
+    b, _ = hh.layer_function().apply(lay, X, y, *W)
+    with pytest.raises(RuntimeError):
+        a.backward()
+    b.backward()
