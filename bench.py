@@ -397,6 +397,17 @@ def sfu_roofline_frac(model, neuron_steps_per_s, peaks):
     return neuron_steps_per_s * (n_exp / peaks["ex2_per_s"] + n_div / peaks["rcp_per_s"])
 
 
+def bptt_sfu_roofline_frac(model, B, N, T, K, bptt_steps_per_s, peaks):
+    """Fraction of the SFU bound of one forward + backward pass of the
+    differentiable layer: four passes of T x K neuron-substeps over B x N
+    neurons (the forward, the segment recompute, the backward's recompute of
+    each outer step's substeps, and the adjoint sweep, whose SFU work per
+    substep equals a forward substep's for alpha-beta gates)."""
+    n_exp, n_div = mufu_ops_per_neuron_step(model)
+    t = 4.0 * T * K * B * N * (n_exp / peaks["ex2_per_s"] + n_div / peaks["rcp_per_s"])
+    return bptt_steps_per_s * t
+
+
 def extra_batched(dev, peaks):
     """The 64 batched heterogeneous networks: sizes LogUniform(1e3, 5e4),
     in-degree U{100..1000}, lognormal weights, half classic and half
@@ -512,6 +523,8 @@ def extras(dev, pk):
     both = timed(lambda: (lay.forward(X, lab, loss), lay.backward(*g)), reps=3)
     out["bptt_layer_b128_t250"] = {"bptt_steps_per_s": 1e3 / both, "forward_ms": fwd,
                                    "backward_ms": both - fwd, "loss": float(loss.item()),
+                                   "sfu_roofline_frac": bptt_sfu_roofline_frac(inp.CLASSIC_HH, 128, 1024, 250, 10,
+                                                                               1e3 / both, pk["sfu"]),
                                    "status": int(lay.readout(hh.HH_LAYER_STATUS)[0])}
     lay.close()
 

@@ -87,3 +87,14 @@ def test_layer_function_host_logic():
     with pytest.raises(RuntimeError):
         a.backward()
     b.backward()
+
+
+def test_bptt_sfu_bound():
+    """One forward + backward of the 128 x 1,024-neuron layer over 250 x 10
+    substeps is four passes of 3.28e8 classic neuron-substeps (10 ex2 + 7
+    rcp each): 3.15 ms at 1e13 ex2/s and 5e12 rcp/s, so 69 passes per
+    second sit at 21.7 % of that bound."""
+    pk = {"ex2_per_s": 1e13, "rcp_per_s": 5e12}
+    t = bench.bptt_sfu_roofline_frac(inp.CLASSIC_HH, 128, 1024, 250, 10, 1.0, pk)
+    assert abs(t - 4 * 250 * 10 * 128 * 1024 * (10 / 1e13 + 7 / 5e12)) < 1e-12
+    assert abs(bench.bptt_sfu_roofline_frac(inp.CLASSIC_HH, 128, 1024, 250, 10, 69.0, pk) - 0.2171) < 1e-3
