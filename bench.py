@@ -342,6 +342,7 @@ def run_gpu(args):
         peak_gops = mufu / t_sfu / 1e9
         nominal_gops = SM_COUNT * MUFU_PER_SM_CLK * sm_max * 1e6 / 1e9
         cpu = cpu_baseline_sample(cores=os.cpu_count()) if not args.no_cpu_baseline else None
+        cpu1 = cpu_baseline_sample(cores=1, sim_steps=200) if not args.no_cpu_baseline else None
         line = {
             "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
             "value": value, "unit": "neuron-steps/s", "n_gpus": world, "steps": args.steps,
@@ -377,6 +378,7 @@ def run_gpu(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+            line["cpu_baseline_single_core"] = cpu1
         if not args.no_extras:
             line["extra"] = extras(dev, dict(pk, sfu=sfu_peaks))
             if args.batched:
@@ -563,7 +565,7 @@ def cpu_baseline_sample(cores, sim_steps=None):
     return {"value": W["n"] * sim_steps / dt_s, "unit": "neuron-steps/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{sim_steps} time steps ({sim_steps * W['dt']:.0f} ms) of the full "
-                      f"38,000-neuron network, FP64, OpenMP over neurons; "
+                      f"38,000-neuron network, FP64, OpenMP over neurons ({cores} thread{'s' if cores != 1 else ''}); "
                       f"{int(r['counts'].sum())} spikes"}
 
 

@@ -98,3 +98,11 @@ def test_bptt_sfu_bound():
     t = bench.bptt_sfu_roofline_frac(inp.CLASSIC_HH, 128, 1024, 250, 10, 1.0, pk)
     assert abs(t - 4 * 250 * 10 * 128 * 1024 * (10 / 1e13 + 7 / 5e12)) < 1e-12
     assert abs(bench.bptt_sfu_roofline_frac(inp.CLASSIC_HH, 128, 1024, 250, 10, 69.0, pk) - 0.2171) < 1e-3
+
+
+def test_cpu_baseline_sample_single_core():
+    """The oracle timed on one host thread: the baseline dict the bench line
+    carries (value, unit, cores, kind, sample)."""
+    r = bench.cpu_baseline_sample(cores=1, sim_steps=5)
+    assert r["cores"] == 1 and r["kind"] == "oracle" and r["unit"] == "neuron-steps/s"
+    assert r["value"] > 0 and "(1 thread)" in r["sample"]
