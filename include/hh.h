@@ -262,7 +262,9 @@ typedef struct {
 typedef struct {
     float* V_trace;           /* device [n_steps][n_trace]: V after each step */
     const int32_t* trace_idx; /* device [n_trace] neuron indices, or NULL for
-                                 neurons 0..n_trace-1                         */
+                                 neurons 0..n_trace-1.  A neuron listed more
+                                 than once is recorded in the last of its
+                                 rows; its earlier rows are left unwritten    */
     int32_t n_trace;
     hh_spike* spikes;         /* device [spike_cap], unordered                */
     int64_t spike_cap;
@@ -418,11 +420,19 @@ typedef struct {
     void* stream;
 } hh_layer_desc;
 
+/* Gradient outputs of a backward pass, caller-owned device buffers,
+ * overwritten (not accumulated).  hh_backward needs the first four;
+ * hh_backward_from skips every NULL field. */
 typedef struct {
-    float* dW_in;   /* device [n_in][N]   */
-    float* dW_rec;  /* device [N][N]      */
-    float* dW_out;  /* device [n_out][N]  */
-    float* dbias;   /* device [N]         */
+    float* dW_in;   /* device [n_in][N]                                    */
+    float* dW_rec;  /* device [N][N]                                       */
+    float* dW_out;  /* device [n_out][N]                                   */
+    float* dbias;   /* device [N]                                          */
+    float* dI;      /* device [T][B][N]: dL/dI_t, the gradient of each outer
+                       step's input current (the hand-derived adjoint)     */
+    float* dX;      /* device [T][B][n_in]: dL/dX_t = dI_t W_in^T (tensor
+                       cores: dI split into bf16 hi + lo parts, fp32
+                       accumulation), for a preceding layer                */
 } hh_grads;
 
 enum { HH_LAYER_SPIKES = 0, /* float [T][B][N] spikes of the last forward  */
@@ -439,16 +449,37 @@ hh_status hh_layer_create(const hh_layer_desc* d, const hh_model_desc* model, hh
 hh_status hh_layer_set_weights(hh_layer* layer, const float* W_in, const float* W_rec,
                                const float* W_out, const float* bias);
 
-/* Forward pass.  X: device fp32 [T][B][n_in] (0/1 spike inputs); labels:
- * device int32 [B]; loss: device fp32 [1]; logits: device [B][n_out] or
- * NULL.  Asynchronous.  Errors: HH_EINVAL, HH_ECUDA. */
+/* Forward pass.  X: device fp32 [T][B][n_in] inputs (0/1 spikes, or any
+ * values, which the input projection rounds to bf16); labels: device int32
+ * [B], or NULL for no built-in loss; loss: device fp32 [1] (needed with
+ * labels, else ignored); logits: device [B][n_out] or NULL.  Asynchronous.
+ * Errors: HH_EINVAL, HH_ECUDA. */
 hh_status hh_layer_forward(hh_layer* layer, const float* X, const int32_t* labels, float* loss,
                            float* logits);
 
-/* Backward pass of the last forward: fills the caller's device gradient
- * buffers (overwritten, not accumulated).  Asynchronous.  Errors: HH_EINVAL,
- * HH_ESTATE (no forward yet), HH_ECUDA. */
+/* Backward pass of the last forward for its built-in loss (the mean
+ * cross-entropy; the forward must have had labels): fills dW_in, dW_rec,
+ * dW_out and dbias (all required), and dI / dX when given.  The same as
+ * hh_backward_from(layer, 1, NULL, NULL, NULL, g).  Asynchronous.
+ * Errors: HH_EINVAL, HH_ESTATE (no forward yet, or one without labels),
+ * HH_ECUDA. */
 hh_status hh_backward(hh_layer* layer, const hh_grads* g);
+
+/* Backward pass of the last forward for any loss of its outputs (Methods,
+ * "Gradient learning support": the hand-derived gradient of the discretised
+ * update, so that HH layers train inside larger models end to end):
+ *   L = ce_weight * CE + sum dL_dlogits * logits + sum dL_dS * S + sum dL_dV * V_T
+ * where CE is the built-in mean cross-entropy of the forward (ce_weight = 0
+ * drops it; nonzero needs a forward with labels), S the [T][B][N] spike
+ * outputs (HH_LAYER_SPIKES) and V_T the [B][N] membrane potentials after the
+ * last step (HH_LAYER_V).  Each cotangent is a device fp32 array or NULL:
+ *   dL_dlogits [B][n_out], dL_dS [T][B][N], dL_dV [B][N].
+ * Every non-NULL field of g is filled.  Asynchronous.  Errors: HH_EINVAL,
+ * HH_ESTATE (no forward yet; ce_weight != 0 after a forward without
+ * labels), HH_ENOMEM (the first request of dX allocates its operands),
+ * HH_ECUDA. */
+hh_status hh_backward_from(hh_layer* layer, float ce_weight, const float* dL_dlogits,
+                           const float* dL_dS, const float* dL_dV, const hh_grads* g);
 
 /* Copy HH_LAYER_* into dst (any memory); synchronous. */
 hh_status hh_layer_readout(hh_layer* layer, int32_t what, void* dst, size_t cap_bytes,
@@ -520,7 +551,10 @@ hh_status hh_profile(hh_net* net, int32_t enable);
  *     uses (it resets the slot map at the start of each call that records
  *     a trace with trace_idx).  Calls whose work overlaps on the GPU -- on
  *     different streams, or from several threads -- race on it.
- *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.  The
+ *     very first launch of the library's kernels in a process may still make
+ *     the CUDA driver load their module (lazy loading), which reserves device
+ *     memory once; later calls leave the free device memory unchanged.
  * All state and I/O pointers are device memory owned by the caller; the
  * state arrays are updated in place. */
 #define HH_NOALLOC_MAX_NEURONS (1 << 20)
@@ -545,9 +579,9 @@ typedef struct {
     void* stream;            /* cudaStream_t, NULL = legacy default stream    */
 } hh_neurons_noalloc;
 
-/* Advance the population by n_steps (Methods, Eq. hh_eq_full with the
- * exponential-Euler discretisation, as hh_step_n for a network without
- * synapses); t0 is the absolute index of the first step (spike records).
+/* Advance the population by n_steps: the same step as hh_step_n for a
+ * network without synapses; t0 is the absolute index of the first step
+ * (spike records).
  * m: the neuron model, host memory.  I_steps: device [n_steps][N] or NULL.
  * rec: as for hh_step_n, or NULL.  Asynchronous on s->stream.
  * Errors: HH_EINVAL (sizes beyond the limits, NULL state pointers, an

@@ -7,7 +7,7 @@ called through ctypes; the BPTT oracle (``oracle.bptt``) is plain PyTorch
 CPU float64.
 
 Parity pins: see ``tests/test_oracle_*.py`` (resting fixed point, spike
-amplitude, repetitive-firing threshold, first-order convergence under dt
+amplitude, repetitive-firing threshold, second-order convergence under dt
 halving, removable singularities, Philox known-answer vectors, Poisson
 moments, dense brute-force routing, central finite differences).
 """

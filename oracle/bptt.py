@@ -105,20 +105,24 @@ def _smooth(x, beta):
     return 0.5 + 0.5 * beta * x / (1.0 + beta * x.abs())
 
 
-def layer_forward(model, X, W_in, W_rec, W_out, bias, labels, *, dt=0.01, K=10, theta=0.0,
-                  beta=0.5, smooth=False, V0=-65.0, return_all=False):
-    """X: [T, B, n_in] (0/1), W_in [n_in, N], W_rec [N, N], W_out [n_out, N],
-    bias [N], labels [B] (long).  Returns loss (and optionally spikes,
-    logits, final V)."""
+def layer_run(model, X, W_in, W_rec, bias, *, dt=0.01, K=10, theta=0.0, beta=0.5, smooth=False,
+              V0=-65.0, currents=None):
+    """The layer's outputs as a differentiable program of its inputs and
+    weights: X [T, B, n_in], W_in [n_in, N], W_rec [N, N], bias [N].
+    Returns (S [T, B, N], V_T [B, N]); if `currents` is a list, the input
+    current I_t of every outer step is appended to it (with retain_grad)."""
     T, B, _ = X.shape
     N = W_in.shape[1]
     V = torch.full((B, N), float(V0), dtype=DT)
     ps = init_state(model, V)
     S_prev = torch.zeros((B, N), dtype=DT)
     spikes = []
-    acc = torch.zeros((B, N), dtype=DT)
     for t in range(T):
         I = bias + X[t] @ W_in + S_prev @ W_rec
+        if currents is not None:
+            if I.requires_grad:
+                I.retain_grad()
+            currents.append(I)
         s_t = torch.zeros((B, N), dtype=DT)
         for _ in range(K):
             Vn, ps = substep(model, V, ps, I, dt)
@@ -129,14 +133,41 @@ def layer_forward(model, X, W_in, W_rec, W_out, bias, labels, *, dt=0.01, K=10, 
             s_t = s_t + c
             V = Vn
         spikes.append(s_t)
-        acc = acc + s_t
         S_prev = s_t
-    r = acc / T
+    return torch.stack(spikes), V
+
+
+def layer_forward(model, X, W_in, W_rec, W_out, bias, labels, *, dt=0.01, K=10, theta=0.0,
+                  beta=0.5, smooth=False, V0=-65.0, return_all=False):
+    """X: [T, B, n_in] (0/1), W_in [n_in, N], W_rec [N, N], W_out [n_out, N],
+    bias [N], labels [B] (long).  Returns loss (and optionally spikes,
+    logits, final V)."""
+    S, V = layer_run(model, X, W_in, W_rec, bias, dt=dt, K=K, theta=theta, beta=beta, smooth=smooth, V0=V0)
+    r = S.sum(0) / S.shape[0]
     logits = r @ W_out.T
     loss = torch.nn.functional.cross_entropy(logits, labels)
     if return_all:
-        return loss, {"spikes": torch.stack(spikes), "logits": logits, "V": V}
+        return loss, {"spikes": S, "logits": logits, "V": V}
     return loss
+
+
+def layer_vjp(model, X, W_in, W_rec, bias, dS, dV, **kw):
+    """Gradients of L = sum(dS * S) + sum(dV * V_T) with respect to X, W_in,
+    W_rec, bias and every outer step's input current I_t (float64 numpy
+    arrays; dS [T, B, N] and dV [B, N] may be None)."""
+    leaves = [torch.tensor(a, dtype=DT, requires_grad=True) for a in (X, W_in, W_rec, bias)]
+    cur = []
+    S, V = layer_run(model, *leaves, currents=cur, **kw)
+    L = torch.zeros((), dtype=DT)
+    if dS is not None:
+        L = L + (S * torch.tensor(dS, dtype=DT)).sum()
+    if dV is not None:
+        L = L + (V * torch.tensor(dV, dtype=DT)).sum()
+    L.backward()
+    out = {"S": S.detach().numpy(), "V": V.detach().numpy(), "dI": torch.stack([c.grad for c in cur]).numpy()}
+    for name, p in zip(("X", "W_in", "W_rec", "bias"), leaves):
+        out["d" + name] = p.grad.numpy()
+    return out
 
 
 def layer_grads(model, X, W_in, W_rec, W_out, bias, labels, **kw):

@@ -164,8 +164,10 @@ __global__ void k_trace_slots(const int32_t* __restrict__ idx, int32_t n, int64_
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) {
         const int32_t i = idx[r];
+        // a neuron listed more than once takes its last row (the largest r),
+        // whatever order the threads run in
         if (i >= 0 && i < N)
-            slot[i] = r;
+            atomicMax(slot + i, r);
     }
 }
 

@@ -7,7 +7,9 @@
 //   K substeps of the neuron update with I_t held; S_t = sum_k c_{t,k},
 //   c_{t,k} = H(V_k - theta)(1 - H(V_{k-1} - theta))   (or the smooth step)
 //   r = (1/T) sum_t S_t,  logits = r W_out^T,  loss = mean_b CE(logits_b, y_b)
-// Backward: dlogits = (softmax - onehot)/B; dS_t = dr/T + dI_{t+1} W_rec^T;
+// Backward, for L = w CE + <dL/dlogits, logits> + <dL/dS, S> + <dL/dV, V_T>:
+// dlogits = w (softmax - onehot)/B + dL/dlogits; dS_t = dr/T + dL/dS_t +
+// dI_{t+1} W_rec^T; lambda_V starts at dL/dV_T;
 // through each substep in reverse with the surrogate 1/(1 + beta|x|)^2 for
 // dH/dx; dW_in = X^T dI, dW_rec = S_prev^T dI, dbias = sum dI (GEMMs over the
 // T*B rows, dI split into bf16 hi + lo parts so the products keep ~16 bits).
@@ -41,6 +43,15 @@ __global__ void k_layer_readout(const float* __restrict__ acc, const float* __re
             sh[o] = s;
     }
     __syncthreads();
+    if (threadIdx.x == 0 && !labels) {
+        // no built-in loss: logits only, no cross-entropy gradient
+        for (int o = 0; o < n_out; ++o) {
+            if (logits)
+                logits[(int64_t)b * n_out + o] = sh[o];
+            dlogits[(int64_t)b * n_out + o] = 0.0f;
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         float mx = -INFINITY;
         for (int o = 0; o < n_out; ++o)
@@ -75,7 +86,7 @@ __global__ void k_layer_bwd_readout(const float* __restrict__ acc, const float* 
                                     float* dW_out, float* ds_direct)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < (int64_t)n_out * N) {
+    if (dW_out && i < (int64_t)n_out * N) {
         const int o = (int)(i / N), n = (int)(i % N);
         float s = 0.0f;
         for (int b = 0; b < B; ++b)
@@ -175,6 +186,55 @@ __global__ void k_colsum_final(const float* __restrict__ part, int N, float* out
     out[n] = s;
 }
 
+// dlog[b][o] = w * ce[b][o] + (ext ? ext[b][o] : 0): the gradient reaching
+// the logits from the weighted built-in loss and the caller's cotangent.
+__global__ void k_combine_dlogits(const float* __restrict__ ce, float w, const float* __restrict__ ext, int n,
+                                  float* dlog)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        dlog[i] = w * ce[i] + (ext ? ext[i] : 0.0f);
+}
+
+// dI [rows][N] fp32 -> out [rows][2N] bf16 (hi | lo): the A operand of
+// dX = dI W_in^T with ~16 significant bits.
+__global__ void k_split_rows_bf16(const float* __restrict__ dI, int64_t rows, int N, uint16_t* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * N)
+        return;
+    const int64_t r = i / N;
+    const int n = (int)(i % N);
+    const float v = dI[i];
+    const uint16_t hi = f2bf(v);
+    out[r * 2 * N + n] = hi;
+    out[r * 2 * N + N + n] = f2bf(v - bf2f(hi));
+}
+
+// WinT [N][ld] (bf16, W_in transposed) -> W2 [c][2N] = (W_in[c][:] | W_in[c][:])
+// for c < rows: the B operand of dX, matching the hi | lo split of dI.
+__global__ void k_win2_from_wint(const uint16_t* __restrict__ WinT, int N, int ld, int rows, uint16_t* W2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * N)
+        return;
+    const int c = (int)(i / N), n = (int)(i % N);
+    const uint16_t v = WinT[(int64_t)n * ld + c];
+    W2[(int64_t)c * 2 * N + n] = v;
+    W2[(int64_t)c * 2 * N + N + n] = v;
+}
+
+// dst [rows][cols] = src [rows][ld] (drop the padding columns)
+__global__ void k_strip_cols(const float* __restrict__ src, int64_t rows, int cols, int ld, float* dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols)
+        return;
+    const int64_t r = i / cols;
+    const int c = (int)(i % cols);
+    dst[i] = src[r * ld + c];
+}
+
 __global__ void k_layer_init(const __grid_constant__ DevModels Ms, const __grid_constant__ LayerParams L, float V0)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -221,6 +281,12 @@ struct LayerImpl {
     int32_t* status;
     int rec_splits, ds_splits, w_splits;
     bool forward_done;
+    bool forward_labels;  // the last forward had labels (built-in loss available)
+    float* dlog_tot;      // [B][n_out] gradient reaching the logits
+    // dX = dI W_in^T operands, allocated at the first request of dX
+    uint16_t *dIrow, *Win2;  // [TB][2N], [n_in_pad][2N]
+    float* dXpart;           // [TB][n_in_pad]
+    bool win2_valid;
     LayerKernels jit;  // fwd / recompute / bwd compiled for the layer's model
     size_t bwd_smem;   // dynamic shared memory of the adjoint kernel
 };
@@ -256,6 +322,7 @@ LayerParams layer_params(const LayerImpl& L)
     p.lamV = L.lamV;
     p.lamP = L.lamP;
     p.ds_direct = L.ds_direct;
+    p.dS_ext = nullptr;
     p.dsp = nullptr;
     p.ds_splits = L.ds_splits;
     p.dI_all = L.dI_all;
@@ -292,21 +359,32 @@ cudaError_t layer_forward(LayerImpl& L, const float* X, const int32_t* labels, f
     }
     k_layer_readout<<<L.B, 256, L.n_out * sizeof(float), st>>>(L.acc, L.W_out, labels, L.N, L.n_out,
                                                                1.0f / L.T, L.B, logits, L.loss_b, L.dlogits);
-    k_layer_loss<<<1, 32, 0, st>>>(L.loss_b, L.B, loss);
+    if (labels)
+        k_layer_loss<<<1, 32, 0, st>>>(L.loss_b, L.B, loss);
     L.forward_done = true;
+    L.forward_labels = labels != nullptr;
     return cudaGetLastError();
 }
 
-cudaError_t layer_backward(LayerImpl& L, float* dW_in, float* dW_rec, float* dW_out, float* dbias)
+// The loss is ce_weight * CE + <dL_dlogits, logits> + <dL_dS, S> + <dL_dV, V_T>
+// (any cotangent may be null); every non-null gradient of g is filled.
+cudaError_t layer_backward(LayerImpl& L, float ce_weight, const float* dL_dlogits, const float* dL_dS,
+                           const float* dL_dV, const hh_grads& g)
 {
     cudaStream_t st = L.st;
     cudaError_t e;
     LayerParams p = layer_params(L);
+    p.dS_ext = dL_dS;
     const int64_t BN = p.BN;
+    const int nlog = L.B * L.n_out;
+    k_combine_dlogits<<<grid1(nlog, 256), 256, 0, st>>>(L.dlogits, ce_weight, dL_dlogits, nlog, L.dlog_tot);
     k_layer_bwd_readout<<<grid1(std::max<int64_t>(BN, (int64_t)L.n_out * L.N), 256), 256, 0, st>>>(
-        L.acc, L.W_out, L.dlogits, L.B, L.N, L.n_out, 1.0f / L.T, dW_out, L.ds_direct);
-    if ((e = cudaMemsetAsync(L.lamV, 0, BN * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(L.lamP, 0, BN * kMaxGates * sizeof(float), st)) != cudaSuccess)
+        L.acc, L.W_out, L.dlog_tot, L.B, L.N, L.n_out, 1.0f / L.T, g.dW_out, L.ds_direct);
+    if (dL_dV)
+        e = cudaMemcpyAsync(L.lamV, dL_dV, BN * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    else
+        e = cudaMemsetAsync(L.lamV, 0, BN * sizeof(float), st);
+    if (e != cudaSuccess || (e = cudaMemsetAsync(L.lamP, 0, BN * kMaxGates * sizeof(float), st)) != cudaSuccess)
         return e;
     for (int g = L.n_ckpt - 1; g >= 0; --g) {
         const int t0 = g * L.ckpt;
@@ -330,14 +408,14 @@ cudaError_t layer_backward(LayerImpl& L, float* dW_in, float* dW_rec, float* dW_
         }
     }
     // weight gradients over the T*B rows
-    {
-        dim3 blk(32, 8);
-        dim3 g1((L.N + 31) / 32, (L.TB + 31) / 32);
+    dim3 blk(32, 8);
+    dim3 g1((L.N + 31) / 32, (L.TB + 31) / 32);
+    if (g.dW_in || g.dW_rec)
         k_transpose_bf16<float><<<g1, blk, 0, st>>>(L.dI_all, L.TB, L.N, L.N, L.dIT_hi, L.TBp, L.dIT_lo);
+    const int s = L.w_splits;
+    if (g.dW_in) {
         dim3 g2((L.n_in_pad + 31) / 32, (L.TB + 31) / 32);
         k_transpose_bf16<uint16_t><<<g2, blk, 0, st>>>(L.Xb, L.TB, L.n_in_pad, L.n_in_pad, L.XT, L.TBp, nullptr);
-        k_transpose_bf16<uint16_t><<<g1, blk, 0, st>>>(L.S, L.TB, L.N, L.N, L.SpT, L.TBp, nullptr);
-        const int s = L.w_splits;
         const int64_t pin = (int64_t)L.N * L.n_in_pad;
         GemmArgs a1{L.dIT_hi, L.N, L.TBp, 0, L.XT, L.n_in_pad, L.TBp, 0, L.wpart, L.N, L.n_in_pad, L.TBp, s};
         GemmArgs a2 = a1;
@@ -347,7 +425,10 @@ cudaError_t layer_backward(LayerImpl& L, float* dW_in, float* dW_rec, float* dW_
             (e = launch_gemm_bf16(a2, L.status, st)) != cudaSuccess)
             return e;
         k_reduce_transpose<<<grid1((int64_t)L.n_in * L.N, 256), 256, 0, st>>>(L.wpart, 2 * s, L.N, L.n_in_pad,
-                                                                              L.n_in, L.N, dW_in);
+                                                                              L.n_in, L.N, g.dW_in);
+    }
+    if (g.dW_rec) {
+        k_transpose_bf16<uint16_t><<<g1, blk, 0, st>>>(L.S, L.TB, L.N, L.N, L.SpT, L.TBp, nullptr);
         const int64_t prc = (int64_t)L.N * L.N;
         GemmArgs b1{L.dIT_hi, L.N, L.TBp, 0, L.SpT, L.N, L.TBp, 0, L.wpart, L.N, L.N, L.TBp, s};
         GemmArgs b2 = b1;
@@ -356,9 +437,30 @@ cudaError_t layer_backward(LayerImpl& L, float* dW_in, float* dW_rec, float* dW_
         if ((e = launch_gemm_bf16(b1, L.status, st)) != cudaSuccess ||
             (e = launch_gemm_bf16(b2, L.status, st)) != cudaSuccess)
             return e;
-        k_reduce_transpose<<<grid1(prc, 256), 256, 0, st>>>(L.wpart, 2 * s, L.N, L.N, L.N, L.N, dW_rec);
+        k_reduce_transpose<<<grid1(prc, 256), 256, 0, st>>>(L.wpart, 2 * s, L.N, L.N, L.N, L.N, g.dW_rec);
+    }
+    if (g.dbias) {
         k_colsum_part<<<dim3(grid1(L.N, 128), kColChunks), 128, 0, st>>>(L.dI_all, L.TB, L.N, L.wpart);
-        k_colsum_final<<<grid1(L.N, 128), 128, 0, st>>>(L.wpart, L.N, dbias);
+        k_colsum_final<<<grid1(L.N, 128), 128, 0, st>>>(L.wpart, L.N, g.dbias);
+    }
+    if (g.dI && (e = cudaMemcpyAsync(g.dI, L.dI_all, (size_t)L.TB * L.N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     st)) != cudaSuccess)
+        return e;
+    if (g.dX) {
+        // dX [TB][n_in] = dI [TB][N] W_in^T on the tensor cores, dI as bf16
+        // hi | lo (K = 2N) against W_in duplicated (exact: W_in is bf16)
+        if (!L.win2_valid) {
+            k_win2_from_wint<<<grid1((int64_t)L.n_in_pad * L.N, 256), 256, 0, st>>>(L.WinT, L.N, L.n_in_pad,
+                                                                                   L.n_in_pad, L.Win2);
+            L.win2_valid = true;
+        }
+        k_split_rows_bf16<<<grid1((int64_t)L.TB * L.N, 256), 256, 0, st>>>(L.dI_all, L.TB, L.N, L.dIrow);
+        GemmArgs gx{L.dIrow, L.TB, 2 * L.N, 0, L.Win2, L.n_in_pad, 2 * L.N, 0, L.dXpart, L.TB, L.n_in_pad,
+                    2 * L.N, 1};
+        if ((e = launch_gemm_bf16(gx, L.status, st)) != cudaSuccess)
+            return e;
+        k_strip_cols<<<grid1((int64_t)L.TB * L.n_in, 256), 256, 0, st>>>(L.dXpart, L.TB, L.n_in, L.n_in_pad,
+                                                                         g.dX);
     }
     return cudaGetLastError();
 }
@@ -499,6 +601,7 @@ hh_status hh_layer_create(const hh_layer_desc* d, const hh_model_desc* model, hh
     A(&L.acc, BN);
     A(&L.dlogits, (size_t)L.B * L.n_out);
     A(&L.loss_b, (size_t)L.B);
+    A(&L.dlog_tot, (size_t)L.B * L.n_out);
     A(&L.segV, (size_t)L.ckpt * BN);
     A(&L.segP, (size_t)L.ckpt * hh::kMaxGates * BN);
     A(&L.lamV, BN);
@@ -576,25 +679,61 @@ hh_status hh_layer_set_weights(hh_layer* ly, const float* W_in, const float* W_r
     if (e != cudaSuccess)
         return hh::fail(HH_ECUDA, "setting weights: %s", cudaGetErrorString(e));
     L.forward_done = false;
+    L.win2_valid = false;
     return HH_OK;
 }
 
 hh_status hh_layer_forward(hh_layer* ly, const float* X, const int32_t* labels, float* loss, float* logits)
 {
-    if (!ly || !X || !labels || !loss)
-        return hh::fail(HH_EINVAL, "layer, X, labels and loss must not be NULL");
+    if (!ly || !X)
+        return hh::fail(HH_EINVAL, "layer and X must not be NULL");
+    if (labels && !loss)
+        return hh::fail(HH_EINVAL, "a forward with labels needs the loss output");
     HH_LCUDA(hh::layer_forward(ly->L, X, labels, loss, logits));
+    return HH_OK;
+}
+
+hh_status hh_backward_from(hh_layer* ly, float ce_weight, const float* dL_dlogits, const float* dL_dS,
+                           const float* dL_dV, const hh_grads* g)
+{
+    if (!ly || !g)
+        return hh::fail(HH_EINVAL, "layer and gradient outputs must not be NULL");
+    hh::LayerImpl& L = ly->L;
+    if (!L.forward_done)
+        return hh::fail(HH_ESTATE, "the backward pass needs a preceding hh_layer_forward");
+    if (ce_weight != 0.0f && !L.forward_labels)
+        return hh::fail(HH_ESTATE, "ce_weight != 0 needs a forward with labels");
+    if (!std::isfinite(ce_weight))
+        return hh::fail(HH_EINVAL, "ce_weight must be finite");
+    if (g->dX && !L.Win2) {
+        cudaError_t e = cudaSuccess;
+        auto A = [&](auto** p, size_t n) {
+            if (e == cudaSuccess)
+                e = ly->alloc(p, n);
+        };
+        A(&L.dIrow, (size_t)L.TB * 2 * L.N);
+        A(&L.Win2, (size_t)L.n_in_pad * 2 * L.N);
+        A(&L.dXpart, (size_t)L.TB * L.n_in_pad);
+        if (e != cudaSuccess) {
+            L.Win2 = nullptr;
+            return hh::fail(e == cudaErrorMemoryAllocation ? HH_ENOMEM : HH_ECUDA, "dX operands: %s",
+                            cudaGetErrorString(e));
+        }
+        L.win2_valid = false;
+    }
+    HH_LCUDA(hh::layer_backward(L, ce_weight, dL_dlogits, dL_dS, dL_dV, *g));
     return HH_OK;
 }
 
 hh_status hh_backward(hh_layer* ly, const hh_grads* g)
 {
     if (!ly || !g || !g->dW_in || !g->dW_rec || !g->dW_out || !g->dbias)
-        return hh::fail(HH_EINVAL, "layer and every gradient buffer must be given");
+        return hh::fail(HH_EINVAL, "layer and the four weight-gradient buffers must be given");
     if (!ly->L.forward_done)
         return hh::fail(HH_ESTATE, "hh_backward needs a preceding hh_layer_forward");
-    HH_LCUDA(hh::layer_backward(ly->L, g->dW_in, g->dW_rec, g->dW_out, g->dbias));
-    return HH_OK;
+    if (!ly->L.forward_labels)
+        return hh::fail(HH_ESTATE, "hh_backward needs a forward with labels (its built-in loss)");
+    return hh_backward_from(ly, 1.0f, nullptr, nullptr, nullptr, g);
 }
 
 hh_status hh_layer_readout(hh_layer* ly, int32_t what, void* dst, size_t cap, size_t* n_bytes)

@@ -216,6 +216,7 @@ struct LayerParams {
     float* lamV;         // [B*N]
     float* lamP;         // [kMaxGates][B*N]
     const float* ds_direct;  // [B*N]
+    const float* dS_ext; // [T][B*N] caller's dL/dS_t, or null
     const float* dsp;    // [splits][B*N] partials of dI_{t+1} W_rec^T
     int32_t ds_splits;
     float* dI_all;       // [T][B*N]
@@ -342,6 +343,8 @@ __device__ __forceinline__ void layer_bwd_body(const DevModel& M, const LayerPar
     }
     Vs[L.K * nt + tid] = st.V;
     float ds = L.ds_direct[i];
+    if (L.dS_ext)
+        ds += L.dS_ext[(int64_t)t * L.BN + i];
     if (L.dsp)
         for (int s = 0; s < L.ds_splits; ++s)
             ds += L.dsp[(int64_t)s * L.BN + i];

@@ -110,7 +110,7 @@ class hh_layer_desc(C.Structure):
 
 class hh_grads(C.Structure):
     _fields_ = [("dW_in", C.c_void_p), ("dW_rec", C.c_void_p), ("dW_out", C.c_void_p),
-                ("dbias", C.c_void_p)]
+                ("dbias", C.c_void_p), ("dI", C.c_void_p), ("dX", C.c_void_p)]
 
 
 HH_LAYER_SPIKES, HH_LAYER_V, HH_LAYER_STATUS = 0, 1, 2
@@ -133,7 +133,7 @@ class hh_record(C.Structure):
 EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_route_spikes",
            "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
-           "hh_layer_forward", "hh_backward", "hh_layer_readout", "hh_layer_destroy",
+           "hh_layer_forward", "hh_backward", "hh_backward_from", "hh_layer_readout", "hh_layer_destroy",
            "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks"]
 
 
@@ -183,6 +183,8 @@ def lib():
             L.hh_layer_forward.argtypes = [vp, vp, vp, vp, vp]
             L.hh_backward.restype = C.c_int
             L.hh_backward.argtypes = [vp, P(hh_grads)]
+            L.hh_backward_from.restype = C.c_int
+            L.hh_backward_from.argtypes = [vp, C.c_float, vp, vp, vp, P(hh_grads)]
             L.hh_layer_readout.restype = C.c_int
             L.hh_layer_readout.argtypes = [vp, C.c_int32, vp, C.c_size_t, P(C.c_size_t)]
             L.hh_layer_destroy.restype = None
@@ -483,13 +485,14 @@ _layer_fn = None
 def layer_function():
     """torch.autograd.Function over one Layer: the forward sets the weights
     (hh_layer_set_weights) and runs hh_layer_forward, giving the mean loss
-    and the logits; the backward runs hh_backward (the hand-derived adjoint
-    with recomputation from checkpoints) and scales its weight gradients by
-    the incoming gradient of the loss.  The spike inputs and labels get no
-    gradient; the logits are not differentiable.  The layer's stream must be
-    the current torch stream (the default: both are the legacy stream), and
-    the backward belongs to the layer's last forward: a later forward on the
-    same layer makes an earlier graph's backward raise."""
+    and the logits; the backward runs hh_backward_from (the hand-derived
+    adjoint with recomputation from checkpoints) with the incoming gradient
+    of the loss as the weight of the built-in cross-entropy and the incoming
+    gradient of the logits as dL/dlogits.  The spike inputs and labels get no
+    gradient (layer_spikes_function differentiates X).  The layer's stream
+    must be the current torch stream (the default: both are the legacy
+    stream), and the backward belongs to the layer's last forward: a later
+    forward on the same layer makes an earlier graph's backward raise."""
     global _layer_fn
     if _layer_fn is None:
         import torch
@@ -505,7 +508,6 @@ def layer_function():
                 ctx.layer = layer
                 ctx.forward_id = layer._forward_id
                 ctx.shapes = (tuple(W_in.shape), tuple(W_rec.shape), tuple(W_out.shape), tuple(bias.shape))
-                ctx.mark_non_differentiable(logits)
                 return loss, logits
 
             @staticmethod
@@ -513,13 +515,66 @@ def layer_function():
                 layer = ctx.layer
                 if layer._forward_id != ctx.forward_id:
                     raise RuntimeError("the layer ran another forward after this one; its backward is lost")
-                dev = g_loss.device
+                dev = (g_loss if g_loss is not None else g_logits).device
                 grads = [torch.empty(s, dtype=torch.float32, device=dev) for s in ctx.shapes]
-                layer.backward(*grads)
-                return (None, None, None) + tuple(g * g_loss for g in grads)
+                ce = 0.0 if g_loss is None else float(g_loss.item())
+                layer.backward_from(ce_weight=ce, dL_dlogits=None if g_logits is None else g_logits.contiguous(),
+                                    dW_in=grads[0], dW_rec=grads[1], dW_out=grads[2], dbias=grads[3])
+                return (None, None, None) + tuple(grads)
 
         _layer_fn = _LayerFn
     return _layer_fn
+
+
+_spikes_fn = None
+
+
+def layer_spikes_function():
+    """torch.autograd.Function over one Layer whose outputs are the spike
+    counts S [T][B][N] and the final membrane potentials V_T [B][N], so that
+    any torch loss of them, and any layer in front of X, composes with the
+    hand-derived adjoint: the forward sets W_in, W_rec and bias
+    (hh_layer_set_weights; the readout weights are zero and unused) and runs
+    hh_layer_forward without labels; the backward runs hh_backward_from with
+    the incoming gradients as dL/dS and dL/dV and returns dL/dX, dL/dW_in,
+    dL/dW_rec and dL/dbias.  X is rounded to bf16 by the input projection
+    (exact for 0/1 spikes).  The same stream and last-forward rules as
+    layer_function apply."""
+    global _spikes_fn
+    if _spikes_fn is None:
+        import torch
+
+        class _SpikesFn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, layer, X, W_in, W_rec, bias):
+                T, B, _, N, n_out = layer.shape
+                dev = X.device
+                layer.set_weights(W_in.detach(), W_rec.detach(),
+                                  torch.zeros((n_out, N), dtype=torch.float32, device=dev), bias.detach())
+                layer.forward(X.detach().to(torch.float32).contiguous())
+                S = torch.empty((T, B, N), dtype=torch.float32, device=dev)
+                V = torch.empty((B, N), dtype=torch.float32, device=dev)
+                layer.outputs(S, V)
+                ctx.layer = layer
+                ctx.forward_id = layer._forward_id
+                ctx.shapes = (tuple(X.shape), tuple(W_in.shape), tuple(W_rec.shape), tuple(bias.shape))
+                return S, V
+
+            @staticmethod
+            def backward(ctx, gS, gV):
+                layer = ctx.layer
+                if layer._forward_id != ctx.forward_id:
+                    raise RuntimeError("the layer ran another forward after this one; its backward is lost")
+                dev = gS.device if gS is not None else gV.device
+                dX, dW_in, dW_rec, dbias = [torch.empty(s, dtype=torch.float32, device=dev) for s in ctx.shapes]
+                layer.backward_from(dL_dS=None if gS is None else gS.contiguous(),
+                                    dL_dV=None if gV is None else gV.contiguous(),
+                                    dW_in=dW_in, dW_rec=dW_rec, dbias=dbias,
+                                    dX=dX if ctx.needs_input_grad[1] else None)
+                return (None, dX if ctx.needs_input_grad[1] else None, dW_in, dW_rec, dbias)
+
+        _spikes_fn = _SpikesFn
+    return _spikes_fn
 
 
 class Layer:
@@ -543,14 +598,35 @@ class Layer:
               for w in (W_in, W_rec, W_out, bias)]
         _check(lib().hh_layer_set_weights(self.handle, *[_ptr(w) for w in ws]))
 
-    def forward(self, X, labels, loss, logits=None):
-        _check(lib().hh_layer_forward(self.handle, X.data_ptr(), labels.data_ptr(), loss.data_ptr(),
-                                      None if logits is None else logits.data_ptr()))
+    def forward(self, X, labels=None, loss=None, logits=None):
+        _check(lib().hh_layer_forward(self.handle, X.data_ptr(), _ptr(labels), _ptr(loss), _ptr(logits)))
         self._forward_id += 1
 
-    def backward(self, dW_in, dW_rec, dW_out, dbias):
-        g = hh_grads(dW_in.data_ptr(), dW_rec.data_ptr(), dW_out.data_ptr(), dbias.data_ptr())
+    def backward(self, dW_in, dW_rec, dW_out, dbias, dI=None, dX=None):
+        g = hh_grads(dW_in.data_ptr(), dW_rec.data_ptr(), dW_out.data_ptr(), dbias.data_ptr(), _ptr(dI),
+                     _ptr(dX))
         _check(lib().hh_backward(self.handle, C.byref(g)))
+
+    def backward_from(self, *, ce_weight=0.0, dL_dlogits=None, dL_dS=None, dL_dV=None, dW_in=None,
+                      dW_rec=None, dW_out=None, dbias=None, dI=None, dX=None):
+        """hh_backward_from: gradients of ce_weight * CE + <dL_dlogits, logits>
+        + <dL_dS, S> + <dL_dV, V_T> into the given device tensors."""
+        g = hh_grads(_ptr(dW_in), _ptr(dW_rec), _ptr(dW_out), _ptr(dbias), _ptr(dI), _ptr(dX))
+        _check(lib().hh_backward_from(self.handle, float(ce_weight), _ptr(dL_dlogits), _ptr(dL_dS),
+                                      _ptr(dL_dV), C.byref(g)))
+
+    def outputs(self, spikes, V):
+        """Copy the last forward's spikes [T][B][N] and final V [B][N] into
+        the given fp32 tensors (device or host; synchronous)."""
+        n = C.c_size_t()
+        _check(lib().hh_layer_readout(self.handle, HH_LAYER_SPIKES, spikes.data_ptr(),
+                                      spikes.numel() * 4, C.byref(n)))
+        _check(lib().hh_layer_readout(self.handle, HH_LAYER_V, V.data_ptr(), V.numel() * 4, C.byref(n)))
+
+    def spikes(self, X, W_in, W_rec, bias):
+        """The layer as a differentiable torch function of its inputs and
+        weights (see layer_spikes_function): returns (S [T][B][N], V_T [B][N])."""
+        return layer_spikes_function().apply(self, X, W_in, W_rec, bias)
 
     def loss(self, X, labels, W_in, W_rec, W_out, bias):
         """The mean cross-entropy loss as a differentiable torch function of

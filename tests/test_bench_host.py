@@ -48,8 +48,9 @@ def test_reference_arm_line(monkeypatch, capsys):
 def test_layer_function_host_logic():
     """The autograd wrapper's own logic, on a stand-in for the library layer
     (CPU tensors): the weights go to set_weights before the forward, the
-    backward's gradients come back scaled by the incoming gradient, the
-    spike inputs and labels get none, and a second forward makes the first
+    incoming gradient of the loss becomes the built-in loss's weight and the
+    incoming gradient of the logits the dL/dlogits cotangent, the spike
+    inputs and labels get no gradient, and a second forward makes the first
     graph's backward raise."""
     import pytest
     import torch
@@ -68,9 +69,10 @@ def test_layer_function_host_logic():
             logits.fill_(1.0)
             self._forward_id += 1
 
-        def backward(self, *g):
-            for k, x in enumerate(g):
-                x.fill_(k + 1.0)
+        def backward_from(self, *, ce_weight, dL_dlogits, dW_in, dW_rec, dW_out, dbias):
+            extra = 0.0 if dL_dlogits is None else float(dL_dlogits.sum())
+            for k, x in enumerate((dW_in, dW_rec, dW_out, dbias)):
+                x.fill_((k + 1.0) * ce_weight + extra)
 
     lay = FakeLayer()
     W = [torch.randn(s, requires_grad=True) for s in ((3, 4), (4, 4), (2, 4), (4,))]
@@ -78,15 +80,65 @@ def test_layer_function_host_logic():
     y = torch.zeros(2, dtype=torch.int32)
     loss, logits = hh.layer_function().apply(lay, X, y, *W)
     assert torch.equal(lay.w[1], W[1].detach())
-    assert loss.requires_grad and not logits.requires_grad
+    assert loss.requires_grad and logits.requires_grad
     (3.0 * loss).backward()
     for k, w in enumerate(W):
         assert torch.equal(w.grad, torch.full_like(w, 3.0 * (k + 1)))
+    for w in W:
+        w.grad = None
+    loss, logits = hh.layer_function().apply(lay, X, y, *W)
+    (2.0 * logits.sum()).backward()
+    for w in W:
+        assert torch.equal(w.grad, torch.full_like(w, 2.0 * 4))
     a, _ = hh.layer_function().apply(lay, X, y, *W)
     b, _ = hh.layer_function().apply(lay, X, y, *W)
     with pytest.raises(RuntimeError):
         a.backward()
     b.backward()
+
+
+def test_layer_spikes_function_host_logic():
+    """The spike-output wrapper on a stand-in layer: the forward runs without
+    labels and returns the layer's S and V_T; the backward hands the incoming
+    gradients over as dL/dS and dL/dV and returns dX and the weight
+    gradients, with dX requested only when X needs it."""
+    import torch
+
+    from paper_2601_21407_gb300 import hh
+
+    class FakeLayer:
+        shape = (5, 2, 3, 4, 2)
+        _forward_id = 0
+
+        def set_weights(self, *w):
+            self.w = [x.clone() for x in w]
+
+        def forward(self, X, labels=None, loss=None, logits=None):
+            assert labels is None and loss is None
+            self.X = X.clone()
+            self._forward_id += 1
+
+        def outputs(self, S, V):
+            S.fill_(1.0)
+            V.fill_(-60.0)
+
+        def backward_from(self, *, dL_dS, dL_dV, dW_in, dW_rec, dbias, dX):
+            self.got = (dL_dS.clone(), dL_dV.clone(), dX is not None)
+            for k, x in enumerate((dW_in, dW_rec, dbias)):
+                x.fill_(float(dL_dS.sum()) + k)
+            if dX is not None:
+                dX.fill_(7.0)
+
+    lay = FakeLayer()
+    W_in, W_rec, bias = [torch.randn(s, requires_grad=True) for s in ((3, 4), (4, 4), (4,))]
+    Z = torch.zeros((5, 2, 3), requires_grad=True)
+    S, V = hh.layer_spikes_function().apply(lay, 2.0 * Z, W_in, W_rec, bias)
+    assert S.shape == (5, 2, 4) and V.shape == (2, 4) and float(V[0, 0]) == -60.0
+    (S.sum() + 0.5 * V.sum()).backward()
+    dS, dV, want_dx = lay.got
+    assert want_dx and float(dS.sum()) == 40.0 and float(dV.sum()) == 4.0
+    assert torch.equal(Z.grad, torch.full_like(Z, 14.0))
+    assert torch.equal(W_rec.grad, torch.full_like(W_rec, 41.0))
 
 
 def test_bptt_sfu_bound():

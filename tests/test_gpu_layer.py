@@ -132,9 +132,10 @@ def test_layer_full_size_sampled():
 
 def test_layer_autograd_function():
     """loss.backward() through the torch.autograd.Function gives exactly the
-    gradients of hh_backward (the same kernels), scaled by the incoming
-    gradient; the spike inputs get none; after a second forward the first
-    graph's backward raises."""
+    gradients of hh_backward_from with the incoming gradient of the loss as
+    the weight of the built-in cross-entropy (the same kernels); the logits
+    are differentiable too; the spike inputs get no gradient; after a second
+    forward the first graph's backward raises."""
     torch = _torch()
     T, B, n_in, N, n_out = 20, 3, 16, 32, 4
     d = small_case(1, T, B, n_in, N, n_out)
@@ -145,21 +146,186 @@ def test_layer_autograd_function():
     X = torch.as_tensor(d["X"], device="cuda")
     y = torch.as_tensor(d["labels"], device="cuda")
     loss, logits = lay.loss(X, y, *W)
-    assert loss.requires_grad and not logits.requires_grad
+    assert loss.requires_grad and logits.requires_grad
     (2.5 * loss).backward()
     lay.set_weights(*[w.detach() for w in W])
     l2 = torch.zeros(1, device="cuda")
     lay.forward(X, y, l2)
     g = [torch.zeros_like(w) for w in W]
-    lay.backward(*g)
+    lay.backward_from(ce_weight=2.5, dW_in=g[0], dW_rec=g[1], dW_out=g[2], dbias=g[3])
     torch.cuda.synchronize()
     assert float(loss.item()) == float(l2.item())
     assert all(float(x.abs().max()) > 0 for x in g)
     for w, gd in zip(W, g):
-        assert torch.equal(w.grad, 2.5 * gd)
+        assert torch.equal(w.grad, gd)
+    # a loss of the logits alone flows through dL/dlogits
+    for w in W:
+        w.grad = None
+    loss, logits = lay.loss(X, y, *W)
+    R = torch.randn_like(logits)
+    (logits * R).sum().backward()
+    lay.set_weights(*[w.detach() for w in W])
+    lay.forward(X, y, l2)
+    g = [torch.zeros_like(w) for w in W]
+    lay.backward_from(dL_dlogits=R, dW_in=g[0], dW_rec=g[1], dW_out=g[2], dbias=g[3])
+    torch.cuda.synchronize()
+    for w, gd in zip(W, g):
+        assert torch.equal(w.grad, gd)
     loss_a, _ = lay.loss(X, y, *W)
     loss_b, _ = lay.loss(X, y, *W)
     with pytest.raises(RuntimeError):
         loss_a.backward()
     loss_b.backward()
+    lay.close()
+
+
+def _elementwise(got, ref, tol):
+    """max |got - ref| / max |ref| (the bound the tests assert per entry)."""
+    scale = max(float(np.abs(ref).max()), 1e-30)
+    return float(np.abs(got - ref).max()) / scale
+
+
+@pytest.mark.parametrize("precision,tol", [(hh.HH_PREC_ACCURATE, 1e-3), (hh.HH_PREC_FAST, 2e-3)])
+def test_layer_backward_from_matches_oracle(precision, tol):
+    """hh_backward_from with caller cotangents dL/dS [T][B][N] and dL/dV [B][N]
+    (no built-in loss): dX, dI, dW_in, dW_rec and dbias agree with the FP64
+    oracle's reverse mode element by element, |got - ref| <= tol * max|ref|
+    for every entry, on an identical spike raster."""
+    torch = _torch()
+    T, B, n_in, N, n_out = 30, 4, 40, 64, 5
+    d = small_case(4, T, B, n_in, N, n_out)
+    rng = np.random.default_rng(9)
+    dS = rng.normal(0, 1.0, (T, B, N)).astype(np.float32)
+    dV = rng.normal(0, 0.05, (B, N)).astype(np.float32)
+    lay = hh.Layer(HH, batch=B, n_in=n_in, n_hidden=N, n_out=n_out, n_steps=T, substeps=10, dt=0.01,
+                   precision=precision, checkpoint_every=7)
+    lay.set_weights(d["W_in"], d["W_rec"], d["W_out"], d["bias"])
+    X = torch.as_tensor(d["X"], device="cuda")
+    lay.forward(X)
+    out = {k: torch.zeros(s, device="cuda") for k, s in
+           (("dX", (T, B, n_in)), ("dI", (T, B, N)), ("dW_in", (n_in, N)), ("dW_rec", (N, N)),
+            ("dbias", (N,)))}
+    lay.backward_from(dL_dS=torch.as_tensor(dS, device="cuda"), dL_dV=torch.as_tensor(dV, device="cuda"), **out)
+    torch.cuda.synchronize()
+    spikes = lay.readout(hh.HH_LAYER_SPIKES).reshape(T, B, N)
+    status = int(lay.readout(hh.HH_LAYER_STATUS)[0])
+    lay.close()
+    ref = bptt.layer_vjp(HH, d["X"], d["W_in"], d["W_rec"], d["bias"], dS.astype(np.float64),
+                         dV.astype(np.float64), K=10, dt=0.01)
+    assert status == 0
+    assert ref["S"].sum() > 20
+    assert np.array_equal(spikes, ref["S"])
+    for k in ("dX", "dI", "dW_in", "dW_rec", "dbias"):
+        e = _elementwise(out[k].cpu().numpy(), ref[k], tol)
+        print(f"{k}: max|err|/max|ref| = {e:.2e}")
+        assert e <= tol, (k, e)
+
+
+def test_layer_spikes_function_composes_with_torch():
+    """layer_spikes_function inside a torch program: a preceding elementwise
+    op on the inputs and an arbitrary loss of S and V_T back-propagate through
+    the hand-derived adjoint; the gradients of the inputs' leaf and of the
+    weights match the FP64 oracle's reverse mode of the same program."""
+    torch = _torch()
+    T, B, n_in, N, n_out = 24, 3, 32, 64, 4
+    d = small_case(6, T, B, n_in, N, n_out)
+    lay = hh.Layer(HH, batch=B, n_in=n_in, n_hidden=N, n_out=n_out, n_steps=T, substeps=10, dt=0.01,
+                   precision=hh.HH_PREC_ACCURATE, checkpoint_every=5)
+    Z = torch.tensor(d["X"], dtype=torch.float32, device="cuda", requires_grad=True)
+    W_in, W_rec, bias = [torch.tensor(d[k], dtype=torch.float32, device="cuda", requires_grad=True)
+                         for k in ("W_in", "W_rec", "bias")]
+    rng = np.random.default_rng(2)
+    mask = (rng.random(n_in) < 0.8).astype(np.float32)
+    X = Z * torch.as_tensor(mask, device="cuda")  # an elementwise op in front of the layer (X stays 0/1)
+    S, V = lay.spikes(X, W_in, W_rec, bias)
+    R = torch.as_tensor(rng.normal(0, 1, (T, B, N)).astype(np.float32), device="cuda")
+    loss = (S * R).sum() + 0.01 * ((V + 60.0) ** 2).mean()
+    loss.backward()
+    Xm = d["X"] * mask
+    ref = bptt.layer_vjp(HH, Xm, d["W_in"], d["W_rec"], d["bias"], R.cpu().numpy().astype(np.float64),
+                         None, K=10, dt=0.01)
+    Vr = ref["V"]
+    dV = 0.01 * 2.0 * (Vr + 60.0) / Vr.size
+    ref = bptt.layer_vjp(HH, Xm, d["W_in"], d["W_rec"], d["bias"], R.cpu().numpy().astype(np.float64),
+                         dV, K=10, dt=0.01)
+    ref["dZ"] = ref["dX"] * mask
+    assert np.array_equal(S.detach().cpu().numpy(), ref["S"])
+    assert ref["S"].sum() > 10
+    for got, name in ((Z.grad, "dZ"), (W_in.grad, "dW_in"), (W_rec.grad, "dW_rec"), (bias.grad, "dbias")):
+        e = _elementwise(got.cpu().numpy(), ref[name], 1e-3)
+        print(f"{name}: max|err|/max|ref| = {e:.2e}")
+        assert e <= 1e-3, (name, e)
+    lay.close()
+
+
+def test_layer_full_size_gradients_elementwise():
+    """The full-size kernel paths (1,024 neurons: recurrent products with
+    split-K 8, dS products with K = 2,048 and split-K 8; 700 inputs;
+    checkpoints every 25 outer steps; 10 substeps) at B = 2, T = 30 with the
+    built-in loss: identical spike raster, and dW_in, dW_rec, dW_out and dbias
+    agree with the FP64 oracle entry by entry, |got - ref| <= 1e-3 max|ref|."""
+    T, B, n_in, N, n_out = 30, 2, 700, 1024, 20
+    d = inp.recurrent_layer(B=B, n_in=n_in, n_hid=N, n_out=n_out, T=T, seed=3, rate_max_hz=400.0,
+                            w_in_scale=60.0)
+    g = run_layer(d, T=T, B=B, n_in=n_in, N=N, n_out=n_out, precision=hh.HH_PREC_ACCURATE, ckpt=25)
+    ref = bptt.layer_grads(HH, d["X"], d["W_in"], d["W_rec"], d["W_out"], d["bias"], d["labels"],
+                           K=10, dt=0.01)
+    assert g["status"] == 0
+    assert ref["spikes"].sum() > 200
+    assert np.array_equal(g["spikes"], ref["spikes"])
+    for k in ("dW_in", "dW_rec", "dW_out", "dbias"):
+        e = _elementwise(g[k], ref[k], 1e-3)
+        print(f"{k}: max|err|/max|ref| = {e:.2e}")
+        assert e <= 1e-3, (k, e)
+
+
+def _bf16_ulp(w):
+    a = np.abs(w.astype(np.float64))
+    e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    return np.where(a > 0, 2.0 ** (e - 7), 0.0)
+
+
+def test_layer_gradient_matches_gpu_finite_differences():
+    """The GPU adjoint against central differences of the GPU's own forward
+    loss (smooth spikes, IEEE FP32, recurrent weights nonzero): along a random
+    direction D per parameter -- one bf16 unit in the last place with a random
+    sign per entry of W_in and W_rec (so W +- D stay exactly representable in
+    the bf16 weights the products use), 1e-3 relative for W_out and bias --
+    (L(P + D) - L(P - D)) / 2, formed in FP64 from the two FP32 losses,
+    agrees with sum(dL/dP * D) to 2 %."""
+    torch = _torch()
+    T, B, n_in, N, n_out = 20, 3, 24, 32, 4
+    d = small_case(8, T, B, n_in, N, n_out, w_rec=3.0)
+    lay = hh.Layer(HH, batch=B, n_in=n_in, n_hidden=N, n_out=n_out, n_steps=T, substeps=10, dt=0.01,
+                   precision=hh.HH_PREC_ACCURATE, smooth=True, checkpoint_every=6)
+    X = torch.as_tensor(d["X"], device="cuda")
+    y = torch.as_tensor(d["labels"], device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    P = {k: d[k].astype(np.float32).copy() for k in ("W_in", "W_rec", "W_out", "bias")}
+
+    def L(p):
+        lay.set_weights(p["W_in"], p["W_rec"], p["W_out"], p["bias"])
+        lay.forward(X, y, loss)
+        torch.cuda.synchronize()
+        return float(loss.item())
+
+    L(P)
+    g = {k: torch.zeros(v.shape, device="cuda") for k, v in P.items()}
+    lay.backward(g["W_in"], g["W_rec"], g["W_out"], g["bias"])
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    for k in P:
+        sign = rng.choice([-1.0, 1.0], P[k].shape)
+        if k in ("W_in", "W_rec"):
+            D = sign * _bf16_ulp(P[k])
+        else:
+            D = sign * 1e-3 * np.maximum(np.abs(P[k]), 1e-2)
+        plus = dict(P, **{k: (P[k].astype(np.float64) + D).astype(np.float32)})
+        minus = dict(P, **{k: (P[k].astype(np.float64) - D).astype(np.float32)})
+        if k in ("W_in", "W_rec"):
+            assert np.array_equal(inp.to_bf16_exact(plus[k]), plus[k])
+        fd = (np.float64(L(plus)) - np.float64(L(minus))) / 2.0
+        an = float((g[k].cpu().numpy().astype(np.float64) * D).sum())
+        print(f"{k}: fd {fd:.6e} adjoint {an:.6e}")
+        assert abs(fd - an) <= 2e-2 * abs(an) + 1e-6, (k, fd, an)
     lay.close()

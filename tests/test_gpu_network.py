@@ -166,22 +166,77 @@ def test_closed_loop_small_network(prec, kernels):
     net.close()
 
 
-def test_network_full_size_first_10ms():
-    """The full 38,000-neuron network (1e8 synapses) for 10 ms against the
-    oracle on the same graph: spike rasters agree for >= 99.9% of neurons."""
+@pytest.fixture(scope="module")
+def network_38k_1s():
+    """The benchmark network (38,000 neurons, in-degree 2,632, 1.0e8
+    synapses, background, dt 0.025 ms) over 1,000 ms (40,000 steps) on the
+    GPU in FAST precision and in the FP64 oracle on the same graph, initial
+    state and background draws."""
     torch = _torch()
     g = inp.network(n=38_000, k_in=2_632, seed=0)
     bg = {"rate_hz": 5.0, "K": 2106, "w": 0.368}
-    T = 400
-    ref = oracle.simulate_network(inp.CLASSIC_HH, g, T, 0.025, 40, SYN, bg=bg, seed=0, spk_cap=8)
+    T = 40_000
     net = make_net(g, bg=bg, seed=0, precision=hh.HH_PREC_FAST)
-    rec, b = hh.make_record(38_000, T, spike_cap=200_000)
+    rec, b = hh.make_record(38_000, T, spike_cap=4_000_000)
     net.step(T, rec=rec)
     torch.cuda.synchronize()
-    counts = b["counts"].cpu().numpy()
-    assert (counts == ref["counts"]).mean() >= 0.999
-    assert abs(int(counts.sum()) - int(ref["counts"].sum())) <= 0.001 * ref["counts"].sum() + 2
+    status = int(net.readout(hh.HH_READ_STATUS)[0])
+    st, ix, _ = hh.spikes_to_numpy(b)
+    n_stored = int(b["n_spikes"].item())
     net.close()
+    ref = oracle.simulate_network(inp.CLASSIC_HH, g, T, 0.025, 40, SYN, bg=bg, seed=0, spk_cap=256)
+    return {"T": T, "status": status, "n_spikes": n_stored, "gpu_step": st, "gpu_idx": ix,
+            "ref_step": ref["spk_step"], "ref_counts": ref["counts"]}
+
+
+def _counts_upto(r, t_ms, N=38_000):
+    s_end = int(round(t_ms / 0.025))
+    cg = np.bincount(r["gpu_idx"][r["gpu_step"] < s_end], minlength=N)
+    ss = r["ref_step"]
+    cr = ((ss >= 0) & (ss < s_end)).sum(1)
+    return cg, cr
+
+
+def test_network_full_size_first_10ms(network_38k_1s):
+    """The full network against the oracle over its first 10 ms: spike
+    counts identical for >= 99.9 % of neurons, totals within 0.1 %."""
+    r = network_38k_1s
+    cg, cr = _counts_upto(r, 10)
+    assert (cg == cr).mean() >= 0.999
+    assert abs(int(cg.sum()) - int(cr.sum())) <= 0.001 * cr.sum() + 2
+
+
+def test_network_full_size_1000ms(network_38k_1s):
+    """Closed-loop parity over the full 1,000 ms.  FP32 and FP64 trajectories
+    of a recurrent spiking network separate in the end (chaos), so the bar is
+    stated per horizon: per-neuron spike counts within +-1 for every neuron
+    up to 500 ms and for >= 99.9 % of neurons at 1,000 ms, total spikes within
+    0.1 %, and the population rate in 1 ms bins correlated at >= 0.85 with
+    the same mean within 1 %."""
+    r = network_38k_1s
+    assert r["status"] == 0
+    ref_cap = r["ref_step"].shape[1]
+    assert (r["ref_counts"] <= ref_cap).all()
+    assert r["n_spikes"] == len(r["gpu_idx"])
+    for t_ms in (50, 100, 200, 500):
+        cg, cr = _counts_upto(r, t_ms)
+        d = np.abs(cg - cr)
+        print(f"{t_ms} ms: equal {(d == 0).mean():.5f}, within 1 {(d <= 1).mean():.5f}, max {d.max()}")
+        assert d.max() <= 1, (t_ms, int(d.max()))
+    cg, cr = _counts_upto(r, 1000)
+    d = np.abs(cg - cr)
+    print(f"1000 ms: equal {(d == 0).mean():.5f}, within 1 {(d <= 1).mean():.5f}, max {d.max()}, "
+          f"spikes {cg.sum()} vs {cr.sum()}")
+    assert (d <= 1).mean() >= 0.999
+    assert abs(int(cg.sum()) - int(cr.sum())) <= 0.001 * cr.sum()
+    bins = np.arange(0, r["T"] + 1, 40)
+    sv = r["ref_step"][r["ref_step"] >= 0]
+    pg = np.histogram(r["gpu_step"], bins)[0].astype(np.float64)
+    pr = np.histogram(sv, bins)[0].astype(np.float64)
+    corr = float(np.corrcoef(pg, pr)[0, 1])
+    print(f"population rate (1 ms bins): correlation {corr:.3f}")
+    assert corr >= 0.85
+    assert abs(pg.mean() - pr.mean()) <= 0.01 * pr.mean()
 
 
 def test_batched_networks_mixed_models():

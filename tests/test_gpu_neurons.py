@@ -259,3 +259,109 @@ def test_measure_peaks_plausible():
     lo, hi = sms * 16 * 1.0e9 / 8, sms * 16 * 2.1e9 * 8
     assert p["ffma_per_s"] > p["ex2_per_s"] > 0 and p["ffma_per_s"] > p["rcp_per_s"] > 0
     assert lo < p["ex2_per_s"] < hi and lo < p["rcp_per_s"] < hi
+
+
+def _linoid_points(model):
+    """(v_half, k) of every linoid rate of the model."""
+    pts = []
+    for ch in model["channels"]:
+        for g in ch["gates"]:
+            for f in (g["f1"], g["f2"]):
+                if f[0] == "linoid":
+                    pts.append((f[2], f[3]))
+    return pts
+
+
+@pytest.mark.parametrize("model_name", ["hh1952", "multi6"])
+@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE])
+def test_linoid_singular_points_one_step(model_name, prec):
+    """One step from V exactly at, and 1e-4 .. 1e-3 mV around, every linoid's
+    removable point a (V - vh)/(1 - e^{-(V - vh)/k}) (and just inside and
+    outside |V - vh| = 0.1 |k|, where the SFU path switches to its series),
+    with the gates away from steady state so that the rate enters the gate
+    update: gates within 2e-6 and V within 1e-4 mV of the FP64 oracle's step.
+    The state is the caller's (the allocation-free entry point, which runs
+    the same neuron step)."""
+    torch = _torch()
+    model = inp.MODELS[model_name]
+    rng = np.random.default_rng(12)
+    V0 = []
+    for vh, k in _linoid_points(model):
+        for d in (0.0, 1e-4, -1e-4, 1e-3, -1e-3, 0.05, -0.05):
+            V0.append(vh + d)
+        for f in (0.099, 0.101):
+            V0 += [vh + f * abs(k), vh - f * abs(k)]
+    V0 = np.asarray(V0, dtype=np.float32)
+    N = V0.size
+    n_g = sum(len(c["gates"]) for c in model["channels"])
+    P0 = rng.uniform(0.05, 0.95, (n_g, N)).astype(np.float32)
+    Ca0 = rng.uniform(0.05, 0.5, N).astype(np.float32)
+    I = rng.uniform(0.0, 10.0, N).astype(np.float32)
+    dt = 0.05
+    gates = torch.zeros((hh.HH_MAX_GATES, N), dtype=torch.float32, device="cuda")
+    gates[:n_g] = torch.as_tensor(P0, device="cuda")
+    V = torch.as_tensor(V0, device="cuda").clone()
+    Ca = torch.as_tensor(Ca0, device="cuda").clone()
+    Ic = torch.as_tensor(I, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = hh.hh_neurons_noalloc()
+    s.n_neurons, s.dt_ms, s.v_threshold, s.v_update, s.precision = N, dt, 0.0, hh.HH_V_EXP_EULER, prec
+    s.V, s.gates, s.Ca, s.I_const, s.status = V.data_ptr(), gates.data_ptr(), Ca.data_ptr(), Ic.data_ptr(), \
+        status.data_ptr()
+    s.init_state = 0
+    hh.hh_step_neurons_noalloc(hh.model_desc(model), s, 0, 1)
+    torch.cuda.synchronize()
+    Vg, Pg = V.cpu().numpy(), gates[:n_g].cpu().numpy()
+    assert int(status.item()) == 0
+    for i in range(N):
+        Vr, pr, _ = oracle.step_neuron(model, float(V0[i]), P0[:, i].astype(np.float64), float(Ca0[i]), dt,
+                                       float(I[i]))
+        assert abs(Vg[i] - Vr) <= 1e-4, (i, float(V0[i]), Vg[i], Vr)
+        assert np.abs(Pg[:, i] - pr).max() <= 2e-6, (i, float(V0[i]), Pg[:, i], pr)
+
+
+@pytest.mark.parametrize("model_name", ["hh1952", "multi6"])
+@pytest.mark.parametrize("prec", [hh.HH_PREC_FAST, hh.HH_PREC_ACCURATE])
+def test_trajectories_from_linoid_singular_points(model_name, prec):
+    """2 ms (200 steps at dt 0.01 ms) of the run-time specialised kernels from
+    V0 at and around each linoid's removable point (gates at steady state):
+    V within 1e-3 mV of the oracle on every step."""
+    model = inp.MODELS[model_name]
+    V0 = []
+    for vh, k in _linoid_points(model):
+        V0 += [vh + d for d in (0.0, 1e-4, -1e-4, 1e-3, -1e-3, 0.1 * abs(k), -0.1 * abs(k))]
+    V0 = np.asarray(V0, dtype=np.float32)
+    I = np.zeros_like(V0)
+    T, dt = 200, 0.01
+    ref = oracle.simulate(model, I, V0, T, dt)
+    g = run_gpu(model, I, V0, T, dt, prec)
+    assert g["status"] == 0
+    err = np.abs(g["V"] - ref["V"]).max()
+    print(f"{model_name} prec {prec}: max |dV| {err:.2e} mV over 2 ms")
+    assert err <= 1e-3
+
+
+@pytest.mark.parametrize("prec,tol", [(hh.HH_PREC_FAST, 1e-3), (hh.HH_PREC_ACCURATE, 2e-4),
+                                      (hh.HH_PREC_COMPENSATED, 2e-4)])
+def test_resting_state_is_a_fixed_point_on_gpu(prec, tol):
+    """From the resting potential of the squid axon (bisection of the steady
+    I-V curve in FP64) with gates at steady state and no input, 100 ms on the
+    GPU stay within tol of V_rest (FP32 rounding of a fixed point; the FP64
+    oracle holds it to 1e-9 mV), with no spike."""
+    lo, hi = -80.0, -50.0
+
+    def f(v):
+        p, _ = oracle.init_neuron(inp.CLASSIC_HH, v)
+        return oracle.ionic_current(inp.CLASSIC_HH, v, p)
+
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) < 0 else (lo, mid)
+    V_rest = np.float32(0.5 * (lo + hi))
+    N, T, dt = 64, 10_000, 0.01
+    V0 = np.full(N, V_rest, dtype=np.float32)
+    g = run_gpu(inp.CLASSIC_HH, np.zeros(N, np.float32), V0, T, dt, prec)
+    drift = np.abs(g["V"] - np.float64(V_rest)).max()
+    print(f"prec {prec}: drift {drift:.2e} mV over 100 ms at V_rest {float(V_rest):.6f}")
+    assert g["counts"].sum() == 0
+    assert drift <= tol

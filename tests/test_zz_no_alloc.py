@@ -7,7 +7,8 @@ array of the library, so it allocates nothing.
 
 Checked through the C ABI against the allocating path (hh_create_network +
 hh_step_n) on two calls in a row, within the tolerances the other GPU tests
-use (V within 1e-2 mV, identical spike counts and rasters).  The allocating
+use (V within 1e-2 mV, identical spike counts and rasters), and the device's
+free memory is the same before and after the second call.  The allocating
 path runs the same precompiled table kernels (HH_KERNELS_TABLE) as the
 entry point: loading run-time compiled kernels allocates device memory, and
 two compilations of the step may contract different multiply-adds, whose
@@ -82,8 +83,14 @@ def test_noalloc_matches_allocating_path(prec, with_status):
     for call, T in enumerate(steps):
         s.init_state = 1 if call == 0 else 0
         rec, b = _record(N, T, trace_idx)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         hh.hh_step_neurons_noalloc(m, s, t0, T, None, rec)
         torch.cuda.synchronize()
+        if call > 0:
+            # the first call may load the library's kernels (lazy module
+            # loading reserves device memory once); later calls take none
+            assert torch.cuda.mem_get_info()[0] == free_before
         t0 += T
         Vtr = b["V_trace"].cpu().numpy()
         Vref, cref, sref = ref[call]
