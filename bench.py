@@ -57,8 +57,7 @@ def workload_config():
             "neurons": W["n"], "in_degree": W["k_in"], "synapses": W["n"] * W["k_in"],
             "exc_frac": W["exc_frac"], "weights": "lognormal(mu=-1,sigma=0.5) nS",
             "tau_E_ms": W["tau_E"], "tau_I_ms": W["tau_I"], "delay_ms": W["delay_ms"],
-            "dt_ms": W["dt"], "sim_ms_per_step": W["T_ms"],
-            "time_steps_per_step": STEPS_PER_SIM,
+            "dt_ms": W["dt"], "sim_ms": W["T_ms"],
             "background": f"{W['bg_K']} Poisson sources x {W['bg_rate_hz']} Hz x {W['bg_w_nS']} nS",
             "model": "classic squid-axon HH (Na, K, leak)", "precision_mode": "fast",
             "l2": "inputs larger than L2 (CSR 800 MB vs 129 MB L2)"}
@@ -127,6 +126,14 @@ def peaks():
         return json.load(open(MEASURED_PEAKS)), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Algorithmic transcendental work of one classic neuron-step (the method's
+# count, independent of how a kernel evaluates it): the six rate functions
+# and the three gate relaxation factors and V's are ten exponentials; the
+# three steady states p_inf = alpha/(alpha+beta) and V's 1/G are four
+# divisions.
+ALGO_EXP_PER_STEP, ALGO_DIV_PER_STEP = 10, 4
 
 
 def mufu_ops_per_neuron_step(model):
@@ -327,25 +334,36 @@ def run_gpu(args):
         n_launch_route, route_ms = kt["route"]
         avg_neuron_ms = neuron_ms / max(1, n_launch_neuron)
         steps_per_launch = STEPS_PER_SIM / max(1, n_launch_neuron)
-        n_exp, n_div = mufu_ops_per_neuron_step(inp.CLASSIC_HH)
+        # the window launch's duration inside the timed schedule: the timed
+        # step divided by its window launches (an upper bound on each launch:
+        # it includes the routing that co-runs with it and the waits on burst
+        # windows), so that launches x duration never exceeds the step
+        in_step_ms = (ms_max / args.steps) / max(1, n_launch_neuron)
+        assert n_launch_neuron * in_step_ms <= ms_max / args.steps * (1 + 1e-9)
+        n_exp, n_div = ALGO_EXP_PER_STEP, ALGO_DIV_PER_STEP
+        k_exp, k_div = mufu_ops_per_neuron_step(inp.CLASSIC_HH)
         mufu = n_exp + n_div
         # one cooperative launch per call (routing inside it) or one neuron
         # launch per window with routing launches beside it
         dominant = ("hh_jit_persistent (whole step in one cooperative launch, routing between steps)"
                     if n_launch_route == 0 else "hh_jit_window (k_net_window specialised by NVRTC)")
-        achieved_gops = mufu * W["n"] * steps_per_launch / (avg_neuron_ms * 1e-3) / 1e9
+        ops_per_launch = mufu * W["n"] * steps_per_launch
+        achieved_gops = ops_per_launch / (in_step_ms * 1e-3) / 1e9
         # SFU bound of one neuron-step from the measured rates: n_exp
         # ex2.approx and n_div rcp.approx results; the peak is the op count
         # over that time.  The nominal 16 results/clk/SM x sm_max stays in the
         # line for context.
         t_sfu = n_exp / sfu_peaks["ex2_per_s"] + n_div / sfu_peaks["rcp_per_s"]
         peak_gops = mufu / t_sfu / 1e9
+        t_sfu_k = k_exp / sfu_peaks["ex2_per_s"] + k_div / sfu_peaks["rcp_per_s"]
+        frac_kernel_count = W["n"] * steps_per_launch * t_sfu_k / (in_step_ms * 1e-3)
         nominal_gops = SM_COUNT * MUFU_PER_SM_CLK * sm_max * 1e6 / 1e9
         cpu = cpu_baseline_sample(cores=os.cpu_count()) if not args.no_cpu_baseline else None
         cpu1 = cpu_baseline_sample(cores=1, sim_steps=200) if not args.no_cpu_baseline else None
         line = {
             "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
             "value": value, "unit": "neuron-steps/s", "n_gpus": world, "steps": args.steps,
+            "time_steps_per_step": STEPS_PER_SIM,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(),
@@ -355,24 +373,33 @@ def run_gpu(args):
                     "h2d_bytes_per_step": W["n"] * 4, "d2h_bytes_per_step": d2h},
             "gpu_launches": (1 + n_launch_neuron + n_launch_route) * args.steps * world,
             "kernels": {"neuron_window": {"launches_per_step": n_launch_neuron,
-                                          "avg_us": avg_neuron_ms * 1e3,
+                                          "in_step_avg_us": in_step_ms * 1e3,
+                                          "profiled_avg_us": avg_neuron_ms * 1e3,
+                                          "profiled_schedule": "hh_profile: launch by launch, CUDA events "
+                                                               "around each launch (no graph)",
                                           "share_of_step": neuron_ms / max(1e-9, neuron_ms + route_ms)},
                         "route": {"launches_per_step": n_launch_route,
                                   "avg_us": route_ms / max(1, n_launch_route) * 1e3}},
             "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops,
                          "unit": "Gop/s (SFU-class: exp + div)",
                          "frac": achieved_gops / peak_gops,
+                         "duration_source": "timed step / window launches per step (the launch's share "
+                                            "of the timed graph schedule, routing co-running)",
                          # dram__bytes_read.sum + dram__bytes_write.sum of one hh_jit_window
                          # launch (20 steps, cold L2) in an ncu capture of this kernel: the 16 B
                          # of delay line per neuron-step plus the state, nothing re-read
-                         "traffic": WINDOW_TRAFFIC_BYTES if n_launch_route > 0 else None,
+                         "traffic": WINDOW_TRAFFIC_BYTES if (n_launch_route > 0 and WINDOW_TRAFFIC_BYTES) else None,
                          "traffic_unit": "bytes per launch (ncu, cold L2)",
                          "peak_source": f"measured (hh_measure_peaks, all SMs, CUDA events): {n_exp} ex2.approx "
                                         f"+ {n_div} rcp.approx per neuron-step at the measured rates",
                          "nominal_peak": nominal_gops,
                          "nominal_source": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} SFU ops/clk x "
                                            f"{sm_max:.0f} MHz ({pk_kind} sm_max)",
-                         "ops_per_neuron_step": {"exp": n_exp, "div": n_div}, "kernel": dominant},
+                         "ops_per_neuron_step": {"exp": n_exp, "div": n_div,
+                                                 "source": "algorithmic count of the classic step"},
+                         "frac_at_kernel_op_count": frac_kernel_count,
+                         "kernel_ops_per_neuron_step": {"exp": k_exp, "div": k_div},
+                         "kernel": dominant},
             "clocks": clk,
             "peaks_measured": {k: v / 1e9 for k, v in sfu_peaks.items()} | {"unit": "G results/s"},
         }
@@ -596,6 +623,7 @@ def run_reference(args):
     value = W["n"] * sample_steps * args.steps / tot
     line = {"impl": "reference", "metric": "HH neuron-steps/s (conductance-based network, plain FP32 path)",
             "value": value, "unit": "neuron-steps/s", "n_gpus": world, "steps": args.steps,
+            "time_steps_per_step": sample_steps,
             "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),

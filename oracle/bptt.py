@@ -137,6 +137,33 @@ def layer_run(model, X, W_in, W_rec, bias, *, dt=0.01, K=10, theta=0.0, beta=0.5
     return torch.stack(spikes), V
 
 
+def threshold_margin(model, X, W_in, W_rec, bias, *, dt=0.01, K=10, theta=0.0, V0=-65.0):
+    """min over every substep of |V_k - theta| per (sample, neuron), [B, N],
+    from the FP64 forward.  The surrogate gradient switches where V_{k-1}
+    crosses theta (the (1 - H(V_{k-1} - theta)) factor), so a trajectory that
+    passes closer to theta than another arithmetic's rounding of V can put a
+    crossing in a different substep and change the gradient by O(1): this is
+    the conditioning of the method's gradient, read off the oracle alone."""
+    with torch.no_grad():
+        X, W_in, W_rec, bias = (torch.as_tensor(a, dtype=DT) for a in (X, W_in, W_rec, bias))
+        T, B, _ = X.shape
+        N = W_in.shape[1]
+        V = torch.full((B, N), float(V0), dtype=DT)
+        ps = init_state(model, V)
+        S_prev = torch.zeros((B, N), dtype=DT)
+        m = torch.full((B, N), float("inf"), dtype=DT)
+        for t in range(T):
+            I = bias + X[t] @ W_in + S_prev @ W_rec
+            s_t = torch.zeros((B, N), dtype=DT)
+            for _ in range(K):
+                Vn, ps = substep(model, V, ps, I, dt)
+                m = torch.minimum(m, (Vn - theta).abs())
+                s_t = s_t + ((Vn >= theta) & ~(V >= theta)).to(DT)
+                V = Vn
+            S_prev = s_t
+    return m.numpy()
+
+
 def layer_forward(model, X, W_in, W_rec, W_out, bias, labels, *, dt=0.01, K=10, theta=0.0,
                   beta=0.5, smooth=False, V0=-65.0, return_all=False):
     """X: [T, B, n_in] (0/1), W_in [n_in, N], W_rec [N, N], W_out [n_out, N],

@@ -448,7 +448,7 @@ def make_record(N, n_steps, *, trace=0, trace_idx=None, spike_cap=0, counts=True
     b = {}
     r = hh_record()
     if trace:
-        b["V_trace"] = torch.empty((n_steps, trace), dtype=torch.float32, device=device)
+        b["V_trace"] = torch.zeros((n_steps, trace), dtype=torch.float32, device=device)
         r.V_trace = b["V_trace"].data_ptr()
         r.n_trace = trace
         if trace_idx is not None:
