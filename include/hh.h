@@ -596,6 +596,19 @@ void hh_destroy(hh_net* net);
 /* Thread-local description of the last error of the calling thread. */
 const char* hh_last_error(void);
 
+/* Bounds of the device-side waits, for every later launch in the process
+ * (failure detection: a wait that runs out records a status and the kernel
+ * returns, so that the context stays usable).  progress_ns bounds each wait
+ * of the persistent kernel on another block's progress counter (global
+ * timer; default 2e9 = 2 s; on expiry HH_STATUS_BARRIER_TIMEOUT is set);
+ * mbarrier_polls bounds each wait of the tensor-core GEMM's pipeline on its
+ * TMA / MMA / epilogue mbarriers (default 2^24 polls; on expiry a nonzero
+ * code is ORed into the GEMM's status word).  0 gives up at the first wait
+ * that has not completed; a negative value restores the default.  The
+ * GEMM's final wait for its own TMA loads in flight always uses the
+ * default, so no copy lands after its block exits.  Errors: none. */
+hh_status hh_set_wait_limits(int64_t progress_ns, int64_t mbarrier_polls);
+
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t hh_version(void);
 

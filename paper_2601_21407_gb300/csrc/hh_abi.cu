@@ -1,5 +1,6 @@
 // C ABI of libhh (see include/hh.h): argument validation, ownership of the
 // network's device memory, model preparation and the launch schedule.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,9 +13,15 @@
 
 namespace {
 thread_local std::string g_err;
+// bounds of the device-side waits, process-wide (hh_set_wait_limits)
+std::atomic<unsigned long long> g_wait_ns{hh::kWaitLimitNs};
+std::atomic<long long> g_wait_polls{hh::kWaitLimitPolls};
 }  // namespace
 
 namespace hh {
+unsigned long long wait_limit_ns() { return g_wait_ns.load(); }
+long long wait_polls() { return g_wait_polls.load(); }
+
 hh_status fail(hh_status s, const char* fmt, ...)
 {
     char buf[2048];
@@ -69,7 +76,7 @@ struct hh_net {
     int64_t* out_ptr = nullptr;
     int32_t* out_post = nullptr;
     float* out_w = nullptr;
-    int64_t *ringE = nullptr, *ringI = nullptr;
+    int64_t* ring = nullptr;  // [R][N][2]: {E, I} per neuron and slot
     int32_t D = 1, R = 1;
     int32_t route_segs = 1;  // most 256-synapse segments in one out-CSR row
     float tau_E = 1.0f, tau_I = 1.0f, E_E = 0.0f, E_I = 0.0f, area = 1.0f;
@@ -268,8 +275,7 @@ struct hh_net {
         p.I_const = I_const;
         p.trace_slot = nullptr;
         p.status = status;
-        p.ringE = ringE;
-        p.ringI = ringI;
+        p.ring = ring;
         p.R = R;
         p.E_E = E_E;
         p.E_I = E_I;
@@ -284,6 +290,12 @@ struct hh_net {
         p.bg_n = nb;
         p.bg_w = bg_w;
         p.seed = seed;
+        // Philox-4x32-10 key schedule (Salmon et al.): the key is bumped by
+        // the Weyl constants after every round
+        for (uint32_t r = 0; r < 10; ++r) {
+            p.rk[2 * r] = (uint32_t)seed + r * 0x9E3779B9u;
+            p.rk[2 * r + 1] = (uint32_t)(seed >> 32) + r * 0xBB67AE85u;
+        }
         for (int j = 0; j < hh::kMaxPoisson; ++j)
             p.bg_thr[j] = thr[j] < (1ull << 32) ? (uint32_t)thr[j] : 0xffffffffu;
         return p;
@@ -297,8 +309,9 @@ struct hh_net {
         r.out_post = out_post;
         r.out_w = out_w;
         r.inh = inh;
-        r.ringE = ringE;
-        r.ringI = ringI;
+        r.ringE = ring;
+        r.ringI = ring ? ring + 1 : nullptr;
+        r.stride = 2;
         r.R = R;
         r.D = D;
         r.open_loop = 0;
@@ -369,6 +382,11 @@ hh::DevFn prep_fn(const hh_fn& f)
     d.ia = f.a != 0.0f ? (float)(1.0 / (double)f.a) : 0.0f;
     const double ac = (double)f.a + (double)f.c;
     d.irate = ac != 0.0 ? (float)(1.0 / ac) : 0.0f;
+    const double ak = (double)f.a * k;
+    d.n0 = (float)ak;
+    d.n1 = (float)(ak / 2.0);
+    d.n2 = (float)(ak / 12.0);
+    d.n4 = (float)(-ak / 720.0);
     return d;
 }
 
@@ -651,10 +669,10 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
     // delay ring and window spike lists
     if (n->has_syn || n->has_bg) {
         n->R = n->has_syn ? n->D : 1;
-        HH_CUDA(n->alloc(&n->ringE, (size_t)n->R * N));
-        HH_CUDA(n->alloc(&n->ringI, (size_t)n->R * N));
-        HH_CUDA(cudaMemsetAsync(n->ringE, 0, (size_t)n->R * N * sizeof(int64_t), st));
-        HH_CUDA(cudaMemsetAsync(n->ringI, 0, (size_t)n->R * N * sizeof(int64_t), st));
+        if ((uint64_t)n->R * (uint64_t)N >= (1ull << 32))
+            return fail(HH_EINVAL, "delay_steps x n_neurons must stay below 2^32 (delay-line index)");
+        HH_CUDA(n->alloc(&n->ring, (size_t)n->R * N * 2));
+        HH_CUDA(cudaMemsetAsync(n->ring, 0, (size_t)n->R * N * 2 * sizeof(int64_t), st));
         const int64_t W = n->has_syn ? n->D : 1;
         n->list.cap = N * ((W + 1) / 2) + 32;
         HH_CUDA(n->alloc(&n->list.step, (size_t)hh::kListSlots * n->list.cap));
@@ -859,7 +877,7 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
     const bool spec = net->kernels != HH_KERNELS_TABLE;
     if (spec && !net->jit_ready) {
         std::string err;
-        if (!hh::jit_get(net->models, net->installed, net->precision, &net->jit, &err))
+        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
         net->persistent_cap = -1;
@@ -905,7 +923,7 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
         const int64_t n_win = (n_steps + W - 1) / W;
         HH_CUDA(cudaMemsetAsync(net->progress, 0, 32 * sizeof(unsigned long long), net->st));
         HH_CUDA(cudaMemsetAsync(net->list.counter, 0, hh::kListSlots * sizeof(int32_t), net->st));
-        const hh::PhaseCounters pc{net->progress, net->progress + 16};
+        const hh::PhaseCounters pc{net->progress, net->progress + 16, hh::wait_limit_ns()};
         HH_CUDA(timed(HH_KERNEL_NEURON, [&] {
             return hh::jit_launch_persistent(net->jit, p, rp, net->t, n_steps, W, net->window_index, I_steps, R,
                                              net->list, pc, net->st);
@@ -934,8 +952,11 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
                     (e = cudaStreamWaitEvent(net->st, net->ev_route[(gw - 2) % hh::kListSlots], 0)) != cudaSuccess)
                     return e;
                 e = timed(HH_KERNEL_NEURON, [&] {
+                    // in the pipelined schedule the window's delay-line slots
+                    // depend only on routing launches the stream waited for
                     if (spec)
-                        return hh::jit_launch_window(net->jit, p, net->t + w0, W, slot, Iw, Rw, net->list, net->st);
+                        return hh::jit_launch_window(net->jit, p, net->t + w0, W, slot, Iw, Rw, net->list,
+                                                     pipe && net->has_syn ? 1 : 0, net->st);
                     return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, slot, Iw, Rw,
                                                  net->list, net->st);
                 });
@@ -1050,9 +1071,8 @@ hh_status hh_reset(hh_net* net, const float* V0)
     HH_CUDA(cudaMemsetAsync(net->gE, 0, net->N * sizeof(float), st));
     HH_CUDA(cudaMemsetAsync(net->gI, 0, net->N * sizeof(float), st));
     HH_CUDA(cudaMemsetAsync(net->status, 0, sizeof(int32_t), st));
-    if (net->ringE) {
-        HH_CUDA(cudaMemsetAsync(net->ringE, 0, (size_t)net->R * net->N * sizeof(int64_t), st));
-        HH_CUDA(cudaMemsetAsync(net->ringI, 0, (size_t)net->R * net->N * sizeof(int64_t), st));
+    if (net->ring) {
+        HH_CUDA(cudaMemsetAsync(net->ring, 0, (size_t)net->R * net->N * 2 * sizeof(int64_t), st));
         HH_CUDA(cudaMemsetAsync(net->list.counter, 0, hh::kListSlots * sizeof(int32_t), st));
     }
     net->t = 0;
@@ -1080,6 +1100,7 @@ hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* s
     rp.n_window = n_window;
     rp.ringE = sum_E;
     rp.ringI = sum_I;
+    rp.stride = 1;
     HH_CUDA(hh::launch_route_list(rp, spk_step, spk_idx, n_spk, net->st));
     return HH_OK;
 }
@@ -1190,7 +1211,7 @@ hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surroga
         return fail(HH_ESTATE, "model 0 is not installed");
     if (!net->jit_ready) {
         std::string err;
-        if (!hh::jit_get(net->models, net->installed, net->precision, &net->jit, &err))
+        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
     }
@@ -1241,6 +1262,13 @@ void hh_destroy(hh_net* net)
 const char* hh_last_error(void) { return g_err.c_str(); }
 
 int32_t hh_version(void) { return 0x000100; }
+
+hh_status hh_set_wait_limits(int64_t progress_ns, int64_t mbarrier_polls)
+{
+    g_wait_ns.store(progress_ns < 0 ? hh::kWaitLimitNs : (unsigned long long)progress_ns);
+    g_wait_polls.store(mbarrier_polls < 0 ? hh::kWaitLimitPolls : (long long)mbarrier_polls);
+    return HH_OK;
+}
 
 }  // extern "C"
 

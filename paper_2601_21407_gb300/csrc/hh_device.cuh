@@ -44,6 +44,9 @@ struct DevFn {
     float vh2, ik2, s2, b2;    // second exponential (bell)
     float ia;                  // 1/a (0 when a = 0)
     float irate;               // 1/(a + c) (0 when a + c = 0): a constant rate's reciprocal
+    // the linoid's series a k (1 + y/2 + y^2/12 - y^4/720) on the SFU path
+    // as n0 + n1 y + y^2 (n2 + n4 y^2)
+    float n0, n1, n2, n4;
 };
 
 struct DevGate {
@@ -94,9 +97,9 @@ struct NeuronParams {
     const float* I_const;  // [N] or nullptr
     const int32_t* trace_slot;  // [N] or nullptr (slot = i for i < n_trace)
     int32_t* status;
-    // synapses
-    int64_t* ringE;   // [R][N] fixed point 2^-32 nS
-    int64_t* ringI;
+    // synapses: the delay line, [R][N] entries of {E, I} (16 bytes, one
+    // load per neuron-step), fixed point 2^-32 nS; R N < 2^32
+    int64_t* ring;
     int32_t R;        // ring slots (= delay steps)
     float E_E, E_I, decE, decI, to_mS;
     // background
@@ -104,6 +107,8 @@ struct NeuronParams {
                       // #{j < bg_n : word >= bg_thr[j]} (nondecreasing table)
     float bg_w;
     uint64_t seed;
+    // Philox-4x32-10 round keys of the seed: (k0, k1) of round r at 2r, 2r + 1
+    uint32_t rk[20];
     uint32_t bg_thr[kMaxPoisson];
 };
 // thresholds compared without a loop on every step (the rest only after a
@@ -128,8 +133,9 @@ struct RouteParams {
     const int32_t* out_post;
     const float* out_w;
     const uint8_t* inh;
-    int64_t* ringE;
-    int64_t* ringI;
+    int64_t* ringE;    // destination of excitatory spikes (ring: the E words)
+    int64_t* ringI;    // of inhibitory spikes (ring: the I words, ringE + 1)
+    int32_t stride;    // words between neighbouring neurons: 2 in the ring, 1 open loop
     int32_t R;         // slots in the destination (ring: R = D; open loop: unused)
     int32_t D;
     int32_t open_loop; // 1: destination is [n_window][N] linear, drop >= n_window
@@ -202,11 +208,13 @@ __device__ __forceinline__ float rate(const DevFn& f, float V)
         // SFU path uses the Bernoulli series 1 + y/2 + y^2/12 - y^4/720
         // (truncation < 1e-10 for |y| < 0.1); the accurate path uses expm1f.
         // Both branches are evaluated and one selected (no divergent branch).
+        // x = V - vh is formed first: near vh the difference is exact, and
+        // both y and a x keep their relative accuracy there
         const float x = V - f.vh;
         if (FAST) {
             const float y = x * f.ik;
             const float y2 = y * y;
-            const float near0 = f.a * f.k * (1.0f + 0.5f * y + y2 * (1.0f / 12.0f - y2 * (1.0f / 720.0f)));
+            const float near0 = fmaf(y2, fmaf(y2, f.n4, f.n2), fmaf(y, f.n1, f.n0));
             const float far = f.a * x * rcpa(1.0f - ex2a(-y * kLog2e));
             r = fabsf(y) < 0.1f ? near0 : far;
         } else {
@@ -466,11 +474,11 @@ __device__ __forceinline__ void store_state(const NeuronParams& P, int64_t i, co
 
 // Warp-aggregated append of this step's spikes to the caller's record:
 // one atomic per warp (ballot + popc), each spiking lane writes its slot.
-// frac = (theta - Vt)/(V - Vt) is formed only by lanes that spiked.
-__device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t idx, float theta, float Vt,
-                                              float V, const RecordParams& R, int32_t* status)
+// frac = (theta - Vt)/(V - Vt) is formed only by lanes that spiked.  `b` is
+// the warp's ballot of spk.
+__device__ __forceinline__ void record_spikes_b(unsigned b, bool spk, int32_t step, int32_t idx, float theta,
+                                                float Vt, float V, const RecordParams& R, int32_t* status)
 {
-    const unsigned b = __ballot_sync(kFull, spk);
     if (b == 0u || R.n_spikes == nullptr)
         return;
     const int lane = threadIdx.x & 31;
@@ -493,10 +501,15 @@ __device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t id
     }
 }
 
-__device__ __forceinline__ void list_append(bool spk, int32_t step, int32_t idx, int32_t* counter,
-                                            int32_t* lstep, int32_t* lidx, int64_t cap)
+__device__ __forceinline__ void record_spikes(bool spk, int32_t step, int32_t idx, float theta, float Vt,
+                                              float V, const RecordParams& R, int32_t* status)
 {
-    const unsigned b = __ballot_sync(kFull, spk);
+    record_spikes_b(__ballot_sync(kFull, spk), spk, step, idx, theta, Vt, V, R, status);
+}
+
+__device__ __forceinline__ void list_append_b(unsigned b, bool spk, int32_t step, int32_t idx, int32_t* counter,
+                                              int32_t* lstep, int32_t* lidx, int64_t cap)
+{
     if (b == 0u)
         return;
     const int lane = threadIdx.x & 31;
@@ -524,6 +537,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
         k.x += 0x9E3779B9u;
         k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same with the ten round keys precomputed (rk[2r], rk[2r + 1] =
+// k + r (0x9E3779B9, 0xBB67AE85)): no key additions per draw.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
     }
     return c;
 }
@@ -591,9 +617,11 @@ __device__ __forceinline__ void load_chunk(const RouteParams& RP, int64_t ea, in
     }
 }
 
-// The atomics of one loaded chunk (entries outside [e0, e1) skipped).
-__device__ __forceinline__ void deliver_chunk(unsigned long long* dst, int64_t ea, int64_t e0, int64_t e1,
-                                              const int4& pa, const int4& pb, const float4& wa, const float4& wb)
+// The atomics of one loaded chunk (entries outside [e0, e1) skipped); the
+// destination word of target p is dst[p * stride].
+__device__ __forceinline__ void deliver_chunk(unsigned long long* dst, int32_t stride, int64_t ea, int64_t e0,
+                                              int64_t e1, const int4& pa, const int4& pb, const float4& wa,
+                                              const float4& wb)
 {
     const int64_t eb = ea + 128;
     const int pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
@@ -602,8 +630,15 @@ __device__ __forceinline__ void deliver_chunk(unsigned long long* dst, int64_t e
     for (int q = 0; q < 8; ++q) {
         const int64_t e = (q < 4 ? ea : eb) + (q & 3);
         if (e >= e0 && e < e1)
-            atomicAdd(dst + pp[q], nS_to_fixed(ww[q]));
+            atomicAdd(dst + (int64_t)pp[q] * stride, nS_to_fixed(ww[q]));
     }
+}
+
+// Destination of presynaptic neuron j's spikes arriving in row `row`.
+__device__ __forceinline__ unsigned long long* route_dst(const RouteParams& RP, int32_t j, int64_t row)
+{
+    return reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) +
+                                                 row * RP.N * RP.stride);
 }
 
 __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_t* __restrict__ st,
@@ -623,8 +658,7 @@ __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_
         } else {
             row = ((int64_t)t + RP.D) % RP.R;
         }
-        unsigned long long* dst =
-            reinterpret_cast<unsigned long long*>((RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
+        unsigned long long* dst = route_dst(RP, j, row);
         const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
         // 256 synapses per warp iteration, software-pipelined: the next
         // chunk's (target, weight) loads are issued before this chunk's
@@ -641,7 +675,7 @@ __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_
             int4 qa, qb;
             float4 va, vb;
             load_chunk(RP, base + 256 + 4 * lane, e1, qa, qb, va, vb);
-            deliver_chunk(dst, base + 4 * lane, e0, e1, pa, pb, wa, wb);
+            deliver_chunk(dst, RP.stride, base + 4 * lane, e0, e1, pa, pb, wa, wb);
             pa = qa;
             pb = qb;
             wa = va;
@@ -673,12 +707,11 @@ __device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t
             const int64_t base = (e0 & ~(int64_t)3) + 256 * (int64_t)q;
             const int64_t row = RP.open_loop ? (int64_t)t + RP.D : ((int64_t)t + RP.D) % RP.R;
             if (base < e1 && (!RP.open_loop || row < RP.n_window)) {
-                unsigned long long* dst = reinterpret_cast<unsigned long long*>(
-                    (RP.inh && RP.inh[j] ? RP.ringI : RP.ringE) + row * RP.N);
+                unsigned long long* dst = route_dst(RP, j, row);
                 int4 pa, pb;
                 float4 wa, wb;
                 load_chunk(RP, base + 4 * lane, e1, pa, pb, wa, wb);
-                deliver_chunk(dst, base + 4 * lane, e0, e1, pa, pb, wa, wb);
+                deliver_chunk(dst, RP.stride, base + 4 * lane, e0, e1, pa, pb, wa, wb);
             }
         }
         sp += dsp;
@@ -773,11 +806,37 @@ __device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams&
     }
 }
 
+// The delay-line entries of the next kRingAhead steps of one neuron, in
+// flight in registers ({E, I} per step: one 16-byte load each).  Slots past
+// the window are read and discarded; inside it the slots are distinct (W <=
+// R) and only cleared after their own step.
+struct RingQueue {
+    longlong2 q[kRingAhead];
+    uint32_t ring_slot;  // slot of the next step
+    uint32_t far_slot;   // slot of the next load
+};
+
+__device__ __forceinline__ longlong2* ring_entry(const NeuronParams& P, uint32_t slot, int64_t i)
+{
+    return reinterpret_cast<longlong2*>(P.ring) + (slot * (uint32_t)P.N + (uint32_t)i);
+}
+
+__device__ __forceinline__ void ring_preload(const NeuronParams& P, int64_t i, int64_t t0, RingQueue& rq)
+{
+    rq.ring_slot = (uint32_t)(t0 % P.R);
+    rq.far_slot = rq.ring_slot;
+#pragma unroll
+    for (int a = 0; a < kRingAhead; ++a) {
+        rq.q[a] = __ldcg(ring_entry(P, rq.far_slot, i));
+        rq.far_slot = rq.far_slot + 1 == (uint32_t)P.R ? 0u : rq.far_slot + 1;
+    }
+}
+
 // W <= D time steps of one network neuron with its state in registers.
 // The delay-line slots of the window were completed by earlier routing;
 // they are read through L2 (.cg: they were written by atomics from other
-// blocks) kRingAhead steps ahead, and cleared after use.  Spikes go to list slot
-// `lslot` (and to the caller's record).
+// blocks) kRingAhead steps ahead (rq, preloaded by the caller), and cleared
+// after use.  Spikes go to list slot `lslot` (and to the caller's record).
 // `between(k)` runs after step k with the whole warp (all lanes, valid or
 // not): the persistent kernel routes part of the previous window there.
 struct NoWork {
@@ -789,36 +848,19 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
                                                 const float* __restrict__ I_steps, const RecordParams& R,
                                                 float* V_trace, int32_t slot, const SpikeList& L, int32_t lslot,
                                                 State<MAXG, PREC>& s, float& gE, float& gI, float Ic,
-                                                int32_t& cnt, uint2 key, const Between& between)
+                                                int32_t& cnt, RingQueue& rq, const Between& between)
 {
-    // The delay-line slots of the next kRingAhead steps are in flight in a
-    // register queue: the step itself is shorter than an L2 round trip.
-    // (Slots past the window are read and discarded; inside it the slots are
-    // distinct, W <= R, and only cleared after their own step.)
-    int32_t ring_slot = (int32_t)(t0 % P.R);
-    int32_t far_slot = ring_slot;
-    long long qE[kRingAhead], qI[kRingAhead];
-#pragma unroll
-    for (int a = 0; a < kRingAhead; ++a) {
-        qE[a] = __ldcg(P.ringE + (int64_t)far_slot * P.N + i);
-        qI[a] = __ldcg(P.ringI + (int64_t)far_slot * P.N + i);
-        far_slot = far_slot + 1 == P.R ? 0 : far_slot + 1;
-    }
     int32_t* lstep = L.step + lslot * L.cap;
     int32_t* lidx = L.idx + lslot * L.cap;
     // one step; `word` is the background word of step t0 + k
     auto step = [&](int32_t k, uint32_t word) {
         const int64_t t = t0 + k;
-        const long long e = qE[0], h = qI[0];
+        const long long e = rq.q[0].x, h = rq.q[0].y;
 #pragma unroll
-        for (int a = 0; a + 1 < kRingAhead; ++a) {
-            qE[a] = qE[a + 1];
-            qI[a] = qI[a + 1];
-        }
-        qE[kRingAhead - 1] = __ldcg(P.ringE + (int64_t)far_slot * P.N + i);
-        qI[kRingAhead - 1] = __ldcg(P.ringI + (int64_t)far_slot * P.N + i);
-        far_slot = far_slot + 1 == P.R ? 0 : far_slot + 1;
-        const int32_t next_slot = ring_slot + 1 == P.R ? 0 : ring_slot + 1;
+        for (int a = 0; a + 1 < kRingAhead; ++a)
+            rq.q[a] = rq.q[a + 1];
+        rq.q[kRingAhead - 1] = __ldcg(ring_entry(P, rq.far_slot, i));
+        rq.far_slot = rq.far_slot + 1 == (uint32_t)P.R ? 0u : rq.far_slot + 1;
         // a. delayed synaptic input (fixed point 2^-32 nS) and background
         // (added unconditionally: + 0 changes no bit, and the step stays
         // free of branches the scheduler cannot look across).  The
@@ -827,13 +869,9 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         // decay into this addition: every copy gives the same bits.
         gE = __fadd_rn(gE, fixed_to_nS(e));
         gI = __fadd_rn(gI, fixed_to_nS(h));
-        if (valid) {
-            const int64_t o = (int64_t)ring_slot * P.N + i;
-            if (e)
-                P.ringE[o] = 0;
-            if (h)
-                P.ringI[o] = 0;
-        }
+        if (valid && (e | h))
+            *ring_entry(P, rq.ring_slot, i) = make_longlong2(0, 0);
+        rq.ring_slot = rq.ring_slot + 1 == (uint32_t)P.R ? 0u : rq.ring_slot + 1;
         if (BG)
             gE = fmaf((float)poisson_count(word, P.bg_thr, P.bg_n), P.bg_w, gE);
         const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
@@ -842,13 +880,16 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
                                       __fmul_rn(gI, P.to_mS), P.E_I, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
         cnt += spk;
-        list_append(spk, (int32_t)t, (int32_t)i, L.counter + lslot, lstep, lidx, L.cap);
-        record_spikes(spk, (int32_t)t, (int32_t)i, P.theta, Vt, s.V, R, P.status);
+        // one ballot for the window list and the caller's record
+        const unsigned b = __ballot_sync(kFull, spk);
+        if (b) {
+            list_append_b(b, spk, (int32_t)t, (int32_t)i, L.counter + lslot, lstep, lidx, L.cap);
+            record_spikes_b(b, spk, (int32_t)t, (int32_t)i, P.theta, Vt, s.V, R, P.status);
+        }
         if (slot >= 0)
             V_trace[(int64_t)k * R.n_trace + slot] = s.V;
         gE = __fmul_rn(gE, P.decE);
         gI = __fmul_rn(gI, P.decI);
-        ring_slot = next_slot;
         between(k);
     };
     // The background words of steps 4q..4q+3 come from one Philox block
@@ -857,7 +898,7 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         uint4 r = make_uint4(0, 0, 0, 0);
         if (BG) {
             const uint64_t q = (uint64_t)t >> 2;
-            r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), key);
+            r = philox4x32_10_rk(make_uint4((uint32_t)q, (uint32_t)i, 1u, (uint32_t)(q >> 32)), P.rk);
         }
         return r;
     };
@@ -910,37 +951,49 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
                                              int64_t i, int64_t t0, int32_t W, const float* __restrict__ I_steps,
                                              const RecordParams& R, float* V_trace, int32_t slot,
                                              const SpikeList& L, int32_t lslot, State<MAXG, PREC>& s,
-                                             float& gE, float& gI, float Ic, int32_t& cnt, uint2 key,
+                                             float& gE, float& gI, float Ic, int32_t& cnt, RingQueue& rq,
                                              const Between& between)
 {
     if (P.bg_n > 0)
         window_steps_bg<MAXG, PREC, true, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
-                                                 lslot, s, gE, gI, Ic, cnt, key, between);
+                                                 lslot, s, gE, gI, Ic, cnt, rq, between);
     else
         window_steps_bg<MAXG, PREC, false, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
-                                                  lslot, s, gE, gI, Ic, cnt, key, between);
+                                                  lslot, s, gE, gI, Ic, cnt, rq, between);
 }
 
 // Network window: W <= D steps; spikes go to the window list for routing.
 // The input of every step in the window comes from spikes at least D steps
 // earlier, already routed by previous launches, so neurons are independent
 // inside the window.
+// early != 0: the launch follows the pipelined schedule, in which the
+// delay-line slots of this window were completed by routing launches that
+// the stream waited for with full event dependencies, and no kernel that
+// may still be running writes them; the first slots are then read before
+// the programmatic wait, overlapping their latency with the previous
+// window's tail.
 template <int MAXG, int PREC, int GROUP, class Dyn>
 __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& P, int64_t t0,
                                             int32_t W, const float* __restrict__ I_steps,
-                                            const RecordParams& R, const SpikeList& L, int32_t parity)
+                                            const RecordParams& R, const SpikeList& L, int32_t parity,
+                                            int32_t early)
 {
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = gi < P.N;
+    const int64_t i = valid ? gi : 0;
+    RingQueue rq;
+    if (early)
+        ring_preload(P, i, t0, rq);
     // Programmatic dependent launch (when the launch asks for it; no-ops
     // otherwise): the next window's blocks may be scheduled now, and this
     // window waits for the previous kernel of the stream to complete before
     // it touches the state that kernel wrote.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!early)
+        ring_preload(P, i, t0, rq);
     if (gi == 0)
         L.counter[parity + 1 == kListSlots ? 0 : parity + 1] = 0;  // next window's slot (its reader has finished)
-    const bool valid = gi < P.N;
-    const int64_t i = valid ? gi : 0;
     const int mid = P.model_id ? P.model_id[i] : 0;
     State<MAXG, PREC> s;
     load_state(P, i, s);
@@ -952,10 +1005,9 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
     if (!valid)
         slot = -1;
-    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     int32_t cnt = 0;
     window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, R.V_trace, slot, L, parity, s, gE, gI,
-                             Ic, cnt, key, NoWork{});
+                                    Ic, cnt, rq, NoWork{});
     if (valid) {
         store_state(P, i, s);
         P.gE[i] = gE;
@@ -975,14 +1027,18 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
 // number of blocks or warps.  This is exact because no block or warp gets
 // more than two windows ahead of the slowest one (see persistent_body), so
 // a slot never holds a contribution from a later window than the one
-// waited for.  Waits are bounded by the global timer (kWaitLimitNs); on
-// expiry the waiter records HH_STATUS_BARRIER_TIMEOUT and gives up.
+// waited for.  Waits are bounded by the global timer (pc.limit_ns,
+// kWaitLimitNs by default); on expiry the waiter records
+// HH_STATUS_BARRIER_TIMEOUT and gives up.
 constexpr int kPhaseSlots = 4;
 struct PhaseCounters {
     unsigned long long* done;    // [kPhaseSlots], one count per neuron block
     unsigned long long* routed;  // [kPhaseSlots], one count per block's routing warps (own 128-B line)
+    unsigned long long limit_ns; // bound of every wait (kWaitLimitNs by default)
 };
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// default bound of a tensor-core pipeline's mbarrier wait, in polls
+constexpr long long kWaitLimitPolls = 1ll << 24;
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -992,14 +1048,14 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 __device__ __forceinline__ bool wait_at_least(const unsigned long long* c, unsigned long long target,
-                                              int32_t* status)
+                                              int32_t* status, unsigned long long limit_ns)
 {
     const volatile unsigned long long* p = c;
     if (*p < target) {
         const unsigned long long t0 = global_ns();
         unsigned ns = 32;  // back-off: few pollers on a line every other SM reads
         while (*p < target) {
-            if (global_ns() - t0 > kWaitLimitNs) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicOr(status, HH_STATUS_BARRIER_TIMEOUT);
                 return false;
             }
@@ -1093,7 +1149,8 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
     auto list_step = [&](int32_t w) { return L.step + (int32_t)((w_index0 + w) % kListSlots) * L.cap; };
     auto list_idx = [&](int32_t w) { return L.idx + (int32_t)((w_index0 + w) % kListSlots) * L.cap; };
     auto window_done = [&](int32_t w, unsigned long long* c, unsigned long long per) {
-        return wait_at_least(c + w % kPhaseSlots, (unsigned long long)(w / kPhaseSlots + 1) * per, P.status);
+        return wait_at_least(c + w % kPhaseSlots, (unsigned long long)(w / kPhaseSlots + 1) * per, P.status,
+                             pc.limit_ns);
     };
     bool ok = true;
     if (threadIdx.x >= kPersistNeurons) {
@@ -1131,7 +1188,6 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
         int32_t slot = -1;
         if (R.V_trace && valid)
             slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
-        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
         int32_t cnt = 0;
         for (int32_t w = 0; w < n_win; ++w) {
             if (w >= 2) {
@@ -1144,10 +1200,13 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
                 }
             }
             const int32_t Ww = min(W, n_steps - w * W);
+            RingQueue rq;
+            ring_preload(P, i, t0 + (int64_t)w * W, rq);
             window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0 + (int64_t)w * W, Ww,
-                                     I_steps ? I_steps + (int64_t)w * W * P.N : nullptr, R,
-                                     R.V_trace ? R.V_trace + (int64_t)w * W * R.n_trace : nullptr, slot, L,
-                                     (int32_t)((w_index0 + w) % kListSlots), s, gE, gI, Ic, cnt, key, NoWork{});
+                                            I_steps ? I_steps + (int64_t)w * W * P.N : nullptr, R,
+                                            R.V_trace ? R.V_trace + (int64_t)w * W * R.n_trace : nullptr, slot, L,
+                                            (int32_t)((w_index0 + w) % kListSlots), s, gE, gI, Ic, cnt, rq,
+                                            NoWork{});
             neuron_bar();
             if (threadIdx.x == 0)
                 signal_done(pc.done + w % kPhaseSlots);

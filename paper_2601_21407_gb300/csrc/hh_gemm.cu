@@ -38,6 +38,7 @@ namespace hh {
 namespace {
 
 using namespace tc;
+static_assert(kWaitLimit == kWaitLimitPolls, "one default bound of the mbarrier waits");
 
 constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
 constexpr int kEpiWarps = 4;
@@ -55,6 +56,7 @@ struct TileGrid {
     int tiles_n, tiles_m, splits;
     int k_blocks, kb_per_split;
     int a_row0, b_row0;
+    long long polls;  // limit of the pipeline's mbarrier waits
 };
 
 __device__ __forceinline__ void tile_of(const TileGrid& g, int tile, int& m0, int& n0, int& split, int& kb0,
@@ -114,7 +116,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                 for (int i = 0; i < nkb; ++i) {
                     const int s = issued % kStages;
                     const uint32_t ph = (issued / kStages) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, err, 1, g.polls)) {
                         ok = false;
                         break;
                     }
@@ -134,7 +136,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
                 const int acc = it & 1;
                 const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-                if (!mbar_wait(&tempty[acc], aph ^ 1u, err, 2))
+                if (!mbar_wait(&tempty[acc], aph ^ 1u, err, 2, g.polls))
                     break;
                 tc_fence_after();
                 int m0, n0, split, kb0, nkb;
@@ -144,7 +146,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                 for (int i = 0; i < nkb; ++i) {
                     const int s = used % kStages;
                     const uint32_t ph = (used / kStages) & 1u;
-                    if (!mbar_wait(&full[s], ph, err, 4)) {
+                    if (!mbar_wait(&full[s], ph, err, 4, g.polls)) {
                         ok = false;
                         break;
                     }
@@ -175,7 +177,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             const uint32_t aph = (uint32_t)(it >> 1) & 1u;
             int got = 1;
             if (lane == 0)
-                got = mbar_wait(&tfull[acc], aph, err, 8) ? 1 : 0;
+                got = mbar_wait(&tfull[acc], aph, err, 8, g.polls) ? 1 : 0;
             if (!__shfl_sync(0xffffffffu, got, 0))
                 break;
             tc_fence_after();
@@ -217,7 +219,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         __syncwarp();
     }
     // no TMA load may still be landing in shared memory when the CTA exits:
-    // the producer waits (bounded) for the last phase of every stage it used
+    // the producer waits (bounded by the default limit, whatever the
+    // pipeline's) for the last phase of every stage it used
     if (warp == 0 && lane == 0) {
         for (int i = (int)issued - 1; i >= 0 && i >= (int)issued - kStages; --i)
             mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u, err, 16);
@@ -323,6 +326,7 @@ cudaError_t launch_gemm_bf16(const GemmArgs& g, int32_t* err, cudaStream_t st)
     tg.kb_per_split = (tg.k_blocks + g.splits - 1) / g.splits;
     tg.a_row0 = g.a_row0;
     tg.b_row0 = g.b_row0;
+    tg.polls = wait_polls();
     const int n_tiles = tg.tiles_n * tg.tiles_m * tg.splits;
     const int grid = n_tiles < n_sm ? n_tiles : n_sm;
     k_gemm_bf16<<<grid, kThreads, kSmemBytes, st>>>(ma, mb, mc, tg, err);

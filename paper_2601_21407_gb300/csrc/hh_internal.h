@@ -13,6 +13,12 @@
 namespace hh {
 
 
+// Limits of the bounded device-side waits (hh_set_wait_limits; hh_abi.cu):
+// the persistent kernel's progress waits in ns of the global timer, the
+// tensor-core pipelines' mbarrier waits in polls.
+unsigned long long wait_limit_ns();
+long long wait_polls();
+
 // error reporting into the thread-local hh_last_error() message (hh_abi.cu)
 hh_status fail(hh_status s, const char* fmt, ...);
 // validate a user model and prepare it for the device (hh_abi.cu)
@@ -102,7 +108,8 @@ cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, co
                                   cudaStream_t st);
 // Compile (or take from the process-wide cache) the kernels for the installed
 // models; false with a message in *err on failure.
-bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernels* out, std::string* err);
+bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, JitKernels* out,
+             std::string* err);
 cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, int64_t t0,
                                    int32_t n_steps, const float* I_steps, const RecordParams& R,
                                    cudaStream_t st);
@@ -111,6 +118,6 @@ cudaError_t jit_launch_indexed(const JitKernels& K, const NeuronParams& P, const
                                const RecordParams& R, cudaStream_t st);
 cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_t t0, int32_t W,
                               int32_t parity, const float* I_steps, const RecordParams& R,
-                              const SpikeList& L, cudaStream_t st);
+                              const SpikeList& L, int32_t early, cudaStream_t st);
 
 }  // namespace hh

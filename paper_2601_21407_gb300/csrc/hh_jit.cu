@@ -45,7 +45,8 @@ void emit_fn(std::string& s, const char* path, const hh::DevFn& f)
     s += b;
     const struct { const char* n; float v; } fields[] = {
         {"a", f.a}, {"c", f.c}, {"vh", f.vh}, {"k", f.k}, {"ik", f.ik}, {"s", f.s}, {"b", f.b},
-        {"vh2", f.vh2}, {"ik2", f.ik2}, {"s2", f.s2}, {"b2", f.b2}, {"ia", f.ia}, {"irate", f.irate}};
+        {"vh2", f.vh2}, {"ik2", f.ik2}, {"s2", f.s2}, {"b2", f.b2}, {"ia", f.ia}, {"irate", f.irate},
+        {"n0", f.n0}, {"n1", f.n1}, {"n2", f.n2}, {"n4", f.n4}};
     for (const auto& fl : fields)
         s += std::string("    ") + path + "." + fl.n + " = " + flt(fl.v) + ";\n";
 }
@@ -115,7 +116,7 @@ std::string abi_constants()
     return s;
 }
 
-std::string generate(const hh::DevModels& M, const bool* installed, int precision, int max_gates)
+std::string generate(const hh::DevModels& M, const bool* installed, int precision, int max_gates, int v_update)
 {
     std::string s = "// generated by libhh: neuron kernels specialised for one model set\n";
     s += abi_constants();
@@ -145,6 +146,12 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
         d += "        default: break;\n        }\n";
         return d;
     };
+    {
+        // the network's V update (exponential or explicit Euler) as a constant
+        char vb[96];
+        snprintf(vb, sizeof(vb), "constexpr int kJitVUpdate = %d;\n\n", v_update);
+        s += vb;
+    }
     s += "struct JitDyn {\n";
     s += "    template <int MAXG, int PREC>\n";
     s += "    __device__ __forceinline__ void load(int mid, const NeuronParams& P, int64_t i, State<MAXG, PREC>& s) const\n    {\n";
@@ -153,7 +160,7 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
     s += "    template <int MAXG, int PREC>\n";
     s += "    __device__ __forceinline__ void step(int mid, float dt, int v_update, float I, float gsE, float EE,\n"
          "                                         float gsI, float EI, State<MAXG, PREC>& s) const\n    {\n";
-    s += dispatch("neuron_step<MAXG, PREC>(M, dt, v_update, I, gsE, EE, gsI, EI, s)");
+    s += dispatch("neuron_step<MAXG, PREC>(M, dt, kJitVUpdate, I, gsE, EE, gsI, EI, s)");
     s += "    }\n};\n\n}  // namespace hh\n\n";
     // Window steps grouped by background block (four steps unrolled) for one
     // installed model with a short step; one step per iteration otherwise,
@@ -174,8 +181,8 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
              "extern \"C\" __global__ void __launch_bounds__(%s)\n"
              "hh_jit_window(const __grid_constant__ hh::NeuronParams P, long long t0, int W,\n"
              "              const float* __restrict__ I_steps, const __grid_constant__ hh::RecordParams R,\n"
-             "              const __grid_constant__ hh::SpikeList L, int parity)\n"
-             "{\n    hh::window_body<kJitMaxG, kJitPrec, kJitGroup>(hh::JitDyn{}, P, t0, W, I_steps, R, L, parity);\n}\n\n"
+             "              const __grid_constant__ hh::SpikeList L, int parity, int early)\n"
+             "{\n    hh::window_body<kJitMaxG, kJitPrec, kJitGroup>(hh::JitDyn{}, P, t0, W, I_steps, R, L, parity, early);\n}\n\n"
              "extern \"C\" __global__ void __launch_bounds__(128)\n"
              "hh_jit_indexed(const __grid_constant__ hh::NeuronParams P, const int* __restrict__ list,\n"
              "               const int* __restrict__ n_list, long long t0, int n_steps,\n"
@@ -276,13 +283,14 @@ int block_for(int64_t N)
 
 namespace hh {
 
-bool jit_get(const DevModels& M, const bool* installed, int precision, JitKernels* out, std::string* err)
+bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, JitKernels* out,
+             std::string* err)
 {
     int max_gates = 1;
     for (int k = 0; k < kMaxModels; ++k)
         if (installed[k] && M.m[k].n_gates > max_gates)
             max_gates = M.m[k].n_gates;
-    const std::string src = generate(M, installed, precision, max_gates);
+    const std::string src = generate(M, installed, precision, max_gates, v_update);
     if (const char* path = getenv("HH_JIT_DUMP")) {
         if (FILE* f = fopen(path, "w")) {
             fwrite(src.data(), 1, src.size(), f);
@@ -368,16 +376,16 @@ cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, i
 
 cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_t t0, int32_t W,
                               int32_t parity, const float* I_steps, const RecordParams& R,
-                              const SpikeList& L, cudaStream_t st)
+                              const SpikeList& L, int32_t early, cudaStream_t st)
 {
     const int bs = block_for(P.N);
     const dim3 grid((unsigned)((P.N + bs - 1) / bs)), block(bs);
     long long t = t0;
-    int w = W, par = parity;
+    int w = W, par = parity, ea = early;
     NeuronParams p = P;
     RecordParams r = R;
     SpikeList l = L;
-    void* args[] = {&p, &t, &w, &I_steps, &r, &l, &par};
+    void* args[] = {&p, &t, &w, &I_steps, &r, &l, &par, &ea};
     // programmatic dependent launch: scheduled while the previous window
     // runs, released by its completion (griddepcontrol in the kernel)
     cudaLaunchConfig_t cfg{};

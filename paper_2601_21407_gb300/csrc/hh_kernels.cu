@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_net_window(const __grid_constant__ DevM
                                                     const __grid_constant__ SpikeList L,
                                                     int32_t parity)
 {
-    window_body<MAXG, PREC, 1>(TableDyn{Ms}, P, t0, W, I_steps, R, L, parity);
+    window_body<MAXG, PREC, 1>(TableDyn{Ms}, P, t0, W, I_steps, R, L, parity, 0);
 }
 
 // Spike routing of a list whose length is read on the device.

@@ -38,12 +38,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false (and *err set) if the phase did not complete.
-constexpr long long kWaitLimit = 1ll << 24;
+// Bounded wait: false (and *err set) if the phase did not complete within
+// `limit` polls (kWaitLimit by default; 0 gives up without polling).
+constexpr long long kWaitLimit = 1ll << 24;  // = kWaitLimitPolls (hh_device.cuh)
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code,
+                                          long long limit = kWaitLimit)
 {
-    for (long long i = 0; i < kWaitLimit; ++i)
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity))
             return true;
     atomicOr(err, code);

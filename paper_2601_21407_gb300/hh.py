@@ -134,7 +134,7 @@ EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_
            "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
            "hh_layer_forward", "hh_backward", "hh_backward_from", "hh_layer_readout", "hh_layer_destroy",
-           "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks"]
+           "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks", "hh_set_wait_limits"]
 
 
 def lib_path() -> str:
@@ -196,6 +196,8 @@ def lib():
             L.hh_version.restype = C.c_int32
             L.hh_measure_peaks.restype = C.c_int
             L.hh_measure_peaks.argtypes = [P(hh_peaks), vp]
+            L.hh_set_wait_limits.restype = C.c_int
+            L.hh_set_wait_limits.argtypes = [C.c_int64, C.c_int64]
             _lib = L
     return _lib
 
@@ -254,6 +256,11 @@ def hh_gemm_bf16(A, Bt, C, M, N, K, splits=1, status=None, stream=None):
     ldb = Bt.stride(0)
     _check(lib().hh_gemm_bf16(A.data_ptr(), lda, Bt.data_ptr(), ldb, C.data_ptr(), M, N, K, splits,
                               status.data_ptr(), stream))
+
+
+def hh_set_wait_limits(progress_ns: int = -1, mbarrier_polls: int = -1):
+    """Bounds of the device-side waits for later launches (-1 = default)."""
+    _check(lib().hh_set_wait_limits(int(progress_ns), int(mbarrier_polls)))
 
 
 def hh_destroy(net: int):

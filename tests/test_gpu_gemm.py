@@ -50,3 +50,34 @@ def test_gemm_rejects_bad_shapes():
     with pytest.raises(hh.HHError) as e:
         hh.hh_gemm_bf16(A, A, C, 128, 40, 64, status=st)   # N not a multiple of 32
     assert e.value.status == hh.HH_EINVAL
+
+
+def test_gemm_wait_expiry_reports_status():
+    """The pipeline's bounded mbarrier waits, made to run out: with the poll
+    limit at 0 every wait gives up at once, the kernel ORs a nonzero code into
+    the status word and returns (no TMA copy or MMA in flight, TMEM freed);
+    the context stays usable, and with the default limit restored the same
+    product is correct."""
+    import torch
+    M, N, K = 256, 256, 256
+    rng = np.random.default_rng(1)
+    A = inp.to_bf16_exact(rng.normal(0, 1, (M, K)))
+    B = inp.to_bf16_exact(rng.normal(0, 1, (K, N)))
+    Ad = torch.as_tensor(A, device="cuda").to(torch.bfloat16)
+    Btd = torch.as_tensor(B.T.copy(), device="cuda").to(torch.bfloat16)
+    C = torch.zeros((1, M, N), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    try:
+        hh.hh_set_wait_limits(mbarrier_polls=0)
+        hh.hh_gemm_bf16(Ad, Btd, C, M, N, K, status=st)
+        torch.cuda.synchronize()
+        code = int(st.item())
+    finally:
+        hh.hh_set_wait_limits()
+    assert code != 0 and (code & 16) == 0, code  # the drain of its own copies did not time out
+    st.zero_()
+    hh.hh_gemm_bf16(Ad, Btd, C, M, N, K, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.abs(C[0].double().cpu().numpy() - ref).max() <= 2e-6 * np.sqrt(K) * 16.0 + 1e-6 * np.abs(ref).max()
