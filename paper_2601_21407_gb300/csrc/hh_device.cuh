@@ -916,7 +916,9 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         return;
     }
     // GROUP == 4: steps grouped by Philox block, so inside a group the draw
-    // is not behind a branch and overlaps the first step's gates.
+    // is not behind a branch and overlaps the first step's gates.  (Drawing
+    // the next group's block one group ahead was measured slower: 10.4 ->
+    // 10.8 us per 20-step window.)
     int32_t k = 0;
     const int32_t head = min(W, (int32_t)((4 - (t0 & 3)) & 3));
     if (head > 0) {

@@ -7,9 +7,11 @@
 //                  delivery from the delay ring + Poisson background, rates,
 //                  gates, V, Ca, threshold, warp-aggregated spike compaction,
 //                  synaptic decay
-//   k_route        spike propagation over the out-CSR: one warp per spike,
-//                  128-bit reads of (target, weight), 64-bit fixed-point
-//                  atomic adds into the delay ring (order independent)
+//   k_route        spike propagation over the out-CSR: one warp per
+//                  (spike, 256-synapse segment) item, or per spike for
+//                  large windows; 128-bit reads of (target, weight), 64-bit
+//                  fixed-point atomic adds into the delay ring (order
+//                  independent)
 //   transpose/check/init/trace helpers.
 // The neuron bodies live in hh_device.cuh and are shared with the per-model
 // kernels compiled at run time (hh_jit.cu).
@@ -71,7 +73,15 @@ __global__ void __launch_bounds__(256) k_route(const __grid_constant__ RoutePara
         n = cap;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    route_spikes(RP, st, ix, n, warp, nw);
+    // Up to 16 segments per warp, every (spike, 256-synapse segment) item is
+    // taken by its own warp, so a spike's fan-out is not a chain of dependent
+    // row reads on one warp (a window of a few hundred spikes would wait for
+    // ten DRAM round trips per spike); beyond, one warp streams each spike's
+    // row with two chunks in flight (bursts, bound by the L2 atomics).
+    if (n * RP.segs <= 16 * nw)
+        route_items(RP, st, ix, n, warp, nw);
+    else
+        route_spikes(RP, st, ix, n, warp, nw);
 }
 
 // -------------------------------------------------------------------------
