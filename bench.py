@@ -302,7 +302,7 @@ def run_gpu(args):
     e2e_value = float(W["n"]) * STEPS_PER_SIM * e2e_steps * world / float(te.item())
 
     # the same network as one cooperative launch per step (comparison)
-    persistent_ms = None
+    persistent_ms = poly_ms = poly_spikes = None
     if rank == 0 and not args.no_extras:
         net2 = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
                           delay_steps=DELAY, bg=BG, seed=W["seed"] + rank, precision=hh.HH_PREC_FAST,
@@ -326,6 +326,29 @@ def run_gpu(args):
         torch.cuda.synchronize()
         persistent_ms = f0.elapsed_time(f1) / 2
         net2.close()
+        # the same network on the polynomial rate tables (HH_PREC_POLY)
+        net3 = hh.Network(g["V0"], W["dt"], csr=(g["row_ptr"], g["col"], g["w"]), inh=g["inh"], syn=SYN,
+                          delay_steps=DELAY, bg=BG, seed=W["seed"] + rank, precision=hh.HH_PREC_POLY,
+                          stream=stream.cuda_stream)
+        net3.set_channels(0, inp.CLASSIC_HH)
+
+        def step3():
+            with torch.cuda.stream(stream):
+                buf["counts"].zero_()
+                buf["n_spikes"].zero_()
+            net3.reset(V0_dev)
+            net3.step(STEPS_PER_SIM, rec=rec)
+
+        step3()
+        torch.cuda.synchronize()
+        f0.record(stream)
+        for _ in range(3):
+            step3()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        poly_ms = f0.elapsed_time(f1) / 3
+        poly_spikes = int(buf["counts"].sum().item())
+        net3.close()
 
     if rank == 0:
         pk, pk_kind = peaks()
@@ -413,6 +436,10 @@ def run_gpu(args):
             line["extra"]["network_persistent_cooperative"] = {
                 "ms_per_step": persistent_ms,
                 "neuron_steps_per_s": float(W["n"]) * STEPS_PER_SIM / (persistent_ms * 1e-3)}
+            line["extra"]["network_poly_rates"] = {
+                "ms_per_step": poly_ms, "neuron_steps_per_s": float(W["n"]) * STEPS_PER_SIM / (poly_ms * 1e-3),
+                "spikes": poly_spikes, "spikes_plain_path": spikes_total // args.steps,
+                "note": "the same workload with HH_PREC_POLY (cubic rate tables fitted at set_channels)"}
         print(json.dumps(line), flush=True)
     net.close()
     if world > 1:
@@ -514,7 +541,8 @@ def extras(dev, pk):
         return e0.elapsed_time(e1) / reps
 
     x = inp.single_neurons(1024, seed=0)
-    for name, prec in (("compensated", hh.HH_PREC_COMPENSATED), ("fast", hh.HH_PREC_FAST)):
+    for name, prec in (("compensated", hh.HH_PREC_COMPENSATED), ("fast", hh.HH_PREC_FAST),
+                       ("poly", hh.HH_PREC_POLY)):
         net = hh.Network(x["V0"], 0.01, I_const=x["I"], precision=prec)
         net.set_channels(0, inp.CLASSIC_HH)
         rec, b = hh.make_record(1024, 10_000, spike_cap=100_000)
@@ -525,17 +553,23 @@ def extras(dev, pk):
         net.close()
 
     y = inp.multi_channel_neurons(1_000_000, seed=0)
-    net = hh.Network(y["V0"], 0.025, I_const=y["I"], precision=hh.HH_PREC_FAST)
-    net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
-    net.step(10)
-    rec, b = hh.make_record(1_000_000, 20_000, spike_cap=0)
-    ms = timed(lambda: net.step(20_000, rec=rec))
-    out["multichannel_1e6_500ms"] = {"neuron_steps_per_s": 1e6 * 20_000 / (ms * 1e-3), "ms": ms,
-                                     "mean_rate_hz": float(b["counts"].sum().item()) / 1e6 / 0.5,
-                                     "sfu_roofline_frac": sfu_roofline_frac(inp.MULTI_CHANNEL,
-                                                                            1e6 * 20_000 / (ms * 1e-3),
-                                                                            pk["sfu"])}
-    net.close()
+    for name, prec in (("multichannel_1e6_500ms", hh.HH_PREC_FAST),
+                       ("multichannel_1e6_500ms_poly", hh.HH_PREC_POLY)):
+        net = hh.Network(y["V0"], 0.025, I_const=y["I"], precision=prec)
+        net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
+        net.step(10)
+        rec, b = hh.make_record(1_000_000, 20_000, spike_cap=0)
+        ms = timed(lambda: net.step(20_000, rec=rec))
+        out[name] = {"neuron_steps_per_s": 1e6 * 20_000 / (ms * 1e-3), "ms": ms,
+                     "mean_rate_hz": float(b["counts"].sum().item()) / 1e6 / 0.5,
+                     "sfu_roofline_frac": sfu_roofline_frac(inp.MULTI_CHANNEL, 1e6 * 20_000 / (ms * 1e-3),
+                                                            pk["sfu"])}
+        if prec == hh.HH_PREC_POLY:
+            info = net.readout(hh.HH_READ_POLY)
+            out[name]["poly_interval_mV"], out[name]["poly_rel_err"] = float(info[0]), float(info[2])
+            out[name]["note"] = ("sfu_roofline_frac: the plain path's SFU work per neuron-step over this "
+                                 "path's time (the tables replace most of that work)")
+        net.close()
     del y
 
     d = inp.recurrent_layer(B=128, n_in=700, n_hid=1024, n_out=20, T=250, seed=0)

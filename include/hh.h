@@ -133,8 +133,27 @@ typedef struct {
  *   HH_PREC_COMPENSATED as ACCURATE, on a two-float (hi + lo) state: each
  *                       increment is added by an error-free two-sum, so the
  *                       state keeps the low bits of small increments over
- *                       many steps.                                        */
-enum { HH_PREC_FAST = 0, HH_PREC_ACCURATE = 1, HH_PREC_COMPENSATED = 2 };
+ *                       many steps;
+ *   HH_PREC_POLY        polynomial approximation of the rates (Results,
+ *                       "BrainFuse": the operators' polynomial
+ *                       approximation): hh_set_channels fits, per model and
+ *                       gate, p_inf(V) and 1 - e^{-dt/tau(V)} by cubics on
+ *                       uniform intervals of [HH_POLY_V_LO, HH_POLY_V_HI)
+ *                       mV (Chebyshev interpolation in FP64), halving the
+ *                       interval from 1 mV down to 1/8 mV until every
+ *                       function's relative error, measured at 64 points
+ *                       per interval, is at most HH_POLY_REL_ERR; each step
+ *                       then takes one table row per gate instead of the
+ *                       rate functions, their division and the exponential
+ *                       (HH_READ_POLY gives the interval and the error
+ *                       reached).  A warp with any lane outside the range
+ *                       takes the FAST arithmetic for that step; V and Ca
+ *                       are as in FAST.  Needs HH_KERNELS_SPECIALISED or
+ *                       HH_KERNELS_PERSISTENT.                             */
+enum { HH_PREC_FAST = 0, HH_PREC_ACCURATE = 1, HH_PREC_COMPENSATED = 2, HH_PREC_POLY = 3 };
+#define HH_POLY_V_LO (-120.0f)
+#define HH_POLY_V_HI 80.0f
+#define HH_POLY_REL_ERR 5e-7f
 enum { HH_V_EXP_EULER = 0, HH_V_FWD_EULER = 1 };
 
 /* Neuron kernels:
@@ -500,7 +519,9 @@ enum {
     HH_READ_TIME = 5,    /* int64: steps advanced since creation / reset    */
     HH_READ_N_OUT = 6,   /* int64 [N+1] out-CSR row pointer (rows = pre)    */
     HH_READ_PROFILE = 7, /* hh_kernel_time [HH_KERNEL_COUNT] since hh_profile(net, 1) */
-    HH_READ_SURROGATE = 8 /* uint64 [2]: neuron-windows taken from the surrogate, declined */
+    HH_READ_SURROGATE = 8, /* uint64 [2]: neuron-windows taken from the surrogate, declined */
+    HH_READ_POLY = 9       /* float [HH_MAX_MODELS][3]: interval (mV), first V (mV) and largest
+                              relative error of the rate tables per model (zeros: none) */
 };
 enum { HH_STATUS_SPIKE_OVERFLOW = 1, HH_STATUS_NONFINITE = 2, HH_STATUS_BARRIER_TIMEOUT = 4 };
 
@@ -608,6 +629,22 @@ const char* hh_last_error(void);
  * GEMM's final wait for its own TMA loads in flight always uses the
  * default, so no copy lands after its block exits.  Errors: none. */
 hh_status hh_set_wait_limits(int64_t progress_ns, int64_t mbarrier_polls);
+
+/* The rate tables HH_PREC_POLY installs for model m at time step dt_ms,
+ * computed on the host (no device work; the same fit hh_set_channels runs).
+ *   info       : host float [3]: interval (mV), first V (mV), largest relative
+ *                error measured
+ *   n_intervals: host, or NULL: intervals of the table
+ *   coeffs     : host float [n_intervals][n_gates][2][4], or NULL: per
+ *                interval j (V in [v_lo + j h, v_lo + (j + 1) h)) and gate (in
+ *                channel order), the coefficients c0..c3 of c0 + x (c1 + x (c2
+ *                + x c3)), x = (V - v_lo)/h - j, for p_inf (zeros for a
+ *                Ca-dependent gate) and for 1 - e^{-dt/tau}
+ *   n_floats   : host, or NULL: floats the table holds
+ * Errors: HH_EINVAL (invalid model or dt), HH_EOVERFLOW (cap_floats too
+ * small; info, n_intervals and n_floats are filled). */
+hh_status hh_poly_fit(const hh_model_desc* m, double dt_ms, float* info, int32_t* n_intervals, float* coeffs,
+                      int64_t cap_floats, int64_t* n_floats);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t hh_version(void);

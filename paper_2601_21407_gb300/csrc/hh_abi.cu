@@ -62,6 +62,12 @@ struct hh_net {
 
     hh::DevModels models{};
     bool installed[HH_MAX_MODELS] = {false, false, false, false};
+    // rate tables of HH_PREC_POLY: per model its fitted rows, and all of
+    // them in one device array (model k at models.m[k].poly_base)
+    std::vector<float> poly_host[HH_MAX_MODELS];
+    float poly_info[HH_MAX_MODELS][3] = {};  // interval, first V, largest relative error
+    float4* poly = nullptr;
+    size_t poly_cap = 0, poly_rows = 0;
     int32_t max_model_used = 0;
 
     // state and per-neuron inputs (device)
@@ -158,6 +164,19 @@ struct hh_net {
         if (e == cudaSuccess)
             allocs.push_back(*p);
         return e;
+    }
+
+    // free one tracked allocation now (nullptr: nothing)
+    void free_tracked(void* p)
+    {
+        if (!p)
+            return;
+        for (size_t k = 0; k < allocs.size(); ++k)
+            if (allocs[k] == p) {
+                cudaFree(p);
+                allocs.erase(allocs.begin() + (long)k);
+                return;
+            }
     }
 
     void release()
@@ -270,6 +289,8 @@ struct hh_net {
         p.Ca = Ca;
         p.gE = gE;
         p.gI = gI;
+        p.poly = poly;
+        p.poly_rows = (int32_t)poly_rows;
         p.model_id = model_id;
         p.gbar = gbar;
         p.I_const = I_const;
@@ -388,6 +409,144 @@ hh::DevFn prep_fn(const hh_fn& f)
     d.n2 = (float)(ak / 12.0);
     d.n4 = (float)(-ak / 720.0);
     return d;
+}
+
+// ---------------------------------------------------------------------------
+// Polynomial rate tables (HH_PREC_POLY)
+// ---------------------------------------------------------------------------
+
+// r(V) = c + form(V) in FP64 (the closed forms of hh_fn; the linoid's
+// removable point by its series)
+double host_rate(const hh_fn& f, double V)
+{
+    const double a = f.a, vh = f.vh, k = f.k != 0.0f ? (double)f.k : 1.0;
+    double r;
+    switch (f.form) {
+    case HH_FN_CONST: r = a; break;
+    case HH_FN_EXP: r = a * std::exp((V - vh) / k); break;
+    case HH_FN_SIGMOID: r = a / (1.0 + std::exp((V - vh) / k)); break;
+    case HH_FN_LINOID: {
+        const double y = (V - vh) / k;
+        r = std::fabs(y) < 1e-8 ? a * k * (1.0 + 0.5 * y) : a * (V - vh) / (-std::expm1(-y));
+        break;
+    }
+    default: {
+        const double k2 = f.k2 != 0.0f ? (double)f.k2 : 1.0;
+        r = a / (std::exp((V - vh) / k) + std::exp((V - (double)f.vh2) / k2));
+        break;
+    }
+    }
+    return r + (double)f.c;
+}
+
+// The two tabulated functions of a gate at V: p_inf (0 for a Ca-dependent
+// gate, whose p_inf depends on Ca) and 1 - e^{-dt/tau}.
+void host_gate(const hh_gate& g, double V, double dt, double* inf, double* E)
+{
+    double z;
+    if (g.kind == HH_GATE_AB) {
+        const double al = host_rate(g.f1, V), be = host_rate(g.f2, V);
+        *inf = al / (al + be);
+        z = dt * (al + be);
+    } else {
+        *inf = g.kind == HH_GATE_INFTAU ? host_rate(g.f1, V) : 0.0;
+        z = dt / host_rate(g.f2, V);
+    }
+    *E = -std::expm1(-z);
+}
+
+struct PolyTable {
+    float h = 0.0f, v_lo = 0.0f, err = 0.0f;
+    int32_t n = 0, n_gates = 0;
+    std::vector<float> c;  // [n][n_gates][2][4]
+};
+
+// Cubic interpolation at the four Chebyshev points of [0, 1) for every
+// interval of h mV and every function; the interval is halved from 1 mV to
+// 1/8 mV until the largest relative error (FP32 Horner, 64 points per
+// interval) is at most HH_POLY_REL_ERR.
+hh_status poly_fit(const hh_model_desc* m, double dt, PolyTable* out)
+{
+    std::vector<const hh_gate*> gates;
+    for (int c = 0; c < m->n_channels; ++c)
+        for (int g = 0; g < m->channels[c].n_gates; ++g)
+            gates.push_back(&m->channels[c].gates[g]);
+    const int ng = (int)gates.size();
+    // monomial coefficients of the interpolant from the values at the nodes:
+    // invert the 4 x 4 Vandermonde matrix of the nodes once
+    double t[4], Vi[4][8];
+    for (int i = 0; i < 4; ++i) {
+        t[i] = 0.5 - 0.5 * std::cos((2 * i + 1) * 3.14159265358979323846 / 8.0);
+        for (int k = 0; k < 4; ++k) {
+            Vi[i][k] = std::pow(t[i], k);
+            Vi[i][4 + k] = (i == k) ? 1.0 : 0.0;
+        }
+    }
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(Vi[r][col]) > std::fabs(Vi[piv][col]))
+                piv = r;
+        for (int k = 0; k < 8; ++k)
+            std::swap(Vi[col][k], Vi[piv][k]);
+        const double d = Vi[col][col];
+        for (int k = 0; k < 8; ++k)
+            Vi[col][k] /= d;
+        for (int r = 0; r < 4; ++r)
+            if (r != col) {
+                const double f = Vi[r][col];
+                for (int k = 0; k < 8; ++k)
+                    Vi[r][k] -= f * Vi[col][k];
+            }
+    }
+    // inverse: coefficient k = sum_i inv[k][i] f(t_i)
+    double inv[4][4];
+    for (int k = 0; k < 4; ++k)
+        for (int i = 0; i < 4; ++i)
+            inv[k][i] = Vi[k][4 + i];
+    const double lo = HH_POLY_V_LO, hi = HH_POLY_V_HI;
+    PolyTable T;
+    for (double h = 1.0; h >= 0.125; h *= 0.5) {
+        T.h = (float)h;
+        T.v_lo = (float)lo;
+        T.n = (int32_t)std::lround((hi - lo) / h);
+        T.n_gates = ng;
+        T.c.assign((size_t)T.n * ng * 8, 0.0f);
+        double worst = 0.0;
+        for (int j = 0; j < T.n; ++j) {
+            const double v0 = lo + j * h;
+            for (int q = 0; q < ng; ++q) {
+                double fv[2][4];
+                for (int i = 0; i < 4; ++i)
+                    host_gate(*gates[q], v0 + t[i] * h, dt, &fv[0][i], &fv[1][i]);
+                for (int f = 0; f < 2; ++f) {
+                    float* c = &T.c[(((size_t)j * ng + q) * 2 + f) * 4];
+                    for (int k = 0; k < 4; ++k) {
+                        double acc = 0.0;
+                        for (int i = 0; i < 4; ++i)
+                            acc += inv[k][i] * fv[f][i];
+                        c[k] = (float)acc;
+                    }
+                    if (f == 0 && gates[q]->kind == HH_GATE_CA)
+                        continue;  // not used
+                    for (int u = 0; u < 64; ++u) {
+                        const float x = ((float)u + 0.5f) / 64.0f;
+                        double ex[2];
+                        host_gate(*gates[q], v0 + (double)x * h, dt, &ex[0], &ex[1]);
+                        const float pv = std::fma(x, std::fma(x, std::fma(x, c[3], c[2]), c[1]), c[0]);
+                        const double e = std::fabs((double)pv - ex[f]) / std::max(std::fabs(ex[f]), 1e-7);
+                        if (!(e <= worst))  // NaN counts as the worst
+                            worst = std::isfinite(e) ? e : 1e30;
+                    }
+                }
+            }
+        }
+        T.err = (float)worst;
+        if (worst <= HH_POLY_REL_ERR)
+            break;
+    }
+    *out = std::move(T);
+    return HH_OK;
 }
 
 }  // namespace
@@ -709,7 +868,7 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
 int persistent_capacity(hh_net* n)
 {
     if (n->persistent_cap < 0)
-        n->persistent_cap = hh::jit_persistent_capacity(n->jit);
+        n->persistent_cap = hh::jit_persistent_capacity(n->jit, n->neuron_params());
     return n->persistent_cap;
 }
 
@@ -750,8 +909,10 @@ hh_status hh_create_network(const hh_net_desc* d, hh_net** out)
         return fail(HH_EINVAL, "v_threshold must be finite");
     if (d->v_update != HH_V_EXP_EULER && d->v_update != HH_V_FWD_EULER)
         return fail(HH_EINVAL, "unknown v_update %d", d->v_update);
-    if (d->precision < HH_PREC_FAST || d->precision > HH_PREC_COMPENSATED)
+    if (d->precision < HH_PREC_FAST || d->precision > HH_PREC_POLY)
         return fail(HH_EINVAL, "unknown precision %d", d->precision);
+    if (d->precision == HH_PREC_POLY && d->kernels == HH_KERNELS_TABLE)
+        return fail(HH_EUNSUPPORTED, "HH_PREC_POLY needs HH_KERNELS_SPECIALISED or HH_KERNELS_PERSISTENT");
     if (d->kernels != HH_KERNELS_SPECIALISED && d->kernels != HH_KERNELS_TABLE &&
         d->kernels != HH_KERNELS_PERSISTENT)
         return fail(HH_EINVAL, "unknown kernels %d", d->kernels);
@@ -787,6 +948,59 @@ hh_status hh_set_channels(hh_net* net, int32_t model_index, const hh_model_desc*
     net->jit_ready = false;
     net->models.max_gates = max_gates_installed(net);
     net->models.n = HH_MAX_MODELS;
+    if (net->precision == HH_PREC_POLY) {
+        PolyTable T;
+        if ((s = poly_fit(m, net->dt, &T)) != HH_OK)
+            return s;
+        net->poly_host[model_index] = std::move(T.c);
+        net->poly_info[model_index][0] = T.h;
+        net->poly_info[model_index][1] = T.v_lo;
+        net->poly_info[model_index][2] = T.err;
+        // every installed model's rows in one device array, each row padded
+        // to 2 n_gates + 1 coefficient vectors (an odd stride)
+        auto rows_of = [&](int k) {
+            const hh::DevModel& M = net->models.m[k];
+            const size_t n = net->poly_host[k].size() / (8 * (size_t)(M.n_gates > 0 ? M.n_gates : 1));
+            return n * (size_t)(2 * M.n_gates + 1);
+        };
+        size_t total = 0;
+        for (int k = 0; k < HH_MAX_MODELS; ++k)
+            if (net->installed[k] && !net->poly_host[k].empty())
+                total += rows_of(k);
+        if (total > net->poly_cap) {
+            net->free_tracked(net->poly);
+            net->poly = nullptr;
+            net->poly_cap = 0;
+            HH_CUDA(net->alloc(&net->poly, total));
+            net->poly_cap = total;
+        }
+        size_t off = 0;
+        for (int k = 0; k < HH_MAX_MODELS; ++k) {
+            hh::DevModel& M = net->models.m[k];
+            M.poly_n = 0;
+            if (!net->installed[k] || net->poly_host[k].empty())
+                continue;
+            const int ng = M.n_gates, stride = 2 * ng + 1;
+            const size_t n = net->poly_host[k].size() / (8 * (size_t)ng);
+            std::vector<float4> padded(n * stride, make_float4(0.f, 0.f, 0.f, 0.f));
+            for (size_t j = 0; j < n; ++j)
+                for (int v = 0; v < 2 * ng; ++v) {
+                    const float* c = &net->poly_host[k][(j * 2 * ng + v) * 4];
+                    padded[j * stride + v] = make_float4(c[0], c[1], c[2], c[3]);
+                }
+            HH_CUDA(cudaMemcpy(net->poly + off, padded.data(), padded.size() * sizeof(float4),
+                               cudaMemcpyHostToDevice));
+            M.poly_base = (int32_t)off;
+            M.poly_stride = stride;
+            M.poly_n = (int32_t)n;
+            M.poly_vlo = net->poly_info[k][1];
+            M.poly_ih = 1.0f / net->poly_info[k][0];
+            off += padded.size();
+        }
+        net->poly_rows = off;
+        if (off > (size_t)INT32_MAX)
+            return fail(HH_EINVAL, "rate tables too large");
+    }
     if (gbar || net->gbar) {
         if (!net->gbar) {
             // first per-neuron table: every other model's neurons take their defaults
@@ -1132,6 +1346,7 @@ hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap, size_t* n
             return fail(HH_ESTATE, "no surrogate trained");
         need = 2 * sizeof(uint64_t);
         break;
+    case HH_READ_POLY: need = sizeof(net->poly_info); break;
     default: return fail(HH_EINVAL, "unknown readout %d", what);
     }
     if (!dst)
@@ -1166,6 +1381,7 @@ hh_status hh_readout(hh_net* net, int32_t what, void* dst, size_t cap, size_t* n
         HH_CUDA(net->harvest());
         HH_CUDA(cudaMemcpy(dst, net->ktime, need, cudaMemcpyDefault));
         break;
+    case HH_READ_POLY: HH_CUDA(cudaMemcpy(dst, net->poly_info, need, cudaMemcpyDefault)); break;
     }
     if (n_bytes)
         *n_bytes = need;
@@ -1205,7 +1421,7 @@ hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surroga
         return fail(HH_EUNSUPPORTED, "the surrogate supports a single model (model_id must be NULL)");
     if (net->kernels != HH_KERNELS_SPECIALISED)
         return fail(HH_EUNSUPPORTED, "the surrogate needs HH_KERNELS_SPECIALISED");
-    if (net->precision == HH_PREC_COMPENSATED)
+    if (net->precision != HH_PREC_FAST && net->precision != HH_PREC_ACCURATE)
         return fail(HH_EUNSUPPORTED, "the surrogate supports HH_PREC_FAST and HH_PREC_ACCURATE");
     if (!net->installed[0])
         return fail(HH_ESTATE, "model 0 is not installed");
@@ -1262,6 +1478,35 @@ void hh_destroy(hh_net* net)
 const char* hh_last_error(void) { return g_err.c_str(); }
 
 int32_t hh_version(void) { return 0x000100; }
+
+hh_status hh_poly_fit(const hh_model_desc* m, double dt_ms, float* info, int32_t* n_intervals, float* coeffs,
+                      int64_t cap_floats, int64_t* n_floats)
+{
+    if (!m || !info)
+        return fail(HH_EINVAL, "model and info must not be NULL");
+    if (!(dt_ms > 0.0))
+        return fail(HH_EINVAL, "dt_ms must be > 0");
+    hh::DevModel dm{};
+    hh_status s = prep_model(m, dt_ms, &dm);
+    if (s != HH_OK)
+        return s;
+    PolyTable T;
+    if ((s = poly_fit(m, dt_ms, &T)) != HH_OK)
+        return s;
+    info[0] = T.h;
+    info[1] = T.v_lo;
+    info[2] = T.err;
+    if (n_intervals)
+        *n_intervals = T.n;
+    if (n_floats)
+        *n_floats = (int64_t)T.c.size();
+    if (coeffs) {
+        if (cap_floats < (int64_t)T.c.size())
+            return fail(HH_EOVERFLOW, "the table needs %zu floats", T.c.size());
+        std::memcpy(coeffs, T.c.data(), T.c.size() * sizeof(float));
+    }
+    return HH_OK;
+}
 
 hh_status hh_set_wait_limits(int64_t progress_ns, int64_t mbarrier_polls)
 {

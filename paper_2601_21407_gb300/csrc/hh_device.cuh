@@ -58,6 +58,14 @@ struct DevGate {
 struct DevModel {
     float C_m, inv_C;
     int32_t n_ch, n_gates, ca_ch;
+    // piecewise-cubic rate tables (HH_PREC_POLY): poly_n intervals of 1/poly_ih
+    // mV from poly_vlo; interval j of gate q holds p_inf and 1 - e^{-dt/tau}
+    // as float4 coefficients (c0, c1, c2, c3) of c0 + x (c1 + x (c2 + x c3)),
+    // x in [0, 1), at NeuronParams::poly[poly_base + j poly_stride + 2 q + f].
+    // poly_stride = 2 n_gates + 1 is odd, so that the rows of the lanes of a
+    // warp start in different shared-memory bank groups.
+    int32_t poly_n, poly_base, poly_stride;
+    float poly_vlo, poly_ih;
     float ca_tau, ca_k, ca_rest, ca_decay;  // ca_decay = exp(-dt/ca_tau)
     float E[kMaxChannels];
     float gbar[kMaxChannels];
@@ -92,6 +100,8 @@ struct NeuronParams {
     float* Ca;
     float* gE;       // nS
     float* gI;       // nS
+    const float4* poly;    // rate tables of the installed models (HH_PREC_POLY) or nullptr
+    int32_t poly_rows;     // float4 rows of poly (staged in shared memory when at most kPolySmemRows)
     const uint8_t* model_id;
     const float* gbar;     // [kMaxChannels][N] or nullptr
     const float* I_const;  // [N] or nullptr
@@ -330,6 +340,7 @@ __device__ __forceinline__ float fixed_to_nS(long long e)
 
 template <int MAXG, int PREC>
 struct State {
+    const float4* poly;     // rate tables (HH_PREC_POLY), in shared or global memory
     float V, Vlo, Ca;
     float p[MAXG];
     float plo[MAXG];
@@ -361,13 +372,45 @@ __device__ __forceinline__ void load_conductances(const DevModel& M, const float
     }
 }
 
+// SFU arithmetic: the FAST mode, and the POLY mode outside its tables.
+template <int PREC>
+__host__ __device__ constexpr bool sfu_math()
+{
+    return PREC == HH_PREC_FAST || PREC == HH_PREC_POLY;
+}
+
 // Gate part of one exponential-Euler step: the gates q with q % 2 == ROLE
 // (ROLE < 0: every gate) from the rates at V_t = s.V.
 template <int MAXG, int PREC, int ROLE>
 __device__ __forceinline__ void neuron_gates(const DevModel& M, float dt, State<MAXG, PREC>& s)
 {
-    constexpr bool FAST = PREC == HH_PREC_FAST;
+    constexpr bool FAST = sfu_math<PREC>();
     const float V = s.V;
+    if (PREC == HH_PREC_POLY && M.poly_n > 0) {
+        // polynomial approximation of the rates (Results, "BrainFuse": the
+        // operators' polynomial approximation): p_inf and 1 - e^{-dt/tau} of
+        // every gate from the cubic of V's interval, when every active lane
+        // of the warp lies inside the tables (else the SFU path below)
+        const float u = (V - M.poly_vlo) * M.poly_ih;
+        const bool in = u >= 0.0f && u < (float)M.poly_n;  // false for NaN
+        if (__all_sync(__activemask(), in)) {
+            const float jf = floorf(u);
+            const float x = u - jf;
+            const float4* b = s.poly + M.poly_base + (int)jf * M.poly_stride;
+#pragma unroll
+            for (int q = 0; q < MAXG; ++q) {
+                if (q < M.n_gates && (ROLE < 0 || (q & 1) == ROLE)) {
+                    const float4 ci = b[2 * q], ce = b[2 * q + 1];
+                    float inf = fmaf(x, fmaf(x, fmaf(x, ci.w, ci.z), ci.y), ci.x);
+                    const float E = fmaf(x, fmaf(x, fmaf(x, ce.w, ce.z), ce.y), ce.x);
+                    if (M.g[q].kind == HH_GATE_CA)
+                        inf = Mth<true>::div(s.Ca, s.Ca + M.g[q].f1.a);
+                    s.p[q] = fmaf(inf - s.p[q], E, s.p[q]);
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < MAXG; ++q) {
         if (q < M.n_gates && (ROLE < 0 || (q & 1) == ROLE)) {
@@ -389,7 +432,7 @@ template <int MAXG, int PREC>
 __device__ __forceinline__ void neuron_vstep(const DevModel& M, float dt, int v_update, float I, float gsE,
                                              float EE, float gsI, float EI, State<MAXG, PREC>& s)
 {
-    constexpr bool FAST = PREC == HH_PREC_FAST;
+    constexpr bool FAST = sfu_math<PREC>();
     using Mt = Mth<FAST>;
     const float V = s.V;
     float G = gsE + gsI + s.gconst;
@@ -442,6 +485,31 @@ __device__ __forceinline__ void neuron_step(const DevModel& M, float dt, int v_u
 {
     neuron_gates<MAXG, PREC, -1>(M, dt, s);
     neuron_vstep<MAXG, PREC>(M, dt, v_update, I, gsE, EE, gsI, EI, s);
+}
+
+// Rate tables of HH_PREC_POLY: a launch whose table has at most
+// kPolySmemRows rows gets them as dynamic shared memory (poly_smem_bytes),
+// copied by the block at its start; larger tables are read from global
+// memory.  Every thread of the block calls stage_poly before any other
+// barrier.
+constexpr int kPolySmemRows = 4096;  // 64 KB
+__host__ __device__ constexpr size_t poly_smem_bytes(int rows)
+{
+    return rows > 0 && rows <= kPolySmemRows ? (size_t)rows * 16 : 0;
+}
+extern __shared__ float4 hh_poly_smem[];
+
+template <int PREC>
+__device__ __forceinline__ const float4* stage_poly(const NeuronParams& P)
+{
+    if (PREC != HH_PREC_POLY || P.poly_rows <= 0)
+        return nullptr;
+    if (P.poly_rows > kPolySmemRows)
+        return P.poly;
+    for (int k = threadIdx.x; k < P.poly_rows; k += blockDim.x)
+        hh_poly_smem[k] = __ldg(P.poly + k);
+    __syncthreads();
+    return hh_poly_smem;
 }
 
 template <int MAXG, int PREC>
@@ -738,11 +806,13 @@ __device__ __forceinline__ void independent_body(const Dyn& dyn, const NeuronPar
                                                  int32_t n_steps, const float* __restrict__ I_steps,
                                                  const RecordParams& R)
 {
+    const float4* tab = stage_poly<PREC>(P);
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = gi < P.N;
     const int64_t i = valid ? gi : 0;
     const int mid = P.model_id ? P.model_id[i] : 0;
     State<MAXG, PREC> s;
+    s.poly = tab;
     load_state(P, i, s);
     dyn.template load<MAXG, PREC>(mid, P, i, s);
     const float Ic = P.I_const ? P.I_const[i] : 0.0f;
@@ -786,6 +856,7 @@ __device__ __forceinline__ void indexed_body(const Dyn& dyn, const NeuronParams&
     const int64_t i = valid ? list[gi] : list[0];
     const int mid = P.model_id ? P.model_id[i] : 0;
     State<MAXG, PREC> s;
+    s.poly = P.poly;  // (the surrogate's networks do not use HH_PREC_POLY)
     load_state(P, i, s);
     dyn.template load<MAXG, PREC>(mid, P, i, s);
     const float Ic = P.I_const ? P.I_const[i] : 0.0f;
@@ -980,6 +1051,7 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
                                             const RecordParams& R, const SpikeList& L, int32_t parity,
                                             int32_t early)
 {
+    const float4* tab = stage_poly<PREC>(P);  // constant tables: before the programmatic wait
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = gi < P.N;
     const int64_t i = valid ? gi : 0;
@@ -998,6 +1070,7 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         L.counter[parity + 1 == kListSlots ? 0 : parity + 1] = 0;  // next window's slot (its reader has finished)
     const int mid = P.model_id ? P.model_id[i] : 0;
     State<MAXG, PREC> s;
+    s.poly = tab;
     load_state(P, i, s);
     dyn.template load<MAXG, PREC>(mid, P, i, s);
     float gE = P.gE[i], gI = P.gI[i];
@@ -1140,6 +1213,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
                                                 const float* __restrict__ I_steps, const RecordParams& R,
                                                 const SpikeList& L, const PhaseCounters& pc)
 {
+    const float4* tab = stage_poly<PREC>(P);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t n_win = (n_steps + W - 1) / W;
     const unsigned long long n_blocks = gridDim.x;
@@ -1183,6 +1257,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
         const int64_t i = valid ? gi : 0;
         const int mid = P.model_id ? P.model_id[i] : 0;
         State<MAXG, PREC> s;
+        s.poly = tab;
         load_state(P, i, s);
         dyn.template load<MAXG, PREC>(mid, P, i, s);
         float gE = P.gE[i], gI = P.gI[i];

@@ -101,7 +101,7 @@ struct JitKernels {
     cudaKernel_t indexed = nullptr;
     cudaKernel_t persistent = nullptr;
 };
-int jit_persistent_capacity(const JitKernels& K);
+int jit_persistent_capacity(const JitKernels& K, const NeuronParams& P);
 cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, const RouteParams& RP, int64_t t0,
                                   int32_t n_steps, int32_t W, int64_t w_index0, const float* I_steps,
                                   const RecordParams& R, const SpikeList& L, const PhaseCounters& pc,

@@ -67,6 +67,11 @@ std::string model_function(const hh::DevModel& m, int idx)
     I("n_ch", m.n_ch);
     I("n_gates", m.n_gates);
     I("ca_ch", m.ca_ch);
+    I("poly_n", m.poly_n);
+    I("poly_base", m.poly_base);
+    I("poly_stride", m.poly_stride);
+    F("poly_vlo", m.poly_vlo);
+    F("poly_ih", m.poly_ih);
     F("ca_tau", m.ca_tau);
     F("ca_k", m.ca_k);
     F("ca_rest", m.ca_rest);
@@ -105,7 +110,8 @@ std::string abi_constants()
         {"HH_FN_LINOID", HH_FN_LINOID}, {"HH_FN_BELL", HH_FN_BELL}, {"HH_GATE_AB", HH_GATE_AB},
         {"HH_GATE_INFTAU", HH_GATE_INFTAU}, {"HH_GATE_CA", HH_GATE_CA},
         {"HH_PREC_FAST", HH_PREC_FAST}, {"HH_PREC_ACCURATE", HH_PREC_ACCURATE},
-        {"HH_PREC_COMPENSATED", HH_PREC_COMPENSATED}, {"HH_V_EXP_EULER", HH_V_EXP_EULER},
+        {"HH_PREC_COMPENSATED", HH_PREC_COMPENSATED}, {"HH_PREC_POLY", HH_PREC_POLY},
+        {"HH_V_EXP_EULER", HH_V_EXP_EULER},
         {"HH_V_FWD_EULER", HH_V_FWD_EULER}, {"HH_STATUS_SPIKE_OVERFLOW", HH_STATUS_SPIKE_OVERFLOW},
         {"HH_STATUS_NONFINITE", HH_STATUS_NONFINITE}, {"HH_STATUS_BARRIER_TIMEOUT", HH_STATUS_BARRIER_TIMEOUT}};
     for (const auto& x : c) {
@@ -360,6 +366,17 @@ cudaError_t jit_launch_layer(cudaKernel_t k, const LayerParams& L, int arg, int6
     return cudaLaunchKernel((const void*)k, dim3((unsigned)((n + 127) / 128)), dim3(128), args, smem, st);
 }
 
+// Dynamic shared memory of a neuron launch: the staged rate tables of
+// HH_PREC_POLY (poly_smem_bytes), with the kernel's limit raised when they
+// exceed the default 48 KB.
+cudaError_t poly_smem(cudaKernel_t k, const NeuronParams& P, size_t* bytes)
+{
+    *bytes = poly_smem_bytes(P.poly_rows);
+    if (*bytes > 48 * 1024)
+        return cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+    return cudaSuccess;
+}
+
 cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, int64_t t0,
                                    int32_t n_steps, const float* I_steps, const RecordParams& R,
                                    cudaStream_t st)
@@ -371,7 +388,11 @@ cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, i
     NeuronParams p = P;
     RecordParams r = R;
     void* args[] = {&p, &t, &n, &I_steps, &r};
-    return cudaLaunchKernel((const void*)K.independent, grid, block, args, 0, st);
+    size_t smem = 0;
+    cudaError_t e = poly_smem(K.independent, P, &smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaLaunchKernel((const void*)K.independent, grid, block, args, smem, st);
 }
 
 cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_t t0, int32_t W,
@@ -392,6 +413,9 @@ cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.stream = st;
+    cudaError_t e = poly_smem(K.window, P, &cfg.dynamicSmemBytes);
+    if (e != cudaSuccess)
+        return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -402,12 +426,13 @@ cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_
 
 // Blocks of the persistent kernel (kPersistNeurons neurons each) that can
 // be resident at once (0 if the query fails).
-int jit_persistent_capacity(const JitKernels& K)
+int jit_persistent_capacity(const JitKernels& K, const NeuronParams& P)
 {
     int per_sm = 0, dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
+    size_t smem = 0;
+    if (poly_smem(K.persistent, P, &smem) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)K.persistent, kPersistThreads, 0) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)K.persistent, kPersistThreads, smem) !=
             cudaSuccess)
         return 0;
     return per_sm * sms;
@@ -430,6 +455,9 @@ cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, co
     cfg.gridDim = dim3((unsigned)((P.N + kPersistNeurons - 1) / kPersistNeurons));
     cfg.blockDim = dim3(kPersistThreads);
     cfg.stream = st;
+    cudaError_t e = poly_smem(K.persistent, P, &cfg.dynamicSmemBytes);
+    if (e != cudaSuccess)
+        return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;

@@ -235,6 +235,7 @@ template <int MAXG, int PREC>
 __device__ __forceinline__ void layer_load(const DevModel& M, const LayerParams& L, const float* V, const float* P,
                                            int64_t i, State<MAXG, PREC>& s)
 {
+    s.poly = nullptr;
     s.V = V[i];
     s.Vlo = 0.0f;
     s.Ca = 0.0f;

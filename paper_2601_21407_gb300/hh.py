@@ -25,11 +25,12 @@ HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA, HH_ETIMEOUT, HH_ESTATE, HH_EUNSUPPORTED, 
 HH_FN = {"const": 0, "exp": 1, "sigmoid": 2, "linoid": 3, "bell": 4}
 HH_GATE = {"ab": 0, "inftau": 1, "ca": 2}
 HH_MAX_CHANNELS, HH_MAX_GATES_PER_CHANNEL, HH_MAX_GATES, HH_MAX_MODELS = 8, 3, 8, 4
-HH_PREC_FAST, HH_PREC_ACCURATE, HH_PREC_COMPENSATED = 0, 1, 2
+HH_PREC_FAST, HH_PREC_ACCURATE, HH_PREC_COMPENSATED, HH_PREC_POLY = 0, 1, 2, 3
+HH_POLY_V_LO, HH_POLY_V_HI, HH_POLY_REL_ERR = -120.0, 80.0, 5e-7
 HH_V_EXP_EULER, HH_V_FWD_EULER = 0, 1
 HH_KERNELS_SPECIALISED, HH_KERNELS_TABLE, HH_KERNELS_PERSISTENT = 0, 1, 2
 (HH_READ_V, HH_READ_GATES, HH_READ_CA, HH_READ_G_SYN, HH_READ_STATUS, HH_READ_TIME,
- HH_READ_N_OUT, HH_READ_PROFILE, HH_READ_SURROGATE) = range(9)
+ HH_READ_N_OUT, HH_READ_PROFILE, HH_READ_SURROGATE, HH_READ_POLY) = range(10)
 HH_KERNEL_NEURON, HH_KERNEL_ROUTE, HH_KERNEL_COUNT = 0, 1, 2
 HH_STATUS_SPIKE_OVERFLOW, HH_STATUS_NONFINITE, HH_STATUS_BARRIER_TIMEOUT = 1, 2, 4
 
@@ -134,7 +135,8 @@ EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_
            "hh_readout", "hh_profile", "hh_step_neurons_noalloc", "hh_gemm_bf16", "hh_destroy",
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
            "hh_layer_forward", "hh_backward", "hh_backward_from", "hh_layer_readout", "hh_layer_destroy",
-           "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks", "hh_set_wait_limits"]
+           "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks", "hh_set_wait_limits",
+           "hh_poly_fit"]
 
 
 def lib_path() -> str:
@@ -198,6 +200,8 @@ def lib():
             L.hh_measure_peaks.argtypes = [P(hh_peaks), vp]
             L.hh_set_wait_limits.restype = C.c_int
             L.hh_set_wait_limits.argtypes = [C.c_int64, C.c_int64]
+            L.hh_poly_fit.restype = C.c_int
+            L.hh_poly_fit.argtypes = [P(hh_model_desc), C.c_double, vp, vp, vp, C.c_int64, vp]
             _lib = L
     return _lib
 
@@ -261,6 +265,22 @@ def hh_gemm_bf16(A, Bt, C, M, N, K, splits=1, status=None, stream=None):
 def hh_set_wait_limits(progress_ns: int = -1, mbarrier_polls: int = -1):
     """Bounds of the device-side waits for later launches (-1 = default)."""
     _check(lib().hh_set_wait_limits(int(progress_ns), int(mbarrier_polls)))
+
+
+def hh_poly_fit(model: dict, dt: float):
+    """The HH_PREC_POLY rate tables of a model (host computation): returns
+    (interval mV, first V mV, largest relative error, coefficients
+    [n_intervals][n_gates][2][4] float32)."""
+    info = np.zeros(3, dtype=np.float32)
+    n = C.c_int32()
+    nf = C.c_int64()
+    md = model_desc(model)
+    _check(lib().hh_poly_fit(C.byref(md), dt, info.ctypes.data, C.addressof(n), None, 0, C.addressof(nf)))
+    c = np.zeros(nf.value, dtype=np.float32)
+    _check(lib().hh_poly_fit(C.byref(md), dt, info.ctypes.data, C.addressof(n), c.ctypes.data, c.size,
+                             C.addressof(nf)))
+    n_gates = sum(len(ch["gates"]) for ch in model["channels"])
+    return float(info[0]), float(info[1]), float(info[2]), c.reshape(n.value, n_gates, 2, 4)
 
 
 def hh_destroy(net: int):
@@ -402,7 +422,7 @@ class Network:
         sizes = {HH_READ_V: (self.N, np.float32), HH_READ_GATES: (HH_MAX_GATES * self.N, np.float32),
                  HH_READ_CA: (self.N, np.float32), HH_READ_G_SYN: (2 * self.N, np.float32),
                  HH_READ_STATUS: (1, np.int32), HH_READ_TIME: (1, np.int64),
-                 HH_READ_N_OUT: (self.N + 1, np.int64)}
+                 HH_READ_N_OUT: (self.N + 1, np.int64), HH_READ_POLY: (3 * HH_MAX_MODELS, np.float32)}
         n, dt = sizes[what]
         out = np.zeros(n, dtype=dt)
         hh_readout(self.handle, what, out.ctypes.data, out.nbytes)

@@ -142,7 +142,9 @@ def test_background_counts_in_network_bit_exact(kernels):
                                           (hh.HH_PREC_ACCURATE, hh.HH_KERNELS_SPECIALISED),
                                           (hh.HH_PREC_COMPENSATED, hh.HH_KERNELS_SPECIALISED),
                                           (hh.HH_PREC_FAST, hh.HH_KERNELS_PERSISTENT),
-                                          (hh.HH_PREC_FAST, hh.HH_KERNELS_TABLE)])
+                                          (hh.HH_PREC_FAST, hh.HH_KERNELS_TABLE),
+                                          (hh.HH_PREC_POLY, hh.HH_KERNELS_SPECIALISED),
+                                          (hh.HH_PREC_POLY, hh.HH_KERNELS_PERSISTENT)])
 def test_closed_loop_small_network(prec, kernels):
     """1,000 neurons, in-degree 100, background, 200 ms closed loop: every
     neuron's spike count within +-1 of the oracle, and the V traces agree to
