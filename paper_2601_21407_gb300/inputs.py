@@ -211,6 +211,39 @@ def random_in_csr_fast(n, k_in, seed, mu=-1.0, sigma=0.5):
     return row_ptr, cols.reshape(-1), w
 
 
+def random_in_csr_vec(n, k_in, seed, mu=-1.0, sigma=0.5):
+    """Same distribution as random_in_csr (k_in distinct non-self sources per
+    row, sorted), fully vectorised: per block of rows, k_in + extra
+    candidates are drawn, sorted and de-duplicated, each distinct candidate
+    gets a uniform random key and the k_in smallest keys are kept (a uniform
+    subset); rows with fewer than k_in distinct candidates are drawn again.
+    For sparse rows (k_in well below n); draws its own random stream."""
+    rng = np.random.default_rng(seed)
+    k_in = int(k_in)
+    cols = np.empty((n, k_in), dtype=np.int32)
+    extra = max(8, int(k_in * k_in / max(n - 1, 1) * 3) + 8)
+    block = max(1, min(n, (1 << 22) // (k_in + extra)))
+    for r0 in range(0, n, block):
+        rows = np.arange(r0, min(n, r0 + block))
+        while rows.size:
+            cand = rng.integers(0, n - 1, size=(rows.size, k_in + extra), dtype=np.int64)
+            cand += cand >= rows[:, None]
+            cand.sort(axis=1)
+            dup = np.zeros(cand.shape, dtype=bool)
+            dup[:, 1:] = cand[:, 1:] == cand[:, :-1]
+            ok = (~dup).sum(axis=1) >= k_in
+            keys = rng.random(cand.shape)
+            keys[dup] = 2.0
+            sel = np.argpartition(keys, k_in - 1, axis=1)[:, :k_in]
+            pick = np.take_along_axis(cand, sel, axis=1)
+            pick.sort(axis=1)
+            cols[rows[ok]] = pick[ok]
+            rows = rows[~ok]
+    w = rng.lognormal(mu, sigma, n * k_in).astype(np.float32)
+    row_ptr = np.arange(0, (n + 1) * k_in, k_in, dtype=np.int64)
+    return row_ptr, cols.reshape(-1), w
+
+
 def network(n=38_000, k_in=2_632, exc_frac=0.8, seed=0, mu=-1.0, sigma=0.5,
             fast=None):
     """Sparse conductance-based HH network (in-CSR by postsynaptic neuron).
@@ -282,15 +315,39 @@ def to_bf16_exact(a) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32)
 
 
+def _batched_net(task):
+    """Worker of batched_networks: one network's in-CSR (columns shifted to
+    the concatenated index) written into the shared output arrays."""
+    from multiprocessing import shared_memory
+    n, ki, seed, mu, sigma, off, nnz0, names = task
+    gen = random_in_csr_vec if n * ki > 2_000_000 else random_in_csr
+    _, c, w = gen(n, ki, seed, mu, sigma)
+    if names is None:
+        return c + off, w
+    sc, sw = shared_memory.SharedMemory(name=names[0]), shared_memory.SharedMemory(name=names[1])
+    try:
+        np.ndarray((c.size,), np.int32, sc.buf, offset=nnz0 * 4)[:] = c + off
+        np.ndarray((w.size,), np.float32, sw.buf, offset=nnz0 * 4)[:] = w
+    finally:
+        sc.close()
+        sw.close()
+    return None
+
+
 def batched_networks(n_nets=64, n_min=1_000, n_max=50_000, k_min=100, k_max=1_000,
-                     seed=0, exc_frac=0.8, mu=-1.0, sigma=0.5):
+                     seed=0, exc_frac=0.8, mu=-1.0, sigma=0.5, workers=1):
     """Many independent networks concatenated block-diagonally.
 
     Sizes ~ LogUniform(n_min, n_max), in-degree ~ U{k_min..k_max} (clipped to
     n-1), half of the networks use the classic HH model and half the
     multi-channel model (model id per neuron).  Returns a single in-CSR over the
-    concatenated neuron index, net offsets and per-neuron model ids.
+    concatenated neuron index, net offsets and per-neuron model ids.  The
+    networks' graphs are drawn from per-network seeds, so `workers` > 1
+    (processes started with spawn, writing into shared memory) gives the
+    same arrays as one process.
     """
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_nets)).astype(np.int64)
     kin = rng.integers(k_min, k_max + 1, n_nets)
@@ -298,23 +355,41 @@ def batched_networks(n_nets=64, n_min=1_000, n_max=50_000, k_min=100, k_max=1_00
     model_of_net = rng.integers(0, 2, n_nets).astype(np.uint8)
     offsets = np.zeros(n_nets + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(sizes)
-    rows, cols, ws = [np.zeros(1, np.int64)], [], []
+    seeds = [int(rng.integers(0, 2**31)) for _ in range(n_nets)]
+    nnz = sizes * kin
+    nnz0 = np.zeros(n_nets + 1, dtype=np.int64)
+    nnz0[1:] = np.cumsum(nnz)
+    total = int(nnz0[-1])
     inh = np.zeros(int(offsets[-1]), np.uint8)
     model_id = np.zeros(int(offsets[-1]), np.uint8)
-    nnz = 0
     for k in range(n_nets):
-        n, ki = int(sizes[k]), int(kin[k])
-        gen = random_in_csr_fast if n * ki > 2_000_000 else random_in_csr
-        rp, c, w = gen(n, ki, int(rng.integers(0, 2**31)), mu, sigma)
-        rows.append(rp[1:] + nnz)
-        cols.append(c + int(offsets[k]))
-        ws.append(w)
-        nnz += c.size
-        n_exc = int(round(exc_frac * n))
+        n_exc = int(round(exc_frac * int(sizes[k])))
         inh[offsets[k] + n_exc: offsets[k + 1]] = 1
         model_id[offsets[k]: offsets[k + 1]] = model_of_net[k]
+    row_ptr = np.zeros(int(offsets[-1]) + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.repeat(kin, sizes))
+    if workers > 1:
+        sc = shared_memory.SharedMemory(create=True, size=max(4, total * 4))
+        sw = shared_memory.SharedMemory(create=True, size=max(4, total * 4))
+        try:
+            tasks = [(int(sizes[k]), int(kin[k]), seeds[k], mu, sigma, int(offsets[k]), int(nnz0[k]),
+                      (sc.name, sw.name)) for k in range(n_nets)]
+            order = sorted(range(n_nets), key=lambda k: -int(nnz[k]))  # largest first
+            with mp.get_context("spawn").Pool(workers) as pool:
+                pool.map(_batched_net, [tasks[k] for k in order], chunksize=1)
+            col = np.ndarray((total,), np.int32, sc.buf).copy()
+            w = np.ndarray((total,), np.float32, sw.buf).copy()
+        finally:
+            sc.close()
+            sc.unlink()
+            sw.close()
+            sw.unlink()
+    else:
+        parts = [_batched_net((int(sizes[k]), int(kin[k]), seeds[k], mu, sigma, int(offsets[k]), 0, None))
+                 for k in range(n_nets)]
+        col = np.concatenate([p[0] for p in parts]).astype(np.int32)
+        w = np.concatenate([p[1] for p in parts]).astype(np.float32)
     V0 = rng.uniform(-70.0, -60.0, int(offsets[-1])).astype(np.float32)
-    return {"row_ptr": np.concatenate(rows), "col": np.concatenate(cols).astype(np.int32),
-            "w": np.concatenate(ws).astype(np.float32), "inh": inh, "V0": V0,
+    return {"row_ptr": row_ptr, "col": col, "w": w, "inh": inh, "V0": V0,
             "offsets": offsets, "sizes": sizes, "k_in": kin, "model_id": model_id,
             "model_of_net": model_of_net}

@@ -89,12 +89,32 @@ def test_untrainable_envelope_is_rejected():
     net.close()
 
 
+def _spike_time_agreement(a, b, N, tol_ms=0.05):
+    """Share of neurons with equal counts in the two runs whose spike times
+    all agree within tol_ms, over the neurons with equal counts."""
+    sa, ia, fa = a["spk"]
+    sb, ib, fb = b["spk"]
+    ta = (sa + fa) * DT
+    tb = (sb + fb) * DT
+    oa, ob = np.argsort(ia, kind="stable"), np.argsort(ib, kind="stable")
+    ca, cb = np.bincount(ia, minlength=N), np.bincount(ib, minlength=N)
+    pa, pb = np.concatenate([[0], np.cumsum(ca)]), np.concatenate([[0], np.cumsum(cb)])
+    eq = np.nonzero(ca == cb)[0]
+    ok = 0
+    for i in eq:
+        x, y = np.sort(ta[oa[pa[i]:pa[i + 1]]]), np.sort(tb[ob[pb[i]:pb[i + 1]]])
+        ok += x.size == 0 or np.abs(x - y).max() <= tol_ms
+    return ok / max(1, eq.size)
+
+
 def test_surrogate_error_is_measured():
-    """Surrogate run of 4,096 multi-channel neurons for 500 ms: a substantial
-    share of neuron-windows is taken from the MLP and the spike-count errors
-    against the plain FP32 path and the FP64 oracle are measured and printed
-    (the plain path itself meets the +-1 target against the oracle; the
-    surrogate does not -- see the design notes)."""
+    """Surrogate run of 4,096 multi-channel neurons for 500 ms: the share of
+    neuron-windows taken from the MLP and the spike-count and spike-time
+    errors against the plain FP32 path and the FP64 oracle, asserted at the
+    levels this surrogate reaches (measured: 63 % of windows accepted, counts
+    within +-1 of the plain path for 62 % of neurons and of the oracle for
+    58 %).  The +-1 / 0.05 ms target is not met; the plain path itself meets
+    it against the oracle."""
     y = inp.multi_channel_neurons(4096, seed=7)
     T = 20_000
     plain = run(y, T)
@@ -114,7 +134,13 @@ def test_surrogate_error_is_measured():
               "count_within_1_vs_oracle": float((dco <= 1).mean()),
               "plain_count_within_1_vs_oracle": float(
                   (np.abs(plain["counts"][idx] - ref["counts"]) <= 1).mean()),
-              "val_loss": sur["rep"]["val_loss"]}
+              "val_loss": sur["rep"]["val_loss"],
+              "spike_times_within_0.05ms_of_plain": _spike_time_agreement(sur, plain, 4096)}
     print(json.dumps(report))
     # the plain path itself meets the count target against the oracle
     assert report["plain_count_within_1_vs_oracle"] == 1.0
+    # the levels the surrogate reaches
+    assert report["accepted_frac"] >= 0.55
+    assert report["count_within_1_vs_plain"] >= 0.55
+    assert report["count_within_1_vs_oracle"] >= 0.5
+    assert report["spike_times_within_0.05ms_of_plain"] >= 0.2
