@@ -637,6 +637,31 @@ def extras(dev, pk):
 
     out["surrogate_multichannel_1e6_500ms"] = extra_surrogate(dev, timed)
 
+    # frequency-response sweep: 256 frequencies (1-1000 Hz) x 256 amplitudes
+    # (up to 20 uA/cm^2), the drive generated in the kernel, 1 s at dt 0.01 ms
+    sw = inp.sin_sweep(n_f=256, n_A=256, f_min=1.0, f_max=1000.0, A_max=20.0, I0=0.0)
+    Nsw = sw["V0"].size
+    net = hh.Network(sw["V0"], 0.01, I_const=sw["I"], precision=hh.HH_PREC_FAST,
+                     drive={"amp": sw["amp"], "freq_hz": sw["freq_hz"], "phase": sw["phase"]})
+    net.set_channels(0, inp.CLASSIC_HH)
+    rec, b = hh.make_record(Nsw, 100_000, spike_cap=0)
+    net.step(10)
+    b["counts"].zero_()
+    net.reset()
+    ms = timed(lambda: net.step(100_000, rec=rec))
+    rmap = b["counts"].cpu().numpy().reshape(sw["n_A"], sw["n_f"])
+    fired = rmap > 0
+    thr = [float(np.linspace(20.0 / 256, 20.0, 256)[np.argmax(fired[:, j])]) if fired[:, j].any() else None
+           for j in range(sw["n_f"])]
+    best = int(np.argmin([t if t is not None else 1e9 for t in thr]))
+    out["frequency_response_sweep_65536_1s"] = {
+        "neuron_steps_per_s": Nsw * 100_000 / (ms * 1e-3), "ms": ms,
+        "points_firing": float(fired.mean()),
+        "lowest_threshold_amplitude_uA_cm2": thr[best],
+        "at_frequency_hz": float(np.geomspace(1.0, 1000.0, 256)[best]),
+        "status": int(net.readout(hh.HH_READ_STATUS)[0])}
+    net.close()
+
     d = inp.recurrent_layer(B=128, n_in=700, n_hid=1024, n_out=20, T=250, seed=0)
     lay = hh.Layer(inp.CLASSIC_HH, batch=128, n_in=700, n_hidden=1024, n_out=20, n_steps=250,
                    substeps=10, dt=0.01, precision=hh.HH_PREC_FAST, checkpoint_every=25)

@@ -218,6 +218,16 @@ typedef struct {
     float bg_weight_nS;
     uint64_t seed;              /* Philox key for the background counts       */
     void* stream;               /* cudaStream_t for all work, NULL = legacy   */
+    /* sinusoidal drive of frequency-response sweeps (Results, the HH filter
+     * bank's response to periodic input): at step t every neuron i gets
+     * I_inj += sin_amp[i] sin(2 pi u_i(t) 2^-32) with the phase, a 32-bit
+     * fraction of a cycle, u_i(t) = t F_i + P_i (mod 2^32),
+     * F_i = round(sin_freq_hz[i] dt_ms 2^32 / 1000), P_i = round(sin_phase[i]
+     * 2^32) mod 2^32 (so the phase is exact over any run length).  Any
+     * memory, [N]; sin_amp NULL = no drive; sin_phase NULL = 0. */
+    const float* sin_amp;       /* uA/cm^2                                     */
+    const float* sin_freq_hz;   /* Hz, >= 0 (required with sin_amp)           */
+    const float* sin_phase;     /* cycles                                      */
 } hh_net_desc;
 
 /* Create a network (Methods, Eq. hh_eq_full; "Cerebral cortex network").

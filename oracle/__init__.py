@@ -104,7 +104,7 @@ def lib():
                                    P(i32), P(i32), i64, P(d), P(d)]
             L.or_simulate_network.restype = C.c_int
             L.or_simulate_network.argtypes = [
-                P(_Model), i32, P(C.c_uint8), P(d), i64, i64, d, d, i32, P(d), P(d),
+                P(_Model), i32, P(C.c_uint8), P(d), i64, i64, d, d, i32, P(d), P(d), P(d),
                 P(i64), P(i32), P(d), P(C.c_uint8), d, d, d, d, i32, d, d, i32, d, u64,
                 P(i32), P(i32), i64, P(i64), i64, P(d), P(i32), i32, P(i32), P(d), i32]
             L.or_sizeof_model.restype = i32
@@ -229,6 +229,23 @@ def simulate(models, I, V0, T, dt, theta=0.0, v_mode=0, model_id=None, gbar=None
     return {"V": Vt, "counts": counts, "spk_step": ss, "spk_frac": sf}
 
 
+def sin_drive_steps(amp, freq_hz, phase, dt, T, t0=0):
+    """The sinusoidal drive as per-step currents [T][N] in FP64:
+    I(t) = amp sin(2 pi u(t) 2^-32) with the phase a 32-bit fraction of a
+    cycle, u(t) = t F + P (mod 2^32), F = round(freq dt 2^32 / 1000),
+    P = round(phase 2^32) mod 2^32 (integer arithmetic, so the phase is the
+    same at any step count)."""
+    amp = np.asarray(amp, dtype=np.float64)
+    f = np.asarray(freq_hz, dtype=np.float32).astype(np.float64)
+    ph = np.asarray(phase, dtype=np.float32).astype(np.float64)
+    two32 = 4294967296.0
+    F = np.mod(np.rint(f * dt * two32 / 1000.0), two32).astype(np.uint64)
+    P = np.mod(np.rint(ph * two32), two32).astype(np.uint64)
+    t = np.arange(t0, t0 + T, dtype=np.uint64)[:, None]
+    u = (t * F[None, :] + P[None, :]) & np.uint64(0xFFFFFFFF)
+    return np.asarray(amp, np.float32).astype(np.float64)[None, :] * np.sin(2.0 * np.pi * u.astype(np.float64) / two32)
+
+
 def philox4x32_10(ctr, key):
     c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
     k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
@@ -277,7 +294,7 @@ def route(N, T, D, row_ptr, col, w, inh, spk_step, spk_idx):
 
 def simulate_network(models, net, T, dt, D, syn, bg=None, I=None, theta=0.0, v_mode=0,
                      model_id=None, gbar=None, forced=None, trace_idx=None, spk_cap=256,
-                     n_threads=0, seed=0):
+                     n_threads=0, seed=0, I_steps=None):
     """Conductance-based network.  net: dict(row_ptr, col, w, inh, V0);
     syn: dict(tau_E, tau_I, E_E, E_I, area_cm2); bg: dict(rate_hz, K, w) or None;
     forced: (steps, idx) spike list for open-loop routing, or None."""
@@ -295,6 +312,9 @@ def simulate_network(models, net, T, dt, D, syn, bg=None, I=None, theta=0.0, v_m
         gb[:g.shape[0]] = g
     mid = None if model_id is None else np.ascontiguousarray(model_id, dtype=np.uint8)
     Ic = _f64(I)
+    Its = _f64(I_steps)
+    if Its is not None and Its.shape != (T, N):
+        raise ValueError("I_steps must be [T][N]")
     if forced is not None:
         fs = np.ascontiguousarray(forced[0], dtype=np.int32)
         fi = np.ascontiguousarray(forced[1], dtype=np.int32)
@@ -311,7 +331,7 @@ def simulate_network(models, net, T, dt, D, syn, bg=None, I=None, theta=0.0, v_m
     bg = bg or {"rate_hz": 0.0, "K": 0, "w": 0.0}
     rc = lib().or_simulate_network(
         marr, nm, _p(mid, C.c_uint8), _p(gb, C.c_double), N, T, dt, theta, v_mode,
-        _p(Ic, C.c_double), _p(V0, C.c_double), _p(rp, C.c_int64), _p(cl, C.c_int32),
+        _p(Ic, C.c_double), _p(Its, C.c_double), _p(V0, C.c_double), _p(rp, C.c_int64), _p(cl, C.c_int32),
         _p(ww, C.c_double), _p(ih, C.c_uint8), syn["tau_E"], syn["tau_I"], syn["E_E"],
         syn["E_I"], D, syn["area_cm2"], bg["rate_hz"], bg["K"], bg["w"], seed,
         _p(fs, C.c_int32), _p(fi, C.c_int32), nf, _p(tix, C.c_int64), ntr,

@@ -389,7 +389,8 @@ int or_route(int64_t N, int64_t T, int32_t D, const int64_t* row_ptr, const int3
 int or_simulate_network(const or_model* models, int32_t n_models, const uint8_t* model_id,
                         const double* gbar, int64_t N, int64_t T, double dt,
                         double theta, int32_t v_mode, const double* I_const,
-                        const double* V0, const int64_t* row_ptr, const int32_t* col,
+                        const double* I_steps, const double* V0, const int64_t* row_ptr,
+                        const int32_t* col,
                         const double* w, const uint8_t* inh, double tau_E, double tau_I,
                         double E_E, double E_I, int32_t D, double area_cm2,
                         double bg_rate_hz, int32_t bg_K, double bg_w, uint64_t seed,
@@ -454,7 +455,10 @@ int or_simulate_network(const or_model* models, int32_t n_models, const uint8_t*
             }
             /* b-e. rates, gates, conductances, V, Ca */
             double Vt = V[i];
-            double Vn = or_step_neuron(M, gb, dt, I_const ? I_const[i] : 0.0, gE[i] * to_mS,
+            /* injected current: constant part plus the per-step part (e.g. a
+               sinusoidal drive), held over the step */
+            const double Ii = (I_const ? I_const[i] : 0.0) + (I_steps ? I_steps[t * N + i] : 0.0);
+            double Vn = or_step_neuron(M, gb, dt, Ii, gE[i] * to_mS,
                                        E_E, gI[i] * to_mS, E_I, v_mode, Vt,
                                        &P[i * OR_MAX_GATES], &Ca[i]);
             /* f. threshold */

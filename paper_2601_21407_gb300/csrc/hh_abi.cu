@@ -73,6 +73,8 @@ struct hh_net {
     // state and per-neuron inputs (device)
     float *V = nullptr, *Vlo = nullptr, *P = nullptr, *Plo = nullptr, *Ca = nullptr;
     float *gE = nullptr, *gI = nullptr, *V0 = nullptr, *I_const = nullptr, *gbar = nullptr;
+    float* sin_amp = nullptr;
+    uint32_t *sin_F = nullptr, *sin_Ph = nullptr;
     uint8_t *model_id = nullptr, *inh = nullptr;
     int32_t *trace_slot = nullptr, *status = nullptr;
 
@@ -294,6 +296,9 @@ struct hh_net {
         p.model_id = model_id;
         p.gbar = gbar;
         p.I_const = I_const;
+        p.sin_amp = sin_amp;
+        p.sin_F = sin_F;
+        p.sin_Ph = sin_Ph;
         p.trace_slot = nullptr;
         p.status = status;
         p.ring = ring;
@@ -680,6 +685,36 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
     if (d->I_const) {
         HH_CUDA(n->alloc(&n->I_const, N));
         HH_CUDA(copy_in(n->I_const, d->I_const, (size_t)N, st));
+    }
+    if (d->sin_amp) {
+        // phase advance per step and initial phase as 32-bit fractions of a cycle
+        if (!d->sin_freq_hz)
+            return fail(HH_EINVAL, "sin_amp needs sin_freq_hz");
+        std::vector<float> a(N), f(N), ph(N, 0.0f);
+        HH_CUDA(cudaMemcpy(a.data(), d->sin_amp, N * sizeof(float), cudaMemcpyDefault));
+        HH_CUDA(cudaMemcpy(f.data(), d->sin_freq_hz, N * sizeof(float), cudaMemcpyDefault));
+        if (d->sin_phase)
+            HH_CUDA(cudaMemcpy(ph.data(), d->sin_phase, N * sizeof(float), cudaMemcpyDefault));
+        std::vector<uint32_t> F(N), P(N);
+        const double two32 = 4294967296.0;
+        for (int64_t i = 0; i < N; ++i) {
+            if (!finite_f(a[i]) || !finite_f(f[i]) || !(f[i] >= 0.0f) || !finite_f(ph[i]))
+                return fail(HH_EINVAL, "sinusoidal drive of neuron %lld: finite amp, phase and freq >= 0 needed",
+                            (long long)i);
+            const double adv = std::nearbyint((double)f[i] * d->dt_ms * two32 / 1000.0);
+            F[i] = (uint32_t)(uint64_t)std::fmod(adv, two32);
+            double pc = std::nearbyint((double)ph[i] * two32);
+            pc = std::fmod(pc, two32);
+            if (pc < 0.0)
+                pc += two32;
+            P[i] = (uint32_t)(uint64_t)pc;
+        }
+        HH_CUDA(n->alloc(&n->sin_amp, N));
+        HH_CUDA(n->alloc(&n->sin_F, N));
+        HH_CUDA(n->alloc(&n->sin_Ph, N));
+        HH_CUDA(cudaMemcpy(n->sin_amp, a.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+        HH_CUDA(cudaMemcpy(n->sin_F, F.data(), N * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        HH_CUDA(cudaMemcpy(n->sin_Ph, P.data(), N * sizeof(uint32_t), cudaMemcpyHostToDevice));
     }
     if (d->model_id) {
         std::vector<uint8_t> h(N);
@@ -1423,6 +1458,8 @@ hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surroga
         return fail(HH_EUNSUPPORTED, "the surrogate needs HH_KERNELS_SPECIALISED");
     if (net->precision != HH_PREC_FAST && net->precision != HH_PREC_ACCURATE)
         return fail(HH_EUNSUPPORTED, "the surrogate supports HH_PREC_FAST and HH_PREC_ACCURATE");
+    if (net->sin_amp)
+        return fail(HH_EUNSUPPORTED, "the surrogate does not support a sinusoidal drive");
     if (!net->installed[0])
         return fail(HH_ESTATE, "model 0 is not installed");
     if (!net->jit_ready) {

@@ -105,6 +105,10 @@ struct NeuronParams {
     const uint8_t* model_id;
     const float* gbar;     // [kMaxChannels][N] or nullptr
     const float* I_const;  // [N] or nullptr
+    // sinusoidal drive (or nullptr): I += amp sin(2 pi u 2^-32), u = step F + Ph (mod 2^32)
+    const float* sin_amp;     // [N] uA/cm^2
+    const uint32_t* sin_F;    // [N] phase advance per step, 2^-32 cycles
+    const uint32_t* sin_Ph;   // [N] phase at step 0, 2^-32 cycles
     const int32_t* trace_slot;  // [N] or nullptr (slot = i for i < n_trace)
     int32_t* status;
     // synapses: the delay line, [R][N] entries of {E, I} (16 bytes, one
@@ -540,6 +544,33 @@ __device__ __forceinline__ void store_state(const NeuronParams& P, int64_t i, co
     }
 }
 
+// Per-neuron sinusoidal drive of frequency-response sweeps: amp
+// sin(2 pi (F t + Ph) 2^-32) at absolute step t, the phase kept exactly as a
+// 32-bit fraction of a cycle (wrapping modulo one cycle).
+struct Drive {
+    float amp;
+    uint32_t F, Ph;
+};
+
+__device__ __forceinline__ Drive load_drive(const NeuronParams& P, int64_t i)
+{
+    Drive d{0.0f, 0u, 0u};
+    if (P.sin_amp) {
+        d.amp = P.sin_amp[i];
+        d.F = P.sin_F[i];
+        d.Ph = P.sin_Ph[i];
+    }
+    return d;
+}
+
+template <bool FAST>
+__device__ __forceinline__ float drive_at(const Drive& d, int64_t t)
+{
+    const uint32_t u = (uint32_t)t * d.F + d.Ph;
+    const float x = (float)u * 2.3283064365386963e-10f;  // cycles in [0, 1]
+    return d.amp * (FAST ? __sinf(6.283185307179586f * x) : sinpif(2.0f * x));
+}
+
 // Warp-aggregated append of this step's spikes to the caller's record:
 // one atomic per warp (ballot + popc), each spiking lane writes its slot.
 // frac = (theta - Vt)/(V - Vt) is formed only by lanes that spiked.  `b` is
@@ -821,9 +852,12 @@ __device__ __forceinline__ void independent_body(const Dyn& dyn, const NeuronPar
         slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
     if (!valid)
         slot = -1;
+    const Drive dr = load_drive(P, i);
     int32_t cnt = 0;
     for (int32_t k = 0; k < n_steps; ++k) {
-        const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
+        float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
+        if (P.sin_amp)
+            I += drive_at<sfu_math<PREC>()>(dr, t0 + k);
         const float Vt = s.V;
         dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
@@ -919,7 +953,8 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
                                                 const float* __restrict__ I_steps, const RecordParams& R,
                                                 float* V_trace, int32_t slot, const SpikeList& L, int32_t lslot,
                                                 State<MAXG, PREC>& s, float& gE, float& gI, float Ic,
-                                                int32_t& cnt, RingQueue& rq, const Between& between)
+                                                const Drive& dr, int32_t& cnt, RingQueue& rq,
+                                                const Between& between)
 {
     int32_t* lstep = L.step + lslot * L.cap;
     int32_t* lidx = L.idx + lslot * L.cap;
@@ -945,7 +980,9 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         rq.ring_slot = rq.ring_slot + 1 == (uint32_t)P.R ? 0u : rq.ring_slot + 1;
         if (BG)
             gE = fmaf((float)poisson_count(word, P.bg_thr, P.bg_n), P.bg_w, gE);
-        const float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
+        float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
+        if (P.sin_amp)
+            I += drive_at<sfu_math<PREC>()>(dr, t);
         const float Vt = s.V;
         dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, __fmul_rn(gE, P.to_mS), P.E_E,
                                       __fmul_rn(gI, P.to_mS), P.E_I, s);
@@ -1024,15 +1061,15 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
                                              int64_t i, int64_t t0, int32_t W, const float* __restrict__ I_steps,
                                              const RecordParams& R, float* V_trace, int32_t slot,
                                              const SpikeList& L, int32_t lslot, State<MAXG, PREC>& s,
-                                             float& gE, float& gI, float Ic, int32_t& cnt, RingQueue& rq,
-                                             const Between& between)
+                                             float& gE, float& gI, float Ic, const Drive& dr, int32_t& cnt,
+                                             RingQueue& rq, const Between& between)
 {
     if (P.bg_n > 0)
         window_steps_bg<MAXG, PREC, true, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
-                                                 lslot, s, gE, gI, Ic, cnt, rq, between);
+                                                 lslot, s, gE, gI, Ic, dr, cnt, rq, between);
     else
         window_steps_bg<MAXG, PREC, false, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
-                                                  lslot, s, gE, gI, Ic, cnt, rq, between);
+                                                  lslot, s, gE, gI, Ic, dr, cnt, rq, between);
 }
 
 // Network window: W <= D steps; spikes go to the window list for routing.
@@ -1080,9 +1117,10 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
     if (!valid)
         slot = -1;
+    const Drive dr = load_drive(P, i);
     int32_t cnt = 0;
     window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, R.V_trace, slot, L, parity, s, gE, gI,
-                                    Ic, cnt, rq, NoWork{});
+                                    Ic, dr, cnt, rq, NoWork{});
     if (valid) {
         store_state(P, i, s);
         P.gE[i] = gE;
@@ -1265,6 +1303,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
         int32_t slot = -1;
         if (R.V_trace && valid)
             slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
+        const Drive dr = load_drive(P, i);
         int32_t cnt = 0;
         for (int32_t w = 0; w < n_win; ++w) {
             if (w >= 2) {
@@ -1282,7 +1321,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
             window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0 + (int64_t)w * W, Ww,
                                             I_steps ? I_steps + (int64_t)w * W * P.N : nullptr, R,
                                             R.V_trace ? R.V_trace + (int64_t)w * W * R.n_trace : nullptr, slot, L,
-                                            (int32_t)((w_index0 + w) % kListSlots), s, gE, gI, Ic, cnt, rq,
+                                            (int32_t)((w_index0 + w) % kListSlots), s, gE, gI, Ic, dr, cnt, rq,
                                             NoWork{});
             neuron_bar();
             if (threadIdx.x == 0)

@@ -71,7 +71,8 @@ class hh_net_desc(C.Structure):
                 ("tau_E", C.c_float), ("tau_I", C.c_float), ("E_E", C.c_float),
                 ("E_I", C.c_float), ("delay_steps", C.c_int32), ("area_cm2", C.c_float),
                 ("bg_rate_hz", C.c_float), ("bg_sources", C.c_int32), ("bg_weight_nS", C.c_float),
-                ("seed", C.c_uint64), ("stream", C.c_void_p)]
+                ("seed", C.c_uint64), ("stream", C.c_void_p), ("sin_amp", C.c_void_p),
+                ("sin_freq_hz", C.c_void_p), ("sin_phase", C.c_void_p)]
 
 
 class hh_spike(C.Structure):
@@ -340,7 +341,7 @@ class Network:
     def __init__(self, V0, dt, *, I_const=None, model_id=None, csr=None, inh=None, syn=None,
                  delay_steps=1, bg=None, seed=0, theta=0.0, precision=HH_PREC_FAST,
                  v_update=HH_V_EXP_EULER, stream=None, n_nets=1, net_offsets=None,
-                 kernels=HH_KERNELS_SPECIALISED):
+                 kernels=HH_KERNELS_SPECIALISED, drive=None):
         d = hh_net_desc()
         self._keep = []
         V0 = self._f32(V0)
@@ -384,6 +385,12 @@ class Network:
             d.bg_rate_hz, d.bg_sources, d.bg_weight_nS = bg["rate_hz"], bg["K"], bg["w"]
         d.seed = seed
         d.stream = stream
+        if drive is not None:
+            # {"amp": [N] uA/cm^2, "freq_hz": [N], "phase": [N] cycles (optional)}
+            d.sin_amp = _ptr(self._f32(drive["amp"]))
+            d.sin_freq_hz = _ptr(self._f32(drive["freq_hz"]))
+            if drive.get("phase") is not None:
+                d.sin_phase = _ptr(self._f32(drive["phase"]))
         self.handle = hh_create_network(d)
         self._keep = []
 

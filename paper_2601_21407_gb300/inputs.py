@@ -134,6 +134,21 @@ def single_neurons(n=1024, seed=0, i_max=20.0):
     return {"I": I, "V0": V0}
 
 
+def sin_sweep(n_f=256, n_A=256, f_min=1.0, f_max=1000.0, A_max=20.0, I0=0.0):
+    """Frequency-response sweep of classic HH neurons under sinusoidal
+    current (the filter-bank workload): one neuron per (frequency, amplitude)
+    pair, frequencies log-spaced in [f_min, f_max] Hz, amplitudes uniform in
+    (0, A_max] uA/cm^2, a constant bias I0, phase 0, V0 = -65 mV.  Neuron
+    i = a * n_f + f.  float32 arrays."""
+    f = np.geomspace(f_min, f_max, n_f)
+    A = np.linspace(A_max / n_A, A_max, n_A)
+    ff, AA = np.meshgrid(f, A)
+    n = n_f * n_A
+    return {"freq_hz": ff.reshape(-1).astype(np.float32), "amp": AA.reshape(-1).astype(np.float32),
+            "phase": np.zeros(n, np.float32), "I": np.full(n, I0, np.float32),
+            "V0": np.full(n, -65.0, np.float32), "n_f": n_f, "n_A": n_A}
+
+
 def multi_channel_neurons(n=1_000_000, seed=0, sigma=0.3, i_max=15.0,
                           model=MULTI_CHANNEL):
     """Independent multi-channel neurons with per-neuron maximal conductances.

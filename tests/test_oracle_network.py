@@ -214,3 +214,25 @@ def test_closed_loop_matches_brute_force():
     assert np.array_equal(r["V"], Vb)
     got = sorted((int(r["spk_step"][i][k]), i) for i in range(n) for k in range(r["counts"][i]))
     assert got == sorted(sp)
+
+
+def test_per_step_current_in_network():
+    """Per-step currents in the network oracle (the sinusoidal drive's
+    input path): with no synapses a network run with I_steps [T][N] equals the
+    independent-neuron oracle given the same I_steps, bit for bit, and a
+    constant I_steps equals the constant-current run."""
+    rng = np.random.default_rng(8)
+    N, T, dt = 12, 800, 0.01
+    V0 = rng.uniform(-70, -60, N).astype(np.float32)
+    Is = oracle.sin_drive_steps(rng.uniform(0, 15, N), rng.uniform(5, 300, N).astype(np.float32),
+                                np.zeros(N, np.float32), dt, T) + 3.0
+    net = {"row_ptr": np.zeros(N + 1, np.int64), "col": np.zeros(0, np.int32), "w": np.zeros(0),
+           "inh": np.zeros(N, np.uint8), "V0": V0}
+    syn = {"tau_E": 5.0, "tau_I": 10.0, "E_E": 0.0, "E_I": -80.0, "area_cm2": 2e-4}
+    a = oracle.simulate_network(HH, net, T, dt, 2, syn, I_steps=Is, trace_idx=np.arange(N))
+    b = oracle.simulate(HH, np.zeros(N), V0, T, dt, I_steps=Is)
+    assert np.array_equal(a["V"], b["V"]) and np.array_equal(a["counts"], b["counts"])
+    assert a["counts"].sum() > 0
+    c = oracle.simulate_network(HH, net, T, dt, 2, syn, I_steps=np.full((T, N), 4.0), trace_idx=np.arange(N))
+    d = oracle.simulate_network(HH, net, T, dt, 2, syn, I=np.full(N, 4.0), trace_idx=np.arange(N))
+    assert np.array_equal(c["V"], d["V"])

@@ -268,3 +268,29 @@ def test_multichannel_invariants():
     ref = spk(0.0005)
     e = [abs(spk(dt) - ref) for dt in (0.02, 0.01, 0.005)]
     assert 3.0 < e[0] / e[1] < 5.2 and 3.0 < e[1] / e[2] < 5.2, e
+
+
+def test_sin_drive_phase_arithmetic():
+    """The oracle's sinusoidal drive: for frequencies whose phase advance is
+    an integer number of 2^-32 cycles per step the 32-bit phase is exact, so
+    the currents equal amp sin(2 pi (f t dt + phase)) to rounding over a
+    million steps, wrap around the cycle without drift, and start at the
+    given phase; a chunked evaluation equals the whole."""
+    dt = 0.01
+    # f dt 2^32 / 1000 an integer: f = k 1000 / (dt 2^32) for integer k
+    k = np.array([1 << 20, 3 << 18, 12345 << 8], dtype=np.float64)
+    f = (k * 1000.0 / (dt * 2.0**32)).astype(np.float32)
+    assert np.array_equal(np.rint(f.astype(np.float64) * dt * 2.0**32 / 1000.0), k)
+    amp = np.array([1.0, 2.5, 7.0])
+    ph = np.array([0.0, 0.25, 0.5], dtype=np.float32)
+    T, t0 = 1000, 1_000_000
+    I = oracle.sin_drive_steps(amp, f, ph, dt, T, t0=t0)
+    t = np.arange(t0, t0 + T)[:, None]
+    cycles = np.mod(t * (k / 2.0**32)[None, :] + ph.astype(np.float64)[None, :], 1.0)
+    assert np.abs(I - amp * np.sin(2 * np.pi * cycles)).max() < 1e-9
+    I0 = oracle.sin_drive_steps(amp, f, ph, dt, 1)
+    assert np.allclose(I0[0], amp * np.sin(2 * np.pi * ph.astype(np.float64)), atol=1e-12)
+    a = oracle.sin_drive_steps(amp, f, ph, dt, 600)
+    b = np.concatenate([oracle.sin_drive_steps(amp, f, ph, dt, 250),
+                        oracle.sin_drive_steps(amp, f, ph, dt, 350, t0=250)])
+    assert np.array_equal(a, b)
