@@ -107,6 +107,9 @@ def lib():
                 P(_Model), i32, P(C.c_uint8), P(d), i64, i64, d, d, i32, P(d), P(d), P(d),
                 P(i64), P(i32), P(d), P(C.c_uint8), d, d, d, d, i32, d, d, i32, d, u64,
                 P(i32), P(i32), i64, P(i64), i64, P(d), P(i32), i32, P(i32), P(d), i32]
+            L.or_simulate_cable.restype = C.c_int
+            L.or_simulate_cable.argtypes = [P(_Model), P(d), i64, P(i64), P(d), d, i64, d, d, P(d), P(d),
+                                            P(d), P(d), P(i32), i32, P(i32), P(d)]
             L.or_sizeof_model.restype = i32
             L.or_sizeof_gate.restype = i32
             assert L.or_sizeof_model() == C.sizeof(_Model)
@@ -244,6 +247,36 @@ def sin_drive_steps(amp, freq_hz, phase, dt, T, t0=0):
     t = np.arange(t0, t0 + T, dtype=np.uint64)[:, None]
     u = (t * F[None, :] + P[None, :]) & np.uint64(0xFFFFFFFF)
     return np.asarray(amp, np.float32).astype(np.float64)[None, :] * np.sin(2.0 * np.pi * u.astype(np.float64) / two32)
+
+
+def simulate_cable(model, parent, area, g_ax, I, V0, T, dt, theta=0.0, gbar=None, I_steps=None,
+                   trace=True, spk_cap=64):
+    """Multi-compartment neurons: compartments joined in a tree (parent[c], -1
+    for a root) by the axial conductance g_ax (mS/cm^2 per unit area of the
+    child), membrane areas `area` (relative), the cable term by the explicit
+    second difference and the channels by exponential Euler.  Returns
+    dict(V [T][N] or None, counts, spk_step, spk_frac)."""
+    M = make_model(model)
+    par = np.ascontiguousarray(parent, dtype=np.int64)
+    N = par.size
+    ar = _f64(area)
+    gb = None
+    if gbar is not None:
+        g = np.asarray(gbar, dtype=np.float64)
+        gb = np.zeros((OR_MAX_CH, N))
+        gb[:g.shape[0]] = g
+    Ic, V0d, Its = _f64(I), _f64(V0), _f64(I_steps)
+    Vt = np.empty((T, N)) if trace else None
+    counts = np.zeros(N, dtype=np.int32)
+    ss = np.full((N, spk_cap), -1, dtype=np.int32)
+    sf = np.zeros((N, spk_cap))
+    rc = lib().or_simulate_cable(C.byref(M), _p(gb, C.c_double), N, _p(par, C.c_int64), _p(ar, C.c_double),
+                                 float(g_ax), T, dt, theta, _p(Ic, C.c_double), _p(Its, C.c_double),
+                                 _p(V0d, C.c_double), _p(Vt, C.c_double), _p(counts, C.c_int32), spk_cap,
+                                 _p(ss, C.c_int32), _p(sf, C.c_double))
+    if rc != 0:
+        raise ValueError("or_simulate_cable rejected its arguments")
+    return {"V": Vt, "counts": counts, "spk_step": ss, "spk_frac": sf}
 
 
 def philox4x32_10(ctr, key):

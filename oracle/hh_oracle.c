@@ -240,6 +240,72 @@ int or_simulate(const or_model* models, int32_t n_models, const uint8_t* model_i
 }
 
 /* ---------------------------------------------------------------------------
+ * Multi-compartment neurons (Methods, Eq. hh_eq_full with the cable term;
+ * "Simplified discretization": exponential Euler for the ion-channel terms,
+ * the second-order explicit difference for the spatial term).  Compartments
+ * form a tree: compartment c with parent[c] >= 0 is joined to it by the
+ * axial conductance g_ax per unit membrane area of c.  Per step, from V_t:
+ *   I_ax[c] += g_ax (V_p - V_c),   I_ax[p] += g_ax (area[c]/area[p]) (V_c - V_p)
+ * (the second difference of the cable, explicit), then every compartment
+ * takes the point-neuron step with I = I_const + I_steps + I_ax held.
+ * ------------------------------------------------------------------------- */
+int or_simulate_cable(const or_model* M, const double* gbar, int64_t N, const int64_t* parent,
+                      const double* area, double g_ax, int64_t T, double dt, double theta,
+                      const double* I_const, const double* I_steps, const double* V0, double* V_trace,
+                      int32_t* counts, int32_t spk_cap, int32_t* spk_step, double* spk_frac)
+{
+    if (N < 0 || T < 0 || !(dt > 0.0) || !(g_ax >= 0.0))
+        return 1;
+    for (int64_t c = 0; c < N; ++c)
+        if (parent[c] >= N || parent[c] == c || !(area[c] > 0.0))
+            return 1;
+    double* V = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double* P = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * OR_MAX_GATES);
+    double* Ca = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double* Iax = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    for (int64_t c = 0; c < N; ++c) {
+        V[c] = V0[c];
+        or_init_neuron(M, V[c], &P[c * OR_MAX_GATES], &Ca[c]);
+        if (counts)
+            counts[c] = 0;
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        for (int64_t c = 0; c < N; ++c)
+            Iax[c] = 0.0;
+        for (int64_t c = 0; c < N; ++c) {
+            const int64_t p = parent[c];
+            if (p < 0)
+                continue;
+            Iax[c] += g_ax * (V[p] - V[c]);
+            Iax[p] += g_ax * (area[c] / area[p]) * (V[c] - V[p]);
+        }
+        for (int64_t c = 0; c < N; ++c) {
+            double gb[OR_MAX_CH];
+            for (int k = 0; k < M->n_channels; ++k)
+                gb[k] = gbar ? gbar[(int64_t)k * N + c] : M->ch[k].gbar;
+            const double I = (I_const ? I_const[c] : 0.0) + (I_steps ? I_steps[t * N + c] : 0.0) + Iax[c];
+            const double Vt = V[c];
+            const double Vn = or_step_neuron(M, gb, dt, I, 0.0, 0.0, 0.0, 0.0, 0, Vt, &P[c * OR_MAX_GATES], &Ca[c]);
+            if (Vt < theta && Vn >= theta) {
+                int32_t k = counts ? counts[c] : 0;
+                if (spk_step && k < spk_cap) {
+                    spk_step[c * spk_cap + k] = (int32_t)t;
+                    spk_frac[c * spk_cap + k] = (theta - Vt) / (Vn - Vt);
+                }
+                if (counts)
+                    counts[c] = k + 1;
+            }
+            V[c] = Vn;
+        }
+        if (V_trace)
+            for (int64_t c = 0; c < N; ++c)
+                V_trace[t * N + c] = V[c];
+    }
+    free(V); free(P); free(Ca); free(Iax);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
  * Philox-4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplies on a
  * 4-word counter with a 2-word Weyl-incremented key.
