@@ -662,6 +662,25 @@ def extras(dev, pk):
         "status": int(net.readout(hh.HH_READ_STATUS)[0])}
     net.close()
 
+    # multi-compartment cells: 65,536 cells of a soma and 3 dendrites x 8
+    # compartments (25 of the 32 lanes of a warp), 100 ms at dt 0.01 ms
+    cb = inp.cable_cells(65_536, seed=0)
+    Ncb = cb["V0"].size
+    net = hh.Network(cb["V0"], 0.01, I_const=cb["I"], precision=hh.HH_PREC_FAST, morph=cb["morph"])
+    net.set_channels(0, inp.CLASSIC_HH, gbar=cb["gbar"])
+    rec, b = hh.make_record(Ncb, 10_000, spike_cap=0)
+    net.step(10)
+    b["counts"].zero_()
+    net.reset()
+    ms = timed(lambda: net.step(10_000, rec=rec))
+    counts = b["counts"].cpu().numpy().reshape(65_536, 32)
+    out["cable_cells_65536x25_100ms"] = {
+        "compartment_steps_per_s": 65_536 * cb["n_comp"] * 10_000 / (ms * 1e-3),
+        "lane_steps_per_s": Ncb * 10_000 / (ms * 1e-3), "ms": ms,
+        "somata_firing": float((counts[:, 0] > 0).mean()),
+        "status": int(net.readout(hh.HH_READ_STATUS)[0])}
+    net.close()
+
     d = inp.recurrent_layer(B=128, n_in=700, n_hid=1024, n_out=20, T=250, seed=0)
     lay = hh.Layer(inp.CLASSIC_HH, batch=128, n_in=700, n_hidden=1024, n_out=20, n_steps=250,
                    substeps=10, dt=0.01, precision=hh.HH_PREC_FAST, checkpoint_every=25)

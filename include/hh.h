@@ -228,7 +228,32 @@ typedef struct {
     const float* sin_amp;       /* uA/cm^2                                     */
     const float* sin_freq_hz;   /* Hz, >= 0 (required with sin_amp)           */
     const float* sin_phase;     /* cycles                                      */
+    const struct hh_morphology* morph; /* multi-compartment cells, or NULL   */
 } hh_net_desc;
+
+/* Multi-compartment cells (Methods, Eq. hh_eq_full with the cable term,
+ * "Simplified discretization": exponential Euler for the ion channels, the
+ * second-order explicit difference for the spatial term; Results,
+ * "neuronal morphology modeling": three dendrites and a soma).  With
+ * hh_net_desc.morph set, every HH_CABLE_LANES consecutive neurons are the
+ * compartments of one cell (n_neurons a multiple of HH_CABLE_LANES): index
+ * 32 k is cell k's soma, 32 k + 1 + d n_per_dendrite + j compartment j
+ * (counted from the soma outward) of dendrite d, and the remaining indices
+ * are ordinary uncoupled point neurons.  Compartments keep every per-neuron
+ * property (model, gbar, currents, synapses, spike records).  At every step
+ * each compartment's injected current gains, from V at the start of the
+ * step, g_axial (V_neighbour - V) for each neighbour -- the compartment
+ * towards the soma and the one further out; the soma's terms towards the
+ * dendrites' first compartments are divided by soma_area_ratio (its
+ * membrane area over a dendritic compartment's).  The explicit coupling is
+ * stable for dt g_axial (2 + 1/soma_area_ratio) / C_m below about 2. */
+#define HH_CABLE_LANES 32
+typedef struct hh_morphology {
+    int32_t n_dendrites;      /* 1..3                                         */
+    int32_t n_per_dendrite;   /* >= 1, 1 + n_dendrites n_per_dendrite <= 32   */
+    float g_axial;            /* mS/cm^2 of membrane (1/(r_l dx^2)), >= 0     */
+    float soma_area_ratio;    /* > 0                                          */
+} hh_morphology;
 
 /* Create a network (Methods, Eq. hh_eq_full; "Cerebral cortex network").
  * Copies every array of *d into library-owned device memory, transposes the

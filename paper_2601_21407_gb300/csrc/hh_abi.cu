@@ -75,6 +75,7 @@ struct hh_net {
     float *gE = nullptr, *gI = nullptr, *V0 = nullptr, *I_const = nullptr, *gbar = nullptr;
     float* sin_amp = nullptr;
     uint32_t *sin_F = nullptr, *sin_Ph = nullptr;
+    hh_morphology morph{};  // n_dendrites 0: point neurons
     uint8_t *model_id = nullptr, *inh = nullptr;
     int32_t *trace_slot = nullptr, *status = nullptr;
 
@@ -299,6 +300,10 @@ struct hh_net {
         p.sin_amp = sin_amp;
         p.sin_F = sin_F;
         p.sin_Ph = sin_Ph;
+        p.cable_nd = morph.n_dendrites;
+        p.cable_np = morph.n_per_dendrite;
+        p.cable_g = morph.g_axial;
+        p.cable_gs = morph.n_dendrites > 0 ? (float)((double)morph.g_axial / (double)morph.soma_area_ratio) : 0.0f;
         p.trace_slot = nullptr;
         p.status = status;
         p.ring = ring;
@@ -685,6 +690,18 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
     if (d->I_const) {
         HH_CUDA(n->alloc(&n->I_const, N));
         HH_CUDA(copy_in(n->I_const, d->I_const, (size_t)N, st));
+    }
+    if (d->morph) {
+        const hh_morphology& m = *d->morph;
+        if (m.n_dendrites < 1 || m.n_dendrites > 3 || m.n_per_dendrite < 1 ||
+            1 + m.n_dendrites * m.n_per_dendrite > HH_CABLE_LANES)
+            return fail(HH_EINVAL, "morphology: 1..3 dendrites, and 1 + n_dendrites n_per_dendrite <= %d",
+                        HH_CABLE_LANES);
+        if (!finite_f(m.g_axial) || m.g_axial < 0.0f || !finite_f(m.soma_area_ratio) || !(m.soma_area_ratio > 0.0f))
+            return fail(HH_EINVAL, "morphology: g_axial >= 0 and soma_area_ratio > 0, finite");
+        if (N % HH_CABLE_LANES != 0)
+            return fail(HH_EINVAL, "with a morphology n_neurons must be a multiple of %d", HH_CABLE_LANES);
+        n->morph = m;
     }
     if (d->sin_amp) {
         // phase advance per step and initial phase as 32-bit fractions of a cycle
@@ -1126,7 +1143,8 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
     const bool spec = net->kernels != HH_KERNELS_TABLE;
     if (spec && !net->jit_ready) {
         std::string err;
-        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, &net->jit, &err))
+        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, net->sin_amp != nullptr,
+                         net->morph.n_dendrites > 0, &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
         net->persistent_cap = -1;
@@ -1458,13 +1476,14 @@ hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surroga
         return fail(HH_EUNSUPPORTED, "the surrogate needs HH_KERNELS_SPECIALISED");
     if (net->precision != HH_PREC_FAST && net->precision != HH_PREC_ACCURATE)
         return fail(HH_EUNSUPPORTED, "the surrogate supports HH_PREC_FAST and HH_PREC_ACCURATE");
-    if (net->sin_amp)
-        return fail(HH_EUNSUPPORTED, "the surrogate does not support a sinusoidal drive");
+    if (net->sin_amp || net->morph.n_dendrites > 0)
+        return fail(HH_EUNSUPPORTED, "the surrogate supports point neurons without a sinusoidal drive");
     if (!net->installed[0])
         return fail(HH_ESTATE, "model 0 is not installed");
     if (!net->jit_ready) {
         std::string err;
-        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, &net->jit, &err))
+        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, net->sin_amp != nullptr,
+                         net->morph.n_dendrites > 0, &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
     }

@@ -109,6 +109,9 @@ struct NeuronParams {
     const float* sin_amp;     // [N] uA/cm^2
     const uint32_t* sin_F;    // [N] phase advance per step, 2^-32 cycles
     const uint32_t* sin_Ph;   // [N] phase at step 0, 2^-32 cycles
+    // multi-compartment cells: one cell per warp (0: point neurons)
+    int32_t cable_nd, cable_np;   // dendrites, compartments per dendrite
+    float cable_g, cable_gs;      // axial conductance, and divided by the soma area ratio
     const int32_t* trace_slot;  // [N] or nullptr (slot = i for i < n_trace)
     int32_t* status;
     // synapses: the delay line, [R][N] entries of {E, I} (16 bytes, one
@@ -571,6 +574,54 @@ __device__ __forceinline__ float drive_at(const Drive& d, int64_t t)
     return d.amp * (FAST ? __sinf(6.283185307179586f * x) : sinpif(2.0f * x));
 }
 
+// Axial coupling of a multi-compartment cell laid out on one warp: lane 0 the
+// soma, lane 1 + d n_per + j compartment j of dendrite d.  Each lane has up
+// to three neighbour lanes and conductances (self and 0 when absent); the
+// current from V_t is the explicit second difference of the cable term.
+struct Axial {
+    int nb0, nb1, nb2;
+    float g0, g1, g2;
+};
+
+__device__ __forceinline__ Axial axial_setup(const NeuronParams& P)
+{
+    const int lane = threadIdx.x & 31;
+    Axial a{lane, lane, lane, 0.0f, 0.0f, 0.0f};
+    const int nd = P.cable_nd, np = P.cable_np;
+    if (nd <= 0)
+        return a;
+    if (lane == 0) {
+        a.nb0 = 1;
+        a.g0 = P.cable_gs;
+        if (nd > 1) {
+            a.nb1 = 1 + np;
+            a.g1 = P.cable_gs;
+        }
+        if (nd > 2) {
+            a.nb2 = 1 + 2 * np;
+            a.g2 = P.cable_gs;
+        }
+    } else if (lane < 1 + nd * np) {
+        const int j = (lane - 1) % np;
+        a.nb0 = j == 0 ? 0 : lane - 1;
+        a.g0 = P.cable_g;
+        if (j + 1 < np) {
+            a.nb1 = lane + 1;
+            a.g1 = P.cable_g;
+        }
+    }
+    return a;
+}
+
+// Called by every lane of the warp.
+__device__ __forceinline__ float axial_current(const Axial& a, float V)
+{
+    const float v0 = __shfl_sync(kFull, V, a.nb0);
+    const float v1 = __shfl_sync(kFull, V, a.nb1);
+    const float v2 = __shfl_sync(kFull, V, a.nb2);
+    return fmaf(a.g0, v0 - V, fmaf(a.g1, v1 - V, a.g2 * (v2 - V)));
+}
+
 // Warp-aggregated append of this step's spikes to the caller's record:
 // one atomic per warp (ballot + popc), each spiking lane writes its slot.
 // frac = (theta - Vt)/(V - Vt) is formed only by lanes that spiked.  `b` is
@@ -826,6 +877,9 @@ __device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t
 // Kernel bodies.  `Dyn` supplies the neuron model(s):
 //   dyn.template load<MAXG, PREC>(mid, P, i, s)  per-neuron conductances
 //   dyn.template step<MAXG, PREC>(mid, dt, v_update, I, gsE, EE, gsI, EI, s)
+//   Dyn::kDrive, Dyn::kCable  whether the kernel carries the sinusoidal drive
+//                            and the axial coupling (run-time compiled
+//                            kernels only for networks that use them)
 // The table interpreter reads a DevModel from the kernel parameters; the
 // run-time compiled kernels build it as a compile-time constant so that the
 // forms, gate counts and parameters fold into the instruction stream.
@@ -852,12 +906,15 @@ __device__ __forceinline__ void independent_body(const Dyn& dyn, const NeuronPar
         slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
     if (!valid)
         slot = -1;
-    const Drive dr = load_drive(P, i);
+    const Drive dr = Dyn::kDrive ? load_drive(P, i) : Drive{0.0f, 0u, 0u};
+    const Axial ax = axial_setup(P);
     int32_t cnt = 0;
     for (int32_t k = 0; k < n_steps; ++k) {
         float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
-        if (P.sin_amp)
+        if (Dyn::kDrive && P.sin_amp)
             I += drive_at<sfu_math<PREC>()>(dr, t0 + k);
+        if (Dyn::kCable && P.cable_nd > 0)
+            I += axial_current(ax, s.V);
         const float Vt = s.V;
         dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, 0.0f, 0.0f, 0.0f, 0.0f, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
@@ -956,6 +1013,7 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
                                                 const Drive& dr, int32_t& cnt, RingQueue& rq,
                                                 const Between& between)
 {
+    const Axial ax = axial_setup(P);
     int32_t* lstep = L.step + lslot * L.cap;
     int32_t* lidx = L.idx + lslot * L.cap;
     // one step; `word` is the background word of step t0 + k
@@ -981,8 +1039,10 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         if (BG)
             gE = fmaf((float)poisson_count(word, P.bg_thr, P.bg_n), P.bg_w, gE);
         float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
-        if (P.sin_amp)
+        if (Dyn::kDrive && P.sin_amp)
             I += drive_at<sfu_math<PREC>()>(dr, t);
+        if (Dyn::kCable && P.cable_nd > 0)
+            I += axial_current(ax, s.V);
         const float Vt = s.V;
         dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, __fmul_rn(gE, P.to_mS), P.E_E,
                                       __fmul_rn(gI, P.to_mS), P.E_I, s);
@@ -1117,7 +1177,7 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
     if (!valid)
         slot = -1;
-    const Drive dr = load_drive(P, i);
+    const Drive dr = Dyn::kDrive ? load_drive(P, i) : Drive{0.0f, 0u, 0u};
     int32_t cnt = 0;
     window_steps<MAXG, PREC, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, R.V_trace, slot, L, parity, s, gE, gI,
                                     Ic, dr, cnt, rq, NoWork{});
@@ -1303,7 +1363,7 @@ __device__ __forceinline__ void persistent_body(const Dyn& dyn, const NeuronPara
         int32_t slot = -1;
         if (R.V_trace && valid)
             slot = P.trace_slot ? P.trace_slot[i] : (i < R.n_trace ? (int32_t)i : -1);
-        const Drive dr = load_drive(P, i);
+        const Drive dr = Dyn::kDrive ? load_drive(P, i) : Drive{0.0f, 0u, 0u};
         int32_t cnt = 0;
         for (int32_t w = 0; w < n_win; ++w) {
             if (w >= 2) {

@@ -108,8 +108,8 @@ cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, co
                                   cudaStream_t st);
 // Compile (or take from the process-wide cache) the kernels for the installed
 // models; false with a message in *err on failure.
-bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, JitKernels* out,
-             std::string* err);
+bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, bool drive, bool cable,
+             JitKernels* out, std::string* err);
 cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, int64_t t0,
                                    int32_t n_steps, const float* I_steps, const RecordParams& R,
                                    cudaStream_t st);

@@ -122,7 +122,8 @@ std::string abi_constants()
     return s;
 }
 
-std::string generate(const hh::DevModels& M, const bool* installed, int precision, int max_gates, int v_update)
+std::string generate(const hh::DevModels& M, const bool* installed, int precision, int max_gates, int v_update,
+                     bool drive, bool cable)
 {
     std::string s = "// generated by libhh: neuron kernels specialised for one model set\n";
     s += abi_constants();
@@ -159,6 +160,8 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
         s += vb;
     }
     s += "struct JitDyn {\n";
+    s += std::string("    static constexpr bool kDrive = ") + (drive ? "true" : "false") + ", kCable = " +
+         (cable ? "true" : "false") + ";\n";
     s += "    template <int MAXG, int PREC>\n";
     s += "    __device__ __forceinline__ void load(int mid, const NeuronParams& P, int64_t i, State<MAXG, PREC>& s) const\n    {\n";
     s += dispatch("load_conductances(M, P.gbar, P.N, i, s)");
@@ -289,14 +292,14 @@ int block_for(int64_t N)
 
 namespace hh {
 
-bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, JitKernels* out,
-             std::string* err)
+bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, bool drive, bool cable,
+             JitKernels* out, std::string* err)
 {
     int max_gates = 1;
     for (int k = 0; k < kMaxModels; ++k)
         if (installed[k] && M.m[k].n_gates > max_gates)
             max_gates = M.m[k].n_gates;
-    const std::string src = generate(M, installed, precision, max_gates, v_update);
+    const std::string src = generate(M, installed, precision, max_gates, v_update, drive, cable);
     if (const char* path = getenv("HH_JIT_DUMP")) {
         if (FILE* f = fopen(path, "w")) {
             fwrite(src.data(), 1, src.size(), f);

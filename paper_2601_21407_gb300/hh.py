@@ -61,6 +61,14 @@ class hh_model_desc(C.Structure):
                 ("ca_tau", C.c_float), ("ca_k", C.c_float), ("ca_rest", C.c_float)]
 
 
+class hh_morphology(C.Structure):
+    _fields_ = [("n_dendrites", C.c_int32), ("n_per_dendrite", C.c_int32), ("g_axial", C.c_float),
+                ("soma_area_ratio", C.c_float)]
+
+
+HH_CABLE_LANES = 32
+
+
 class hh_net_desc(C.Structure):
     _fields_ = [("n_neurons", C.c_int64), ("n_nets", C.c_int32), ("net_offsets", C.c_void_p),
                 ("dt_ms", C.c_double), ("v_threshold", C.c_float), ("v_update", C.c_int32),
@@ -72,7 +80,7 @@ class hh_net_desc(C.Structure):
                 ("E_I", C.c_float), ("delay_steps", C.c_int32), ("area_cm2", C.c_float),
                 ("bg_rate_hz", C.c_float), ("bg_sources", C.c_int32), ("bg_weight_nS", C.c_float),
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("sin_amp", C.c_void_p),
-                ("sin_freq_hz", C.c_void_p), ("sin_phase", C.c_void_p)]
+                ("sin_freq_hz", C.c_void_p), ("sin_phase", C.c_void_p), ("morph", C.POINTER(hh_morphology))]
 
 
 class hh_spike(C.Structure):
@@ -341,7 +349,7 @@ class Network:
     def __init__(self, V0, dt, *, I_const=None, model_id=None, csr=None, inh=None, syn=None,
                  delay_steps=1, bg=None, seed=0, theta=0.0, precision=HH_PREC_FAST,
                  v_update=HH_V_EXP_EULER, stream=None, n_nets=1, net_offsets=None,
-                 kernels=HH_KERNELS_SPECIALISED, drive=None):
+                 kernels=HH_KERNELS_SPECIALISED, drive=None, morph=None):
         d = hh_net_desc()
         self._keep = []
         V0 = self._f32(V0)
@@ -391,6 +399,12 @@ class Network:
             d.sin_freq_hz = _ptr(self._f32(drive["freq_hz"]))
             if drive.get("phase") is not None:
                 d.sin_phase = _ptr(self._f32(drive["phase"]))
+        if morph is not None:
+            # {"n_dendrites", "n_per_dendrite", "g_axial", "soma_area_ratio"}
+            m = hh_morphology(morph["n_dendrites"], morph["n_per_dendrite"], morph["g_axial"],
+                              morph["soma_area_ratio"])
+            self._keep.append(m)
+            d.morph = C.pointer(m)
         self.handle = hh_create_network(d)
         self._keep = []
 

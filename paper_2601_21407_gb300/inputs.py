@@ -149,6 +149,51 @@ def sin_sweep(n_f=256, n_A=256, f_min=1.0, f_max=1000.0, A_max=20.0, I0=0.0):
             "V0": np.full(n, -65.0, np.float32), "n_f": n_f, "n_A": n_A}
 
 
+CABLE_LANES = 32
+
+
+def cable_cells(n_cells, n_dend=3, n_per=8, seed=0, g_axial=2.0, soma_area_ratio=4.0,
+                dend_scale=1.0 / 3.0):
+    """Multi-compartment cells of the classic HH channels (the morphology
+    workload: a soma and three dendrites), laid out 32 compartments per cell:
+    index 32 k the soma of cell k, 32 k + 1 + d n_per + j compartment j of
+    dendrite d, the remaining lanes passive and unstimulated.  Somata carry the
+    full channel densities, dendrites dend_scale of the Na and K densities.
+    Each cell is stimulated, by a constant current U(5, 40) uA/cm^2, at its
+    soma, at the last compartment of a random dendrite, or at both.  Returns
+    V0, I, gbar [3][N] (float32), the parent index and relative area of every
+    compartment (-1 and 1 for the idle lanes) and the morphology."""
+    rng = np.random.default_rng(seed)
+    L = CABLE_LANES
+    n_comp = 1 + n_dend * n_per
+    assert n_comp <= L
+    N = n_cells * L
+    g0 = model_gbar(CLASSIC_HH).astype(np.float32)
+    gbar = np.zeros((3, N), np.float32)
+    parent = np.full(N, -1, np.int64)
+    area = np.ones(N)
+    I = np.zeros(N, np.float32)
+    for k in range(n_cells):
+        b = k * L
+        gbar[:, b] = g0
+        area[b] = soma_area_ratio
+        for d in range(n_dend):
+            for j in range(n_per):
+                c = b + 1 + d * n_per + j
+                parent[c] = b if j == 0 else c - 1
+                gbar[:, c] = g0 * np.array([dend_scale, dend_scale, 1.0], np.float32)
+        gbar[2, b + n_comp: b + L] = g0[2]  # idle lanes: leak only
+        where = rng.integers(0, 3)
+        amp = rng.uniform(5.0, 40.0)
+        if where in (0, 2):
+            I[b] = amp
+        if where in (1, 2):
+            I[b + 1 + int(rng.integers(0, n_dend)) * n_per + n_per - 1] = amp
+    return {"V0": np.full(N, -65.0, np.float32), "I": I, "gbar": gbar, "parent": parent, "area": area,
+            "morph": {"n_dendrites": n_dend, "n_per_dendrite": n_per, "g_axial": g_axial,
+                      "soma_area_ratio": soma_area_ratio}, "n_cells": n_cells, "n_comp": n_comp}
+
+
 def multi_channel_neurons(n=1_000_000, seed=0, sigma=0.3, i_max=15.0,
                           model=MULTI_CHANNEL):
     """Independent multi-channel neurons with per-neuron maximal conductances.

@@ -47,7 +47,8 @@ int main(void){
  printf("%zu %zu\\n", sizeof(hh_neurons_noalloc), offsetof(hh_neurons_noalloc, status));
  printf("%zu %zu %zu %zu %zu\\n", offsetof(hh_net_desc, dt_ms), offsetof(hh_net_desc, n_synapses),
    offsetof(hh_net_desc, seed), offsetof(hh_net_desc, stream), offsetof(hh_model_desc, ca_tau));
- printf("%zu %zu\\n", offsetof(hh_net_desc, V0), offsetof(hh_net_desc, sin_phase));
+ printf("%zu %zu %zu %zu\\n", offsetof(hh_net_desc, V0), offsetof(hh_net_desc, sin_phase),
+   offsetof(hh_net_desc, morph), sizeof(hh_morphology));
  printf("%zu %zu\\n", sizeof(hh_peaks), offsetof(hh_peaks, rcp_per_s));
  printf("%zu %zu\\n", sizeof(hh_grads), offsetof(hh_grads, dX));
  return 0; }
@@ -63,6 +64,7 @@ int main(void){
             hh.hh_neurons_noalloc.status.offset, hh.hh_net_desc.dt_ms.offset, hh.hh_net_desc.n_synapses.offset,
             hh.hh_net_desc.seed.offset, hh.hh_net_desc.stream.offset,
             hh.hh_model_desc.ca_tau.offset, hh.hh_net_desc.V0.offset, hh.hh_net_desc.sin_phase.offset,
+            hh.hh_net_desc.morph.offset, C.sizeof(hh.hh_morphology),
             C.sizeof(hh.hh_peaks), hh.hh_peaks.rcp_per_s.offset,
             C.sizeof(hh.hh_grads), hh.hh_grads.dX.offset]
     assert got == want
