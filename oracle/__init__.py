@@ -98,6 +98,10 @@ def lib():
             L.or_poisson_sample.restype = i32
             L.or_poisson_sample.argtypes = [C.c_uint32, P(u64), i32]
             L.or_background_lambda.restype = d
+            L.or_background_normal.restype = d
+            L.or_background_normal.argtypes = [u64, i64, i64]
+            L.or_background_input.restype = d
+            L.or_background_input.argtypes = [u64, i64, i64, P(u64), i32, d, d]
             L.or_background_lambda.argtypes = [i32, d, d]
             L.or_route.restype = C.c_int
             L.or_route.argtypes = [i64, i64, i32, P(i64), P(i32), P(d), P(C.c_uint8),
@@ -105,7 +109,7 @@ def lib():
             L.or_simulate_network.restype = C.c_int
             L.or_simulate_network.argtypes = [
                 P(_Model), i32, P(C.c_uint8), P(d), i64, i64, d, d, i32, P(d), P(d), P(d),
-                P(i64), P(i32), P(d), P(C.c_uint8), d, d, d, d, i32, d, d, i32, d, u64,
+                P(i64), P(i32), P(d), P(C.c_uint8), d, d, d, d, i32, d, d, i32, d, u64, d, i32,
                 P(i32), P(i32), i64, P(i64), i64, P(d), P(i32), i32, P(i32), P(d), i32]
             L.or_simulate_cable.restype = C.c_int
             L.or_simulate_cable.argtypes = [P(_Model), P(d), i64, P(i64), P(d), d, i64, d, d, P(d), P(d),
@@ -302,6 +306,18 @@ def poisson_sample(u, thr):
     return lib().or_poisson_sample(int(u), _p(thr, C.c_uint64), thr.size)
 
 
+def background_normal(seed, t, i):
+    return lib().or_background_normal(C.c_uint64(seed), int(t), int(i))
+
+
+def background_input(seed, t, i, K, rate_hz, dt, w, sd=0.0):
+    """The network oracle's background input of neuron i at step t (the
+    same C function its loop calls)."""
+    thr = poisson_table(background_lambda(K, rate_hz, dt))
+    tt = (C.c_uint64 * len(thr))(*[int(x) for x in thr])
+    return lib().or_background_input(C.c_uint64(seed), int(t), int(i), tt, len(thr), float(w), float(sd))
+
+
 def background_lambda(K, rate_hz, dt_ms):
     return lib().or_background_lambda(int(K), float(rate_hz), float(dt_ms))
 
@@ -327,10 +343,13 @@ def route(N, T, D, row_ptr, col, w, inh, spk_step, spk_idx):
 
 def simulate_network(models, net, T, dt, D, syn, bg=None, I=None, theta=0.0, v_mode=0,
                      model_id=None, gbar=None, forced=None, trace_idx=None, spk_cap=256,
-                     n_threads=0, seed=0, I_steps=None):
-    """Conductance-based network.  net: dict(row_ptr, col, w, inh, V0);
-    syn: dict(tau_E, tau_I, E_E, E_I, area_cm2); bg: dict(rate_hz, K, w) or None;
-    forced: (steps, idx) spike list for open-loop routing, or None."""
+                     n_threads=0, seed=0, I_steps=None, syn_current=False):
+    """Network of point neurons.  net: dict(row_ptr, col, w, inh, V0);
+    syn: dict(tau_E, tau_I, E_E, E_I, area_cm2); bg: dict(rate_hz, K, w[, sd])
+    or None (sd > 0: compound background, the sum of the count's Gaussian
+    amplitudes); forced: (steps, idx) spike list for open-loop routing, or
+    None.  syn_current: synapses inject their filtered current (weights in
+    uA/cm^2, excitatory minus inhibitory) instead of a conductance."""
     marr, nm = _models_array(models)
     V0 = _f64(net["V0"])
     N = V0.size
@@ -366,7 +385,8 @@ def simulate_network(models, net, T, dt, D, syn, bg=None, I=None, theta=0.0, v_m
         marr, nm, _p(mid, C.c_uint8), _p(gb, C.c_double), N, T, dt, theta, v_mode,
         _p(Ic, C.c_double), _p(Its, C.c_double), _p(V0, C.c_double), _p(rp, C.c_int64), _p(cl, C.c_int32),
         _p(ww, C.c_double), _p(ih, C.c_uint8), syn["tau_E"], syn["tau_I"], syn["E_E"],
-        syn["E_I"], D, syn["area_cm2"], bg["rate_hz"], bg["K"], bg["w"], seed,
+        syn["E_I"], D, syn["area_cm2"], bg["rate_hz"], bg["K"], bg["w"], seed, float(bg.get("sd", 0.0)),
+        1 if syn_current else 0,
         _p(fs, C.c_int32), _p(fi, C.c_int32), nf, _p(tix, C.c_int64), ntr,
         _p(Vt, C.c_double), _p(counts, C.c_int32), spk_cap, _p(ss, C.c_int32),
         _p(sf, C.c_double), n_threads)

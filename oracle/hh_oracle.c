@@ -343,6 +343,28 @@ uint32_t or_background_word(uint64_t seed, int64_t t, int64_t i)
     return out[(uint64_t)t & 3u];
 }
 
+/* Standard normal of the compound background (Methods, "Cerebral cortex
+ * network": the background after integration is sum_i Poisson(lambda)_i
+ * Gaussian(mu, sigma)_i, sampled directly as N(k mu, k sigma^2) for the
+ * Poisson count k): Box-Muller on the Philox-4x32-10 block of counter
+ * (t/4, i, 2, (t/4) >> 32), key = seed.  Steps 4q, 4q+1 use words 0, 1 and
+ * steps 4q+2, 4q+3 words 2, 3, as r cos(2 pi u2) and r sin(2 pi u2) with
+ * r = sqrt(-2 ln u1), u = (word + 1/2) 2^-32. */
+double or_background_normal(uint64_t seed, int64_t t, int64_t i)
+{
+    uint64_t q = (uint64_t)t >> 2;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)i, 2u, (uint32_t)(q >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    const int pair = (int)(((uint64_t)t & 3u) >> 1);
+    const double u1 = ((double)out[2 * pair] + 0.5) / 4294967296.0;
+    const double u2 = ((double)out[2 * pair + 1] + 0.5) / 4294967296.0;
+    const double r = sqrt(-2.0 * log(u1));
+    const double a = 2.0 * 3.14159265358979323846 * u2;
+    return ((uint64_t)t & 1u) ? r * sin(a) : r * cos(a);
+}
+
 /* Poisson CDF thresholds on the 2^32 grid: thr[j] = min(2^32, floor(F(j) 2^32))
  * with F(j) = sum_{i<=j} e^-lambda lambda^i / i!, accumulated as
  * pmf_0 = exp(-lambda), pmf_j = (pmf_{j-1} * lambda) / j, F_j = F_{j-1} + pmf_j.
@@ -380,6 +402,19 @@ int32_t or_poisson_sample(uint32_t u, const uint64_t* thr, int32_t n)
 double or_background_lambda(int32_t K, double rate_hz, double dt_ms)
 {
     return (((double)K * rate_hz) * dt_ms) / 1000.0;
+}
+
+/* Background input of neuron i at step t: k w for the Poisson count k of
+ * the step, plus sqrt(k) sd z with z the step's standard normal when sd > 0
+ * (the compound Poisson x Gaussian sum of the k event amplitudes). */
+double or_background_input(uint64_t seed, int64_t t, int64_t i, const uint64_t* thr, int32_t n_thr, double w,
+                           double sd)
+{
+    const int32_t k = or_poisson_sample(or_background_word(seed, t, i), thr, n_thr);
+    double amp = (double)k * w;
+    if (sd > 0.0 && k > 0)
+        amp += sqrt((double)k) * sd * or_background_normal(seed, t, i);
+    return amp;
 }
 
 /* ---------------------------------------------------------------------------
@@ -460,6 +495,7 @@ int or_simulate_network(const or_model* models, int32_t n_models, const uint8_t*
                         const double* w, const uint8_t* inh, double tau_E, double tau_I,
                         double E_E, double E_I, int32_t D, double area_cm2,
                         double bg_rate_hz, int32_t bg_K, double bg_w, uint64_t seed,
+                        double bg_sd, int32_t syn_current,
                         const int32_t* forced_step, const int32_t* forced_idx,
                         int64_t n_forced, const int64_t* trace_idx, int64_t n_trace,
                         double* V_trace, int32_t* counts, int32_t spk_cap,
@@ -515,17 +551,20 @@ int or_simulate_network(const or_model* models, int32_t n_models, const uint8_t*
             gI[i] += ringI[slot * N + i];
             ringE[slot * N + i] = 0.0;
             ringI[slot * N + i] = 0.0;
-            if (n_thr > 0) {
-                int32_t k = or_poisson_sample(or_background_word(seed, t, i), thr, n_thr);
-                gE[i] += (double)k * bg_w;
-            }
+            if (n_thr > 0)
+                gE[i] += or_background_input(seed, t, i, thr, n_thr, bg_w, bg_sd);
             /* b-e. rates, gates, conductances, V, Ca */
             double Vt = V[i];
             /* injected current: constant part plus the per-step part (e.g. a
-               sinusoidal drive), held over the step */
-            const double Ii = (I_const ? I_const[i] : 0.0) + (I_steps ? I_steps[t * N + i] : 0.0);
-            double Vn = or_step_neuron(M, gb, dt, Ii, gE[i] * to_mS,
-                                       E_E, gI[i] * to_mS, E_I, v_mode, Vt,
+               sinusoidal drive), held over the step; current-based synapses
+               add their filtered currents (excitatory minus inhibitory) */
+            double Ii = (I_const ? I_const[i] : 0.0) + (I_steps ? I_steps[t * N + i] : 0.0);
+            double gEs = gE[i] * to_mS, gIs = gI[i] * to_mS;
+            if (syn_current) {
+                Ii += gE[i] - gI[i];
+                gEs = gIs = 0.0;
+            }
+            double Vn = or_step_neuron(M, gb, dt, Ii, gEs, E_E, gIs, E_I, v_mode, Vt,
                                        &P[i * OR_MAX_GATES], &Ca[i]);
             /* f. threshold */
             spiked[i] = 0;

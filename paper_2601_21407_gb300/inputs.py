@@ -109,7 +109,62 @@ MULTI_CHANNEL = {
     "calcium": {"channel": "CaL", "tau": 20.0, "k": 0.05, "rest": 0.05},
 }
 
-MODELS = {"hh1952": CLASSIC_HH, "multi6": MULTI_CHANNEL}
+def _bc2008(name, gNa, gKd, gM, gL, EL, VT, tau_max):
+    """Pospischil et al. 2008 minimal HH-type cortical neuron (Traub-Miles Na
+    and delayed-rectifier K with threshold shift V_T, a slow M-type K current
+    p with p_inf = 1/(1 + e^{-(V+35)/10}) and tau_p = tau_max/(3.3 e^{(V+35)/20}
+    + e^{-(V+35)/20}), leak), in the closed forms of this table: the Traub
+    rates are linoid / exp / sigmoid forms with half-points shifted by V_T,
+    and 3.3 e^{x/20} = e^{(x + 20 ln 3.3)/20} puts tau_p in the bell form."""
+    return {
+        "name": name, "C_m": 1.0,
+        "channels": [
+            {"name": "Na", "E": 50.0, "gbar": gNa, "gates": [
+                {"kind": "ab", "power": 3, "f1": fn("linoid", 0.32, VT + 13.0, 4.0),
+                 "f2": fn("linoid", -0.28, VT + 40.0, -5.0)},
+                {"kind": "ab", "power": 1, "f1": fn("exp", 0.128, VT + 17.0, -18.0),
+                 "f2": fn("sigmoid", 4.0, VT + 40.0, -5.0)},
+            ]},
+            {"name": "Kd", "E": -90.0, "gbar": gKd, "gates": [
+                {"kind": "ab", "power": 4, "f1": fn("linoid", 0.032, VT + 15.0, 5.0),
+                 "f2": fn("exp", 0.5, VT + 10.0, -40.0)},
+            ]},
+            {"name": "M", "E": -90.0, "gbar": gM, "gates": [
+                {"kind": "inftau", "power": 1, "f1": fn("sigmoid", 1.0, -35.0, -10.0),
+                 "f2": fn("bell", tau_max, -35.0 - 20.0 * math.log(3.3), 20.0, -35.0, -20.0)},
+            ]},
+            {"name": "L", "E": EL, "gbar": gL, "gates": []},
+        ],
+        "calcium": None,
+    }
+
+
+# Regular-spiking pyramidal and fast-spiking interneuron parameter sets of the
+# BC2008 model (the cortex variant's excitatory and inhibitory cells).
+BC2008_RS = _bc2008("bc2008_rs", 56.0, 6.0, 0.075, 0.0205, -70.3, -56.2, 608.0)
+BC2008_FS = _bc2008("bc2008_fs", 58.0, 3.9, 0.0787, 0.038, -70.4, -57.9, 502.0)
+
+MODELS = {"hh1952": CLASSIC_HH, "multi6": MULTI_CHANNEL, "bc2008_rs": BC2008_RS, "bc2008_fs": BC2008_FS}
+
+
+def cortex_network(n=10_000, k_in=1_000, exc_frac=0.8, seed=0, w_mu=0.26, w_sd=0.026, g_inh=4.0):
+    """The current-based cortex variant's stand-in network (the Potjans-
+    Diesmann connection tables are not in this container): fixed in-degree
+    k_in from distinct random sources, 80 % excitatory regular-spiking and
+    20 % inhibitory fast-spiking BC2008 cells (model ids 0 / 1), synaptic
+    current amplitudes ~ N(w_mu, w_sd) uA/cm^2 clipped at 0, inhibitory ones
+    scaled by g_inh (their sign is that of the inhibitory current);
+    V0 ~ U(-72, -66) mV."""
+    gen = random_in_csr_fast if n * k_in > 2_000_000 else random_in_csr
+    row_ptr, col, _ = gen(n, k_in, seed)
+    rng = np.random.default_rng(seed + 7)
+    n_exc = int(round(exc_frac * n))
+    inh = np.zeros(n, np.uint8)
+    inh[n_exc:] = 1
+    w = np.clip(rng.normal(w_mu, w_sd, col.size), 0.0, None)
+    w = np.where(inh[col] == 1, g_inh * w, w).astype(np.float32)
+    return {"row_ptr": row_ptr, "col": col, "w": w, "inh": inh, "model_id": inh.copy(),
+            "V0": rng.uniform(-72.0, -66.0, n).astype(np.float32), "n": n, "k_in": k_in}
 
 
 def model_gbar(model) -> np.ndarray:
