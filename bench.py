@@ -662,6 +662,37 @@ def extras(dev, pk):
         "status": int(net.readout(hh.HH_READ_STATUS)[0])}
     net.close()
 
+    # current-based cortex variant: 77,000 BC2008 cells (80 % RS, 20 % FS),
+    # in-degree 1,000 (7.7e7 synapses), current synapses N(0.26, 0.026)
+    # uA/cm^2 (inhibitory x 4), compound background 2,000 x 8 Hz x N(0.17,
+    # 0.017), dt 0.1 ms, 1.5 ms delay, 1 s simulated
+    ct = inp.cortex_network(n=77_000, k_in=1_000, seed=0)
+    csyn = {"tau_E": 0.5, "tau_I": 0.5, "E_E": 0.0, "E_I": -80.0, "area_cm2": 2e-4}
+    net = hh.Network(ct["V0"], 0.1, csr=(ct["row_ptr"], ct["col"], ct["w"]), inh=ct["inh"], syn=csyn,
+                     delay_steps=15, bg={"rate_hz": 8.0, "K": 2000, "w": 0.17, "sd": 0.017}, seed=1,
+                     precision=hh.HH_PREC_FAST, model_id=ct["model_id"], syn_mode=hh.HH_SYN_CURRENT)
+    net.set_channels(0, inp.BC2008_RS)
+    net.set_channels(1, inp.BC2008_FS)
+    V0c = torch.as_tensor(ct["V0"], device=dev)
+    rec, b = hh.make_record(77_000, 10_000, spike_cap=0)
+
+    def run_ct():
+        b["counts"].zero_()
+        net.reset(V0c)
+        net.step(10_000, rec=rec)
+
+    run_ct()
+    ms = timed(run_ct, reps=2)
+    cc = b["counts"].cpu().numpy()
+    out_deg = np.diff(net.readout(hh.HH_READ_N_OUT))
+    out["cortex_current_based_77k_1s"] = {
+        "neuron_steps_per_s": 77_000 * 10_000 / (ms * 1e-3), "ms_per_1s_sim": ms,
+        "synaptic_events_per_s": float((cc.astype(np.int64) * out_deg).sum()) / (ms * 1e-3),
+        "rate_exc_hz": float(cc[:61_600].mean()), "rate_inh_hz": float(cc[61_600:].mean()),
+        "status": int(net.readout(hh.HH_READ_STATUS)[0])}
+    net.close()
+    del ct
+
     # multi-compartment cells: 65,536 cells of a soma and 3 dendrites x 8
     # compartments (25 of the 32 lanes of a warp), 100 ms at dt 0.01 ms
     cb = inp.cable_cells(65_536, seed=0)

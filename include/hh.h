@@ -229,7 +229,20 @@ typedef struct {
     const float* sin_freq_hz;   /* Hz, >= 0 (required with sin_amp)           */
     const float* sin_phase;     /* cycles                                      */
     const struct hh_morphology* morph; /* multi-compartment cells, or NULL   */
+    /* synapse model (Methods, "Cerebral cortex network"): HH_SYN_CONDUCTANCE
+     * (g_E (V - E_E) + g_I (V - E_I), weights in nS) or HH_SYN_CURRENT (the
+     * synapses inject their filtered currents, I_E - I_I, weights in
+     * uA/cm^2; E_E, E_I and area_cm2 unused); tau_E, tau_I filter both */
+    int32_t syn_mode;
+    /* compound background: with bg_weight_sd > 0 each step's background is
+     * N(k bg_weight_nS, k bg_weight_sd^2) for its Poisson count k (the sum of
+     * k Gaussian event amplitudes), the normal by Box-Muller on the
+     * Philox-4x32-10 block of counter (t/4, i, 2, (t/4) >> 32): steps 4q,
+     * 4q + 1 take r cos and r sin of words 0, 1, steps 4q + 2, 4q + 3 of words
+     * 2, 3 (r = sqrt(-2 ln u1), angle 2 pi u2, u = (word + 1/2) 2^-32) */
+    float bg_weight_sd;
 } hh_net_desc;
+enum { HH_SYN_CONDUCTANCE = 0, HH_SYN_CURRENT = 1 };
 
 /* Multi-compartment cells (Methods, Eq. hh_eq_full with the cable term,
  * "Simplified discretization": exponential Euler for the ion channels, the

@@ -76,6 +76,19 @@ struct hh_net {
     float* sin_amp = nullptr;
     uint32_t *sin_F = nullptr, *sin_Ph = nullptr;
     hh_morphology morph{};  // n_dendrites 0: point neurons
+    int32_t syn_mode = HH_SYN_CONDUCTANCE;
+    float bg_sd = 0.0f;
+
+    hh::JitFlags jit_flags() const
+    {
+        hh::JitFlags f;
+        f.v_update = v_update;
+        f.drive = sin_amp != nullptr;
+        f.cable = morph.n_dendrites > 0;
+        f.syn_current = syn_mode == HH_SYN_CURRENT;
+        f.compound = has_bg && bg_sd > 0.0f;
+        return f;
+    }
     uint8_t *model_id = nullptr, *inh = nullptr;
     int32_t *trace_slot = nullptr, *status = nullptr;
 
@@ -320,6 +333,8 @@ struct hh_net {
             ++nb;
         p.bg_n = nb;
         p.bg_w = bg_w;
+        p.bg_sd = bg_sd;
+        p.syn_current = syn_mode == HH_SYN_CURRENT ? 1 : 0;
         p.seed = seed;
         // Philox-4x32-10 key schedule (Salmon et al.): the key is bumped by
         // the Weyl constants after every round
@@ -873,6 +888,12 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
     n->has_bg = d->bg_sources > 0 && d->bg_rate_hz > 0.0f;
     n->seed = d->seed;
     n->bg_w = d->bg_weight_nS;
+    if (!finite_f(d->bg_weight_sd) || d->bg_weight_sd < 0.0f)
+        return fail(HH_EINVAL, "bg_weight_sd must be finite and >= 0");
+    n->bg_sd = d->bg_weight_sd;
+    if (d->syn_mode != HH_SYN_CONDUCTANCE && d->syn_mode != HH_SYN_CURRENT)
+        return fail(HH_EINVAL, "unknown syn_mode %d", d->syn_mode);
+    n->syn_mode = d->syn_mode;
     if (n->has_bg) {
         const double lambda = (((double)d->bg_sources * (double)d->bg_rate_hz) * d->dt_ms) / 1000.0;
         n->n_thr = poisson_thresholds(lambda, n->thr, hh::kMaxPoisson);
@@ -1143,8 +1164,7 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
     const bool spec = net->kernels != HH_KERNELS_TABLE;
     if (spec && !net->jit_ready) {
         std::string err;
-        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, net->sin_amp != nullptr,
-                         net->morph.n_dendrites > 0, &net->jit, &err))
+        if (!hh::jit_get(net->models, net->installed, net->precision, net->jit_flags(), &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
         net->persistent_cap = -1;
@@ -1482,8 +1502,7 @@ hh_status hh_surrogate_train(hh_net* net, const hh_surrogate_desc* d, hh_surroga
         return fail(HH_ESTATE, "model 0 is not installed");
     if (!net->jit_ready) {
         std::string err;
-        if (!hh::jit_get(net->models, net->installed, net->precision, net->v_update, net->sin_amp != nullptr,
-                         net->morph.n_dendrites > 0, &net->jit, &err))
+        if (!hh::jit_get(net->models, net->installed, net->precision, net->jit_flags(), &net->jit, &err))
             return fail(HH_ECUDA, "%s", err.c_str());
         net->jit_ready = true;
     }

@@ -123,6 +123,8 @@ struct NeuronParams {
     int32_t bg_n;     // thresholds below 2^32 (0 = off); the count of a step is
                       // #{j < bg_n : word >= bg_thr[j]} (nondecreasing table)
     float bg_w;
+    float bg_sd;      // > 0: compound background N(k bg_w, k bg_sd^2)
+    int32_t syn_current;  // 1: synapses inject gE - gI as a current (uA/cm^2)
     uint64_t seed;
     // Philox-4x32-10 round keys of the seed: (k0, k1) of round r at 2r, 2r + 1
     uint32_t rk[20];
@@ -704,6 +706,36 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk)
     return c;
 }
 
+// The four standard normals of steps 4q..4q+3 of the compound background
+// from the Philox block of counter (q, i, 2, q >> 32): Box-Muller on words
+// (0, 1) and (2, 3), cos then sin.
+template <bool FAST>
+__device__ __forceinline__ float4 bg_normals(uint64_t q, int64_t i, const uint32_t* rk)
+{
+    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)q, (uint32_t)i, 2u, (uint32_t)(q >> 32)), rk);
+    const float s = 2.3283064365386963e-10f;
+    const float u1 = fmaf((float)w.x, s, 0.5f * s), u2 = fmaf((float)w.y, s, 0.5f * s);
+    const float u3 = fmaf((float)w.z, s, 0.5f * s), u4 = fmaf((float)w.w, s, 0.5f * s);
+    float r0, r1, s0, c0, s1, c1;
+    if (FAST) {
+        r0 = sqrtf(-2.0f * __logf(u1));
+        r1 = sqrtf(-2.0f * __logf(u3));
+        __sincosf(6.283185307179586f * u2, &s0, &c0);
+        __sincosf(6.283185307179586f * u4, &s1, &c1);
+    } else {
+        r0 = sqrtf(-2.0f * logf(u1));
+        r1 = sqrtf(-2.0f * logf(u3));
+        sincospif(2.0f * u2, &s0, &c0);
+        sincospif(2.0f * u4, &s1, &c1);
+    }
+    return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+__device__ __forceinline__ float pickf(const float4& v, int w)
+{
+    return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
 __device__ __forceinline__ uint32_t pick(const uint4& v, int w)
 {
     return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
@@ -877,9 +909,10 @@ __device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t
 // Kernel bodies.  `Dyn` supplies the neuron model(s):
 //   dyn.template load<MAXG, PREC>(mid, P, i, s)  per-neuron conductances
 //   dyn.template step<MAXG, PREC>(mid, dt, v_update, I, gsE, EE, gsI, EI, s)
-//   Dyn::kDrive, Dyn::kCable  whether the kernel carries the sinusoidal drive
-//                            and the axial coupling (run-time compiled
-//                            kernels only for networks that use them)
+//   Dyn::kDrive, Dyn::kCable, Dyn::kSynCurrent, Dyn::kCompound  whether the
+//       kernel carries the sinusoidal drive, the axial coupling, current-based
+//       synapses and the compound background (the run-time compiled kernels
+//       only for networks that use them)
 // The table interpreter reads a DevModel from the kernel parameters; the
 // run-time compiled kernels build it as a compile-time constant so that the
 // forms, gate counts and parameters fold into the instruction stream.
@@ -1004,7 +1037,7 @@ __device__ __forceinline__ void ring_preload(const NeuronParams& P, int64_t i, i
 struct NoWork {
     __device__ __forceinline__ void operator()(int32_t) const {}
 };
-template <int MAXG, int PREC, bool BG, int GROUP, class Dyn, class Between>
+template <int MAXG, int PREC, bool BG, bool CB, int GROUP, class Dyn, class Between>
 __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const NeuronParams& P, bool valid,
                                                 int64_t i, int64_t t0, int32_t W,
                                                 const float* __restrict__ I_steps, const RecordParams& R,
@@ -1016,8 +1049,9 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
     const Axial ax = axial_setup(P);
     int32_t* lstep = L.step + lslot * L.cap;
     int32_t* lidx = L.idx + lslot * L.cap;
-    // one step; `word` is the background word of step t0 + k
-    auto step = [&](int32_t k, uint32_t word) {
+    // one step; `word` is the background word of step t0 + k and `z` its
+    // standard normal (compound background)
+    auto step = [&](int32_t k, uint32_t word, float z) {
         const int64_t t = t0 + k;
         const long long e = rq.q[0].x, h = rq.q[0].y;
 #pragma unroll
@@ -1036,16 +1070,25 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         if (valid && (e | h))
             *ring_entry(P, rq.ring_slot, i) = make_longlong2(0, 0);
         rq.ring_slot = rq.ring_slot + 1 == (uint32_t)P.R ? 0u : rq.ring_slot + 1;
-        if (BG)
-            gE = fmaf((float)poisson_count(word, P.bg_thr, P.bg_n), P.bg_w, gE);
+        if (BG) {
+            const float kb = (float)poisson_count(word, P.bg_thr, P.bg_n);
+            if (CB)  // the sum of k Gaussian amplitudes: N(k w, k sd^2)
+                gE = __fadd_rn(gE, fmaf(sqrtf(kb) * P.bg_sd, z, kb * P.bg_w));
+            else
+                gE = fmaf(kb, P.bg_w, gE);
+        }
         float I = Ic + (I_steps ? I_steps[(int64_t)k * P.N + i] : 0.0f);
         if (Dyn::kDrive && P.sin_amp)
             I += drive_at<sfu_math<PREC>()>(dr, t);
         if (Dyn::kCable && P.cable_nd > 0)
             I += axial_current(ax, s.V);
         const float Vt = s.V;
-        dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, __fmul_rn(gE, P.to_mS), P.E_E,
-                                      __fmul_rn(gI, P.to_mS), P.E_I, s);
+        if (Dyn::kSynCurrent && P.syn_current)
+            dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, __fadd_rn(I, __fsub_rn(gE, gI)), 0.0f, 0.0f, 0.0f,
+                                          0.0f, s);
+        else
+            dyn.template step<MAXG, PREC>(mid, P.dt, P.v_update, I, __fmul_rn(gE, P.to_mS), P.E_E,
+                                          __fmul_rn(gI, P.to_mS), P.E_I, s);
         const bool spk = valid && Vt < P.theta && s.V >= P.theta;
         cnt += spk;
         // one ballot for the window list and the caller's record
@@ -1070,16 +1113,26 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         }
         return r;
     };
+    // the block of normals of steps 4q..4q+3 (compound background)
+    auto normals = [&](int64_t t) {
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (CB)
+            z = bg_normals<sfu_math<PREC>()>((uint64_t)t >> 2, i, P.rk);
+        return z;
+    };
     if (GROUP != 4) {
         // one step per iteration, the block drawn at its first step (the
         // smaller loop body, for models whose step is long)
         uint4 r = make_uint4(0, 0, 0, 0);
+        float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll kRingAhead
         for (int32_t k = 0; k < W; ++k) {
             const int64_t t = t0 + k;
-            if (BG && (k == 0 || (t & 3) == 0))
+            if (BG && (k == 0 || (t & 3) == 0)) {
                 r = draw(t);
-            step(k, pick(r, (int)(t & 3)));
+                zz = normals(t);
+            }
+            step(k, pick(r, (int)(t & 3)), pickf(zz, (int)(t & 3)));
         }
         return;
     }
@@ -1091,8 +1144,9 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
     const int32_t head = min(W, (int32_t)((4 - (t0 & 3)) & 3));
     if (head > 0) {
         const uint4 r = draw(t0);
+        const float4 zz = normals(t0);
         for (; k < head; ++k)
-            step(k, pick(r, (int)((t0 + k) & 3)));
+            step(k, pick(r, (int)((t0 + k) & 3)), pickf(zz, (int)((t0 + k) & 3)));
     }
     // unrolled by four steps, a multiple of the queue depth, so that the
     // queue rotates by renaming registers instead of moving values whose
@@ -1101,15 +1155,17 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
 #pragma unroll 1
     for (; k + 4 <= W; k += 4) {
         const uint4 r = draw(t0 + k);
-        step(k, r.x);
-        step(k + 1, r.y);
-        step(k + 2, r.z);
-        step(k + 3, r.w);
+        const float4 zz = normals(t0 + k);
+        step(k, r.x, zz.x);
+        step(k + 1, r.y, zz.y);
+        step(k + 2, r.z, zz.z);
+        step(k + 3, r.w, zz.w);
     }
     if (k < W) {
         const uint4 r = draw(t0 + k);
+        const float4 zz = normals(t0 + k);
         for (; k < W; ++k)
-            step(k, pick(r, (int)((t0 + k) & 3)));
+            step(k, pick(r, (int)((t0 + k) & 3)), pickf(zz, (int)((t0 + k) & 3)));
     }
 }
 
@@ -1124,12 +1180,16 @@ __device__ __forceinline__ void window_steps(const Dyn& dyn, int mid, const Neur
                                              float& gE, float& gI, float Ic, const Drive& dr, int32_t& cnt,
                                              RingQueue& rq, const Between& between)
 {
-    if (P.bg_n > 0)
-        window_steps_bg<MAXG, PREC, true, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
-                                                 lslot, s, gE, gI, Ic, dr, cnt, rq, between);
+    if (P.bg_n > 0 && Dyn::kCompound && P.bg_sd > 0.0f)
+        window_steps_bg<MAXG, PREC, true, Dyn::kCompound, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R,
+                                                                 V_trace, slot, L, lslot, s, gE, gI, Ic, dr, cnt,
+                                                                 rq, between);
+    else if (P.bg_n > 0)
+        window_steps_bg<MAXG, PREC, true, false, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot,
+                                                        L, lslot, s, gE, gI, Ic, dr, cnt, rq, between);
     else
-        window_steps_bg<MAXG, PREC, false, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot, L,
-                                                  lslot, s, gE, gI, Ic, dr, cnt, rq, between);
+        window_steps_bg<MAXG, PREC, false, false, GROUP>(dyn, mid, P, valid, i, t0, W, I_steps, R, V_trace, slot,
+                                                         L, lslot, s, gE, gI, Ic, dr, cnt, rq, between);
 }
 
 // Network window: W <= D steps; spikes go to the window list for routing.

@@ -108,8 +108,14 @@ cudaError_t jit_launch_persistent(const JitKernels& K, const NeuronParams& P, co
                                   cudaStream_t st);
 // Compile (or take from the process-wide cache) the kernels for the installed
 // models; false with a message in *err on failure.
-bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, bool drive, bool cable,
-             JitKernels* out, std::string* err);
+// What the run-time compiled neuron kernels of a network carry besides the
+// models: its V update and the optional per-step inputs.
+struct JitFlags {
+    int v_update = HH_V_EXP_EULER;
+    bool drive = false, cable = false, syn_current = false, compound = false;
+};
+bool jit_get(const DevModels& M, const bool* installed, int precision, const JitFlags& f, JitKernels* out,
+             std::string* err);
 cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, int64_t t0,
                                    int32_t n_steps, const float* I_steps, const RecordParams& R,
                                    cudaStream_t st);

@@ -122,8 +122,8 @@ std::string abi_constants()
     return s;
 }
 
-std::string generate(const hh::DevModels& M, const bool* installed, int precision, int max_gates, int v_update,
-                     bool drive, bool cable)
+std::string generate(const hh::DevModels& M, const bool* installed, int precision, int max_gates,
+                     const hh::JitFlags& f)
 {
     std::string s = "// generated by libhh: neuron kernels specialised for one model set\n";
     s += abi_constants();
@@ -156,12 +156,13 @@ std::string generate(const hh::DevModels& M, const bool* installed, int precisio
     {
         // the network's V update (exponential or explicit Euler) as a constant
         char vb[96];
-        snprintf(vb, sizeof(vb), "constexpr int kJitVUpdate = %d;\n\n", v_update);
+        snprintf(vb, sizeof(vb), "constexpr int kJitVUpdate = %d;\n\n", f.v_update);
         s += vb;
     }
     s += "struct JitDyn {\n";
-    s += std::string("    static constexpr bool kDrive = ") + (drive ? "true" : "false") + ", kCable = " +
-         (cable ? "true" : "false") + ";\n";
+    auto tf = [](bool x) { return x ? "true" : "false"; };
+    s += std::string("    static constexpr bool kDrive = ") + tf(f.drive) + ", kCable = " + tf(f.cable) +
+         ", kSynCurrent = " + tf(f.syn_current) + ", kCompound = " + tf(f.compound) + ";\n";
     s += "    template <int MAXG, int PREC>\n";
     s += "    __device__ __forceinline__ void load(int mid, const NeuronParams& P, int64_t i, State<MAXG, PREC>& s) const\n    {\n";
     s += dispatch("load_conductances(M, P.gbar, P.N, i, s)");
@@ -292,14 +293,14 @@ int block_for(int64_t N)
 
 namespace hh {
 
-bool jit_get(const DevModels& M, const bool* installed, int precision, int v_update, bool drive, bool cable,
-             JitKernels* out, std::string* err)
+bool jit_get(const DevModels& M, const bool* installed, int precision, const JitFlags& f, JitKernels* out,
+             std::string* err)
 {
     int max_gates = 1;
     for (int k = 0; k < kMaxModels; ++k)
         if (installed[k] && M.m[k].n_gates > max_gates)
             max_gates = M.m[k].n_gates;
-    const std::string src = generate(M, installed, precision, max_gates, v_update, drive, cable);
+    const std::string src = generate(M, installed, precision, max_gates, f);
     if (const char* path = getenv("HH_JIT_DUMP")) {
         if (FILE* f = fopen(path, "w")) {
             fwrite(src.data(), 1, src.size(), f);

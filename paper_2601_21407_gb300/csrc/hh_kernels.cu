@@ -24,7 +24,7 @@ namespace {
 
 // Dynamics read from a model table in the kernel parameters.
 struct TableDyn {
-    static constexpr bool kDrive = true, kCable = true;
+    static constexpr bool kDrive = true, kCable = true, kSynCurrent = true, kCompound = true;
     const DevModels& Ms;
     template <int MAXG, int PREC>
     __device__ __forceinline__ void load(int mid, const NeuronParams& P, int64_t i,

@@ -80,7 +80,11 @@ class hh_net_desc(C.Structure):
                 ("E_I", C.c_float), ("delay_steps", C.c_int32), ("area_cm2", C.c_float),
                 ("bg_rate_hz", C.c_float), ("bg_sources", C.c_int32), ("bg_weight_nS", C.c_float),
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("sin_amp", C.c_void_p),
-                ("sin_freq_hz", C.c_void_p), ("sin_phase", C.c_void_p), ("morph", C.POINTER(hh_morphology))]
+                ("sin_freq_hz", C.c_void_p), ("sin_phase", C.c_void_p), ("morph", C.POINTER(hh_morphology)),
+                ("syn_mode", C.c_int32), ("bg_weight_sd", C.c_float)]
+
+
+HH_SYN_CONDUCTANCE, HH_SYN_CURRENT = 0, 1
 
 
 class hh_spike(C.Structure):
@@ -349,7 +353,7 @@ class Network:
     def __init__(self, V0, dt, *, I_const=None, model_id=None, csr=None, inh=None, syn=None,
                  delay_steps=1, bg=None, seed=0, theta=0.0, precision=HH_PREC_FAST,
                  v_update=HH_V_EXP_EULER, stream=None, n_nets=1, net_offsets=None,
-                 kernels=HH_KERNELS_SPECIALISED, drive=None, morph=None):
+                 kernels=HH_KERNELS_SPECIALISED, drive=None, morph=None, syn_mode=HH_SYN_CONDUCTANCE):
         d = hh_net_desc()
         self._keep = []
         V0 = self._f32(V0)
@@ -391,6 +395,8 @@ class Network:
         d.delay_steps = delay_steps
         if bg:
             d.bg_rate_hz, d.bg_sources, d.bg_weight_nS = bg["rate_hz"], bg["K"], bg["w"]
+            d.bg_weight_sd = bg.get("sd", 0.0)
+        d.syn_mode = syn_mode
         d.seed = seed
         d.stream = stream
         if drive is not None:

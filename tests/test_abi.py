@@ -49,6 +49,7 @@ int main(void){
    offsetof(hh_net_desc, seed), offsetof(hh_net_desc, stream), offsetof(hh_model_desc, ca_tau));
  printf("%zu %zu %zu %zu\\n", offsetof(hh_net_desc, V0), offsetof(hh_net_desc, sin_phase),
    offsetof(hh_net_desc, morph), sizeof(hh_morphology));
+ printf("%zu %zu\\n", offsetof(hh_net_desc, bg_weight_sd), sizeof(hh_net_desc));
  printf("%zu %zu\\n", sizeof(hh_peaks), offsetof(hh_peaks, rcp_per_s));
  printf("%zu %zu\\n", sizeof(hh_grads), offsetof(hh_grads, dX));
  return 0; }
@@ -65,6 +66,7 @@ int main(void){
             hh.hh_net_desc.seed.offset, hh.hh_net_desc.stream.offset,
             hh.hh_model_desc.ca_tau.offset, hh.hh_net_desc.V0.offset, hh.hh_net_desc.sin_phase.offset,
             hh.hh_net_desc.morph.offset, C.sizeof(hh.hh_morphology),
+            hh.hh_net_desc.bg_weight_sd.offset, C.sizeof(hh.hh_net_desc),
             C.sizeof(hh.hh_peaks), hh.hh_peaks.rcp_per_s.offset,
             C.sizeof(hh.hh_grads), hh.hh_grads.dX.offset]
     assert got == want
