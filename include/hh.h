@@ -376,6 +376,25 @@ hh_status hh_reset(hh_net* net, const float* V0);
 hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* spk_idx,
                           int64_t n_spk, int32_t n_window, int64_t* sum_E, int64_t* sum_I);
 
+/* Pull routing of dense windows (Methods, "Cerebral cortex network": the
+ * delayed delivery of spikes over the synapse graph).  A window of the
+ * window schedule in which at least min_spikes spikes occurred is routed by
+ * a pull over the in-CSR (every postsynaptic row read once, one 64-bit
+ * atomic per nonzero (step, E/I) sum of a row) instead of the push over the
+ * out-CSR (one atomic per synaptic event); both give the same delay-line
+ * bits, since the fixed-point sums are exact.  Possible for networks with
+ * synapses, at most 65,536 neurons and windows of at most 64 steps
+ * (delay_steps <= 129).  Off by default (on GB300 the pull costs about as
+ * much as the push even for windows in which half the network spikes).
+ *   min_spikes: >= 0 the threshold (0: every window with a spike), < 0 off.
+ * The first call with min_spikes >= 0 builds the in-CSR (8 bytes per
+ * synapse, from the out-CSR) and the last-spike tables; it is synchronous.
+ * Takes effect at the next hh_step_n; the persistent schedule and
+ * hh_route_spikes always push.  Errors: HH_EINVAL (net NULL),
+ * HH_EUNSUPPORTED (min_spikes >= 0 for a network that cannot pull),
+ * HH_ENOMEM, HH_ECUDA. */
+hh_status hh_set_route_pull(hh_net* net, int64_t min_spikes);
+
 /* ------------------------------------------------------------------ */
 /* Learned multi-step surrogate                                         */
 /* ------------------------------------------------------------------ */

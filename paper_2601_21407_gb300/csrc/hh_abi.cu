@@ -101,6 +101,15 @@ struct hh_net {
     int64_t* ring = nullptr;  // [R][N][2]: {E, I} per neuron and slot
     int32_t D = 1, R = 1;
     int32_t route_segs = 1;  // most 256-synapse segments in one out-CSR row
+    // pull routing of dense windows (networks of at most 65,536 neurons whose
+    // windows have at most 64 steps): the in-CSR as 8-byte records (16-bit
+    // presynaptic index, fixed-point weight in 16-bit parts) and the
+    // last-spike tables the window kernels write
+    std::vector<int64_t> in_ptr_host;  // the caller's row_ptr where pull routing is possible
+    int64_t* in_ptr = nullptr;
+    uint2* in_rec = nullptr;
+    uint8_t* last_spk = nullptr;
+    int64_t pull_min = -1;
     float tau_E = 1.0f, tau_I = 1.0f, E_E = 0.0f, E_I = 0.0f, area = 1.0f;
 
     // background
@@ -321,6 +330,7 @@ struct hh_net {
         p.status = status;
         p.ring = ring;
         p.R = R;
+        p.last_spk = in_rec && pull_min >= 0 ? last_spk : nullptr;
         p.E_E = E_E;
         p.E_I = E_I;
         p.decE = (float)std::exp(-dt / (double)tau_E);
@@ -363,6 +373,11 @@ struct hh_net {
         r.open_loop = 0;
         r.n_window = 0;
         r.segs = route_segs;
+        r.in_ptr = in_ptr;
+        r.in_rec = in_rec;
+        r.last_spk = last_spk;
+        r.pull_min = in_rec ? pull_min : -1;
+        r.pull_w = D >= 2 ? D / 2 : D;
         return r;
     }
 };
@@ -872,12 +887,21 @@ hh_status build_network(const hh_net_desc* d, hh_net* n)
                 rc = fail(HH_ECUDA, "filling the out-CSR: %s", cudaGetErrorString(e));
                 break;
             }
+            // pull routing is possible for windows of D/2 steps (1 step when
+            // D = 1) of at most kPullMaxW steps; its in-CSR is built from the
+            // out-CSR when it is first asked for (hh_set_route_pull)
+            const int32_t Wnet = n->D >= 2 ? n->D / 2 : n->D;
+            if (N <= hh::kPullMaxN && Wnet <= hh::kPullMaxW)
+                n->in_ptr_host = rp;
         } while (0);
         cleanup();
         if (rc != HH_OK)
             return rc;
         if (d->is_inhibitory) {
-            HH_CUDA(n->alloc(&n->inh, N));
+            // padded to the last-spike tables' row (zeros), read 16 at a time
+            const size_t Np = (size_t)hh::pull_stride(N);
+            HH_CUDA(n->alloc(&n->inh, Np));
+            HH_CUDA(cudaMemsetAsync(n->inh, 0, Np, st));
             HH_CUDA(copy_in(n->inh, d->is_inhibitory, (size_t)N, st));
         }
     }
@@ -1253,13 +1277,15 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
                     if ((e = cudaEventRecord(net->ev_neuron[slot], net->st)) != cudaSuccess ||
                         (e = cudaStreamWaitEvent(net->st_route, net->ev_neuron[slot], 0)) != cudaSuccess ||
                         (e = timed_on(net->st_route, HH_KERNEL_ROUTE, [&] {
-                             return hh::launch_route_window(rp, net->list, slot, net->st_route);
+                             return hh::launch_route_window(rp, net->list, slot, net->t + w0, W, net->st_route);
                          })) != cudaSuccess ||
                         (e = cudaEventRecord(net->ev_route[slot], net->st_route)) != cudaSuccess)
                         return e;
                     last_route = gw;
                 } else if (net->has_syn) {
-                    e = timed(HH_KERNEL_ROUTE, [&] { return hh::launch_route_window(rp, net->list, slot, net->st); });
+                    e = timed(HH_KERNEL_ROUTE, [&] {
+                        return hh::launch_route_window(rp, net->list, slot, net->t + w0, W, net->st);
+                    });
                 } else {
                     e = cudaMemsetAsync(net->list.counter + slot, 0, sizeof(int32_t), net->st);
                 }
@@ -1525,6 +1551,64 @@ hh_status hh_surrogate_enable(hh_net* net, int32_t enable)
     net->sur_on = enable != 0;
     if (net->sur)
         HH_CUDA(hh::surrogate_reset_stats(net->sur, net->st));
+    return HH_OK;
+}
+
+hh_status hh_set_route_pull(hh_net* net, int64_t min_spikes)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (min_spikes < 0) {
+        net->pull_min = -1;
+        return HH_OK;
+    }
+    if (!net->has_syn || net->in_ptr_host.empty())
+        return fail(HH_EUNSUPPORTED, "pull routing needs synapses, at most %lld neurons and windows of at most %d "
+                    "steps", (long long)hh::kPullMaxN, hh::kPullMaxW);
+    if (!net->in_rec) {
+        // the in-CSR from the out-CSR (k_fill_out run on the out-CSR
+        // transposes it back; the order inside a row is free), then its
+        // records; the last-spike tables
+        const int64_t N = net->N, S = net->S;
+        const cudaStream_t st = net->st;
+        const size_t Np = (size_t)hh::pull_stride(N);
+        int32_t* col = nullptr;
+        float* w = nullptr;
+        unsigned long long* cursor = nullptr;
+        cudaError_t e;
+        hh_status rc = HH_OK;
+        if ((e = net->alloc(&net->in_ptr, N + 1)) != cudaSuccess ||
+            (e = net->alloc(&net->in_rec, S + 8)) != cudaSuccess ||
+            (e = net->alloc(&net->last_spk, hh::kListSlots * Np)) != cudaSuccess ||
+            (e = cudaMalloc(&col, S * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&w, S * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&cursor, N * sizeof(unsigned long long))) != cudaSuccess)
+            rc = fail(HH_ENOMEM, "allocating the in-CSR of pull routing: %s", cudaGetErrorString(e));
+        else if ((e = copy_in(net->in_ptr, net->in_ptr_host.data(), (size_t)N + 1, st)) != cudaSuccess ||
+                 (e = copy_in(reinterpret_cast<int64_t*>(cursor), net->in_ptr_host.data(), (size_t)N, st)) !=
+                     cudaSuccess ||
+                 (e = hh::launch_fill_out(net->out_ptr, net->out_post, net->out_w, N, cursor, col, w, st)) !=
+                     cudaSuccess ||
+                 (e = hh::launch_pull_records(col, w, S, net->in_rec, st)) != cudaSuccess ||
+                 (e = cudaMemsetAsync(net->in_rec + S, 0, 8 * sizeof(uint2), st)) != cudaSuccess ||
+                 (e = cudaMemsetAsync(net->last_spk, hh::kPullNone, hh::kListSlots * Np, st)) != cudaSuccess ||
+                 (e = hh::route_pull_prepare()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            rc = fail(HH_ECUDA, "building the in-CSR of pull routing: %s", cudaGetErrorString(e));
+        cudaStreamSynchronize(st);
+        for (void* q : {(void*)col, (void*)w, (void*)cursor})
+            if (q)
+                cudaFree(q);
+        if (rc != HH_OK) {
+            net->free_tracked(net->in_ptr);
+            net->free_tracked(net->in_rec);
+            net->free_tracked(net->last_spk);
+            net->in_ptr = nullptr;
+            net->in_rec = nullptr;
+            net->last_spk = nullptr;
+            return rc;
+        }
+    }
+    net->pull_min = min_spikes;
     return HH_OK;
 }
 

@@ -118,6 +118,10 @@ struct NeuronParams {
     // load per neuron-step), fixed point 2^-32 nS; R N < 2^32
     int64_t* ring;
     int32_t R;        // ring slots (= delay steps)
+    // [kListSlots][pull_stride(N)] or nullptr: per window list slot, the
+    // window-relative step of each neuron's last spike in the window
+    // (kPullNone: none), read by the pull routing of dense windows
+    uint8_t* last_spk;
     float E_E, E_I, decE, decI, to_mS;
     // background
     int32_t bg_n;     // thresholds below 2^32 (0 = off); the count of a step is
@@ -160,7 +164,41 @@ struct RouteParams {
     int32_t open_loop; // 1: destination is [n_window][N] linear, drop >= n_window
     int32_t n_window;
     int32_t segs;      // most 256-synapse segments of a row (route_items)
+    // pull routing of dense windows (nullptr in_rec: off): the in-CSR (rows =
+    // postsynaptic neuron) as one 8-byte record per synapse, {presynaptic
+    // index | p0 << 16, p1 | p2 << 16} with p0 + p1 2^16 + p2 2^32 the
+    // weight in fixed point (nS_to_fixed), padded by 8 zero records; and the
+    // neurons' last-spike tables of the window lists
+    const int64_t* in_ptr;
+    const uint2* in_rec;
+    const uint8_t* last_spk;
+    int64_t pull_min;  // windows of at least this many spikes are pulled (< 0: never)
+    int32_t pull_w;    // the network's window steps (<= kPullMaxW): sums per replica 2 pull_w + 1
 };
+// Pull routing limits: 16-bit presynaptic indices, and the window-relative
+// step of a spike in 6 bits of its table entry (bit 7: inhibitory)
+constexpr int64_t kPullMaxN = 65536;
+constexpr int kPullMaxW = 64;
+constexpr uint8_t kPullNone = 0xff;
+constexpr int kPullWarps = 8;  // warps per routing block (256 threads)
+// A warp's (step, E/I) sums are kept as three 32-bit words of 16-bit parts
+// of the 48-bit fixed-point weights (a row of at most 32,767 synapses puts
+// at most ~4,100 parts below 2^16 into a word: below 2^29, no overflow), so
+// that a synapse adds with native 32-bit shared-
+// memory atomics; lane l adds into copy l mod kPullRep of the sums, so that
+// the lanes of a burst, whose synapses hit a few sums, do not serialise.
+constexpr int kPullRep = 8;
+// entries per list slot of the last-spike tables (16-byte rows)
+__host__ __device__ constexpr int64_t pull_stride(int64_t N) { return (N + 15) & ~(int64_t)15; }
+// 32-bit words of one copy of the sums: 3 per (step, E/I), plus one (odd:
+// the copies of a word fall in different banks)
+__host__ __device__ constexpr int32_t pull_copy_words(int32_t W) { return 6 * W + 1; }
+// dynamic shared memory of a routing block that may pull: the staged table
+// and the warps' copies of the sums
+__host__ __device__ constexpr size_t pull_smem_bytes(int64_t N, int32_t W)
+{
+    return (size_t)pull_stride(N) + (size_t)kPullWarps * kPullRep * pull_copy_words(W) * sizeof(uint32_t);
+}
 // Window spike lists used between the neuron and the routing kernels: three
 // slots (window index mod 3) so that a window's list can be routed while the
 // next window's neurons append to another slot.
@@ -823,47 +861,51 @@ __device__ __forceinline__ unsigned long long* route_dst(const RouteParams& RP, 
                                                  row * RP.N * RP.stride);
 }
 
+// One spike (presynaptic j at step t) delivered by the calling warp (j and
+// t uniform over it).
+__device__ __forceinline__ void route_one(const RouteParams& RP, int32_t j, int32_t t, int lane)
+{
+    if (j < 0 || j >= RP.N || t < 0)
+        return;
+    int64_t row;
+    if (RP.open_loop) {
+        row = (int64_t)t + RP.D;
+        if (row >= RP.n_window)
+            return;
+    } else {
+        row = ((int64_t)t + RP.D) % RP.R;
+    }
+    unsigned long long* dst = route_dst(RP, j, row);
+    const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
+    // 256 synapses per warp iteration, software-pipelined: the next chunk's
+    // (target, weight) loads are issued before this chunk's atomics, so two
+    // chunks are in flight per warp (the loop is latency-bound otherwise).
+    // Streaming (evict-first) loads: the rows are read once per spike and
+    // must not push the delay line out of L2.
+    int64_t base = e0 & ~(int64_t)3;
+    if (base >= e1)
+        return;
+    int4 pa, pb;
+    float4 wa, wb;
+    load_chunk(RP, base + 4 * lane, e1, pa, pb, wa, wb);
+    for (; base < e1; base += 256) {
+        int4 qa, qb;
+        float4 va, vb;
+        load_chunk(RP, base + 256 + 4 * lane, e1, qa, qb, va, vb);
+        deliver_chunk(dst, RP.stride, base + 4 * lane, e0, e1, pa, pb, wa, wb);
+        pa = qa;
+        pb = qb;
+        wa = va;
+        wb = vb;
+    }
+}
+
 __device__ __forceinline__ void route_spikes(const RouteParams& RP, const int32_t* __restrict__ st,
                                              const int32_t* __restrict__ ix, int64_t n, int64_t warp, int64_t nw)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t sp = warp; sp < n; sp += nw) {
-        const int32_t j = __ldcg(ix + sp);
-        const int32_t t = __ldcg(st + sp);
-        if (j < 0 || j >= RP.N || t < 0)
-            continue;
-        int64_t row;
-        if (RP.open_loop) {
-            row = (int64_t)t + RP.D;
-            if (row >= RP.n_window)
-                continue;
-        } else {
-            row = ((int64_t)t + RP.D) % RP.R;
-        }
-        unsigned long long* dst = route_dst(RP, j, row);
-        const int64_t e0 = RP.out_ptr[j], e1 = RP.out_ptr[j + 1];
-        // 256 synapses per warp iteration, software-pipelined: the next
-        // chunk's (target, weight) loads are issued before this chunk's
-        // atomics, so two chunks are in flight per warp (the loop is
-        // latency-bound otherwise).  Streaming (evict-first) loads: the rows
-        // are read once per spike and must not push the delay line out of L2.
-        int64_t base = e0 & ~(int64_t)3;
-        if (base >= e1)
-            continue;
-        int4 pa, pb;
-        float4 wa, wb;
-        load_chunk(RP, base + 4 * lane, e1, pa, pb, wa, wb);
-        for (; base < e1; base += 256) {
-            int4 qa, qb;
-            float4 va, vb;
-            load_chunk(RP, base + 256 + 4 * lane, e1, qa, qb, va, vb);
-            deliver_chunk(dst, RP.stride, base + 4 * lane, e0, e1, pa, pb, wa, wb);
-            pa = qa;
-            pb = qb;
-            wa = va;
-            wb = vb;
-        }
-    }
+    for (int64_t sp = warp; sp < n; sp += nw)
+        route_one(RP, __ldcg(ix + sp), __ldcg(st + sp), lane);
 }
 
 // The same delivery split into items of (spike, 256-synapse segment): item
@@ -901,6 +943,221 @@ __device__ __forceinline__ void route_items(const RouteParams& RP, const int32_t
         if (q >= S) {
             q -= S;
             ++sp;
+        }
+    }
+}
+
+// Pull routing of a dense window: the same sums as the push above (fixed-
+// point addition is exact, so the order does not matter).  Every row of the
+// in-CSR (rows = postsynaptic neuron) is read once.  When a good part of the
+// network spikes in one window, streaming the in-CSR (8 bytes a synapse)
+// costs less than one L2 atomic per synaptic event.
+//   a. every block stages the window's last-spike table, with the
+//      presynaptic type in bit 7, in shared memory;
+//   b. warp per target row: the row's records (presynaptic index and
+//      weight) are streamed (8 synapses a lane, 256-synapse chunks, two
+//      chunks ahead, across row ends);
+//      a synapse whose source spiked adds its fixed-point weight to the
+//      warp's shared-memory sum for (spike step, E/I) (in the lane's copy),
+//      and the row's nonzero sums go to the delay line, one 64-bit atomic
+//      each;
+//   c. spikes that are not the last of their neuron in the window (a neuron
+//      that fired twice) are pushed.
+// Entered by whole blocks (the condition is uniform over the grid).
+
+// bit 7 of every byte of x that is nonzero
+__device__ __forceinline__ uint32_t nonzero_bytes_b7(uint32_t x)
+{
+    return (((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;
+}
+
+// One 256-synapse chunk of a row in flight: the lane's 8 records from ea =
+// base + 8 lane (zeros past the row; the records are padded by 8).  The
+// loads are volatile so that they are issued here, two chunks ahead of
+// their use, and not moved to the uses behind the spike test.
+struct PullChunk {
+    uint4 r[4];               // records ea .. ea + 7, two per vector
+    int64_t i, e0, e1, base;  // row, its bounds, chunk start (i < 0: none)
+};
+
+__device__ __forceinline__ void pull_issue(const RouteParams& RP, int64_t i, int64_t e0, int64_t e1, int64_t base,
+                                           int lane, PullChunk& c)
+{
+    c.i = i;
+    c.e0 = e0;
+    c.e1 = e1;
+    c.base = base;
+    const int64_t ea = base + 8 * lane;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        c.r[q] = make_uint4(0, 0, 0, 0);
+        if (ea < e1) {
+            const uint2* pr = RP.in_rec + ea + 2 * q;
+            asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(c.r[q].x), "=r"(c.r[q].y), "=r"(c.r[q].z), "=r"(c.r[q].w)
+                         : "l"(pr));
+        }
+    }
+}
+
+// The chunk cursor of a warp over its rows i0, i0 + nw, ... (empty rows
+// skipped), with the bounds of the row after the current one read ahead.
+struct PullCursor {
+    int64_t i, e0, e1, base;  // next chunk to issue (i >= N: done)
+    int64_t ni, ne0, ne1;     // the row after i
+};
+
+__device__ __forceinline__ void pull_row_bounds(const RouteParams& RP, int64_t i, int64_t& e0, int64_t& e1)
+{
+    e0 = 0;
+    e1 = 0;
+    if (i < RP.N) {
+        e0 = __ldg(RP.in_ptr + i);
+        e1 = __ldg(RP.in_ptr + i + 1);
+    }
+}
+
+__device__ __forceinline__ void pull_advance_row(const RouteParams& RP, int64_t nw, PullCursor& k)
+{
+    for (;;) {
+        k.i = k.ni;
+        k.e0 = k.ne0;
+        k.e1 = k.ne1;
+        k.base = k.e0 & ~(int64_t)7;
+        k.ni = k.i + nw;
+        pull_row_bounds(RP, k.ni, k.ne0, k.ne1);
+        if (k.i >= RP.N || k.base < k.e1)
+            return;
+    }
+}
+
+// issue the cursor's chunk into c and advance the cursor
+__device__ __forceinline__ void pull_next(const RouteParams& RP, int64_t nw, int lane, PullCursor& k, PullChunk& c)
+{
+    if (k.i >= RP.N) {
+        c.i = -1;
+        return;
+    }
+    pull_issue(RP, k.i, k.e0, k.e1, k.base, lane, c);
+    k.base += 256;
+    if (k.base >= k.e1)
+        pull_advance_row(RP, nw, k);
+}
+
+// records lo .. hi - 1 of a lane's 8 belong to the row
+__device__ __forceinline__ void pull_chunk(const uint8_t* tab, uint32_t* mine, int32_t lo, int32_t hi,
+                                           const uint4 (&r)[4])
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t x = (q & 1) ? r[q >> 1].z : r[q >> 1].x;
+        const uint32_t y = (q & 1) ? r[q >> 1].w : r[q >> 1].y;
+        const uint32_t v = tab[x & 0xffffu];  // index < N: another row's record or padding 0
+        if (q >= lo && q < hi && v != kPullNone) {
+            uint32_t* a = mine + 3 * (2 * (v & 63u) + (v >> 7));
+            atomicAdd(a, x >> 16);
+            atomicAdd(a + 1, y & 0xffffu);
+            atomicAdd(a + 2, y >> 16);
+        }
+    }
+}
+
+__device__ __forceinline__ void route_pull(const RouteParams& RP, const int32_t* __restrict__ st,
+                                           const int32_t* __restrict__ ix, int64_t n, int64_t t0, int32_t W,
+                                           int32_t lslot, unsigned char* smem)
+{
+    const int64_t N = RP.N;
+    const int64_t Np = pull_stride(N);
+    const int lane = threadIdx.x & 31;
+    const int32_t rs = pull_copy_words(RP.pull_w);
+    uint8_t* tab = smem;
+    uint32_t* acc = reinterpret_cast<uint32_t*>(smem + Np) + (threadIdx.x >> 5) * kPullRep * rs;
+    uint32_t* mine = acc + (lane % kPullRep) * rs;
+    // a. 16 entries per load (tables and inh hold Np entries)
+    const uint4* last = reinterpret_cast<const uint4*>(RP.last_spk + (int64_t)lslot * Np);
+    const uint4* inh = reinterpret_cast<const uint4*>(RP.inh);
+    for (int64_t q = threadIdx.x; q < Np / 16; q += blockDim.x) {
+        uint4 v = __ldcg(last + q);
+        if (inh) {  // sets bit 7 of an inhibitory neuron's entry; kPullNone stays
+            const uint4 h = __ldg(inh + q);
+            v.x |= nonzero_bytes_b7(h.x);
+            v.y |= nonzero_bytes_b7(h.y);
+            v.z |= nonzero_bytes_b7(h.z);
+            v.w |= nonzero_bytes_b7(h.w);
+        }
+        reinterpret_cast<uint4*>(tab)[q] = v;
+    }
+    for (int q = lane; q < kPullRep * rs; q += 32)
+        acc[q] = 0u;
+    __syncthreads();
+    // b.
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the row's sums (all copies) to the delay line, then cleared
+    auto flush = [&](int64_t i) {
+        __syncwarp();
+        for (int q = lane; q < 2 * W; q += 32) {
+            unsigned long long a = 0ull;
+#pragma unroll
+            for (int r = 0; r < kPullRep; ++r) {
+                uint32_t* c = acc + r * rs + 3 * q;
+                a += (unsigned long long)c[0] + ((unsigned long long)c[1] << 16) + ((unsigned long long)c[2] << 32);
+                c[0] = 0u;
+                c[1] = 0u;
+                c[2] = 0u;
+            }
+            if (a) {
+                const int64_t row = (t0 + (q >> 1) + RP.D) % RP.R;
+                atomicAdd(reinterpret_cast<unsigned long long*>((q & 1) ? RP.ringI : RP.ringE) +
+                              (row * N + i) * RP.stride,
+                          a);
+            }
+        }
+        __syncwarp();
+    };
+    auto use = [&](const PullChunk& c) {
+        const int64_t ea = c.base + 8 * lane;
+        const int32_t lo = (int32_t)max(min(c.e0 - ea, (int64_t)8), (int64_t)0);
+        const int32_t hi = (int32_t)max(min(c.e1 - ea, (int64_t)8), (int64_t)0);
+        pull_chunk(tab, mine, lo, hi, c.r);
+        if (c.base + 256 >= c.e1)  // the row's last chunk
+            flush(c.i);
+    };
+    // a stream of chunks over the warp's rows, two chunks in flight (also
+    // across row ends)
+    PullCursor k;
+    k.ni = warp;
+    pull_row_bounds(RP, k.ni, k.ne0, k.ne1);
+    pull_advance_row(RP, nw, k);
+    PullChunk A, B;
+    pull_next(RP, nw, lane, k, A);
+    pull_next(RP, nw, lane, k, B);
+    while (A.i >= 0) {
+        use(A);
+        pull_next(RP, nw, lane, k, A);
+        if (B.i < 0)
+            break;
+        use(B);
+        pull_next(RP, nw, lane, k, B);
+    }
+    // c. 32 list entries per warp and round
+    for (int64_t b0 = warp * 32; b0 < n; b0 += nw * 32) {
+        const int64_t sp = b0 + lane;
+        int32_t j = -1, t = -1;
+        bool extra = false;
+        if (sp < n) {
+            j = __ldcg(ix + sp);
+            t = __ldcg(st + sp);
+            if (j >= 0 && j < N && t >= 0) {
+                const uint32_t v = tab[j];
+                extra = t < t0 || t >= t0 + W || v == kPullNone || (int64_t)(v & 63u) != t - t0;
+            }
+        }
+        unsigned m = __ballot_sync(kFull, extra);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            route_one(RP, __shfl_sync(kFull, j, l), __shfl_sync(kFull, t, l), lane);
         }
     }
 }
@@ -1096,6 +1353,8 @@ __device__ __forceinline__ void window_steps_bg(const Dyn& dyn, int mid, const N
         if (b) {
             list_append_b(b, spk, (int32_t)t, (int32_t)i, L.counter + lslot, lstep, lidx, L.cap);
             record_spikes_b(b, spk, (int32_t)t, (int32_t)i, P.theta, Vt, s.V, R, P.status);
+            if (spk && P.last_spk)
+                P.last_spk[lslot * pull_stride(P.N) + i] = (uint8_t)k;
         }
         if (slot >= 0)
             V_trace[(int64_t)k * R.n_trace + slot] = s.V;
@@ -1225,6 +1484,8 @@ __device__ __forceinline__ void window_body(const Dyn& dyn, const NeuronParams& 
         ring_preload(P, i, t0, rq);
     if (gi == 0)
         L.counter[parity + 1 == kListSlots ? 0 : parity + 1] = 0;  // next window's slot (its reader has finished)
+    if (valid && P.last_spk)
+        P.last_spk[parity * pull_stride(P.N) + i] = kPullNone;  // its reader finished before this launch
     const int mid = P.model_id ? P.model_id[i] : 0;
     State<MAXG, PREC> s;
     s.poly = tab;

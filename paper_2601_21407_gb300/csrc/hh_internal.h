@@ -34,13 +34,15 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
                               int64_t t0, int32_t W, int32_t window_parity,
                               const float* I_steps, const RecordParams& R,
                               const SpikeList& L, cudaStream_t st);
-cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L,
-                                int32_t window_parity, cudaStream_t st);
+cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity, int64_t t0,
+                                int32_t W, cudaStream_t st);
+cudaError_t route_pull_prepare();
 cudaError_t launch_route_list(const RouteParams& RP, const int32_t* step, const int32_t* idx,
                               int64_t n, cudaStream_t st);
 cudaError_t launch_csr_check(const int32_t* col, const float* w, int64_t S, int64_t N,
                              int32_t* flag, cudaStream_t st);
 cudaError_t launch_count_pre(const int32_t* col, int64_t S, int32_t* cnt, cudaStream_t st);
+cudaError_t launch_pull_records(const int32_t* col, const float* w, int64_t S, uint2* out, cudaStream_t st);
 cudaError_t launch_fill_out(const int64_t* row_ptr, const int32_t* col, const float* w,
                             int64_t N, unsigned long long* cursor, int32_t* out_post,
                             float* out_w, cudaStream_t st);

@@ -315,6 +315,15 @@ bool jit_get(const DevModels& M, const bool* installed, int precision, const Jit
     out->window = e->kernels[1];
     out->indexed = e->kernels[2];
     out->persistent = e->kernels[3];
+    // the routing kernel co-running with the window kernel may hold shared
+    // memory (pull routing); the same carveout lets their blocks share SMs
+    const cudaError_t ce = cudaFuncSetAttribute((const void*)out->window,
+                                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                cudaSharedmemCarveoutMaxShared);
+    if (ce != cudaSuccess) {
+        *err = std::string("setting the window kernel's carveout: ") + cudaGetErrorString(ce);
+        return false;
+    }
     return true;
 }
 

@@ -62,16 +62,25 @@ __global__ void __launch_bounds__(128) k_net_window(const __grid_constant__ DevM
     window_body<MAXG, PREC, 1>(TableDyn{Ms}, P, t0, W, I_steps, R, L, parity, 0);
 }
 
-// Spike routing of a list whose length is read on the device.
+// Spike routing of a list whose length is read on the device.  A window of
+// the window schedule (W > 0: steps t0 .. t0 + W - 1, list slot lslot) with
+// at least RP.pull_min spikes is pulled over the in-CSR when the network
+// keeps one (dynamic shared memory: pull_smem_bytes(N)).
 __global__ void __launch_bounds__(256) k_route(const __grid_constant__ RouteParams RP,
                                                const int32_t* __restrict__ st,
                                                const int32_t* __restrict__ ix,
                                                const int32_t* __restrict__ n_dev, int64_t n_host,
-                                               int64_t cap)
+                                               int64_t cap, int64_t t0, int32_t W, int32_t lslot)
 {
     int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     if (n > cap)
         n = cap;
+    if (RP.in_rec && RP.last_spk && W > 0 && W <= RP.pull_w && RP.pull_min >= 0 && n > 0 && n >= RP.pull_min &&
+        blockDim.x == 32 * kPullWarps) {
+        extern __shared__ __align__(16) unsigned char pull_smem[];
+        route_pull(RP, st, ix, n, t0, W, lslot, pull_smem);
+        return;
+    }
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // Up to 16 segments per warp, every (spike, 256-synapse segment) item is
@@ -153,6 +162,19 @@ __global__ void k_fill_out(const int64_t* __restrict__ row_ptr, const int32_t* _
             out_post[pos] = (int32_t)r;
             out_w[pos] = w[e];
         }
+    }
+}
+
+// pull-routing records of the in-CSR: presynaptic index (checked to lie in
+// [0, N), N <= 65536) and the three 16-bit parts of the weight's fixed-point
+// value (the value the push adds)
+__global__ void k_pull_records(const int32_t* __restrict__ col, const float* __restrict__ w, int64_t S,
+                               uint2* out)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < S; e += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long f = nS_to_fixed(w[e]);
+        out[e] = make_uint2((uint32_t)col[e] | ((uint32_t)(f & 0xffffu) << 16),
+                            (uint32_t)((f >> 16) & 0xffffu) | ((uint32_t)(f >> 32) << 16));
     }
 }
 
@@ -241,14 +263,29 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
     return cudaGetLastError();
 }
 
-cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity,
-                                cudaStream_t st)
+// the shared memory a pulling routing block may take, and the largest
+// shared-memory carveout, which the window kernels it co-runs with prefer as
+// well (blocks of kernels with different carveouts do not share an SM); set
+// on the current device where a network that may pull is created
+cudaError_t route_pull_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_route, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pull_smem_bytes(kPullMaxN, kPullMaxW));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_route, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity, int64_t t0,
+                                int32_t W, cudaStream_t st)
 {
     // two resident blocks per SM whose warps loop over the window's spikes:
     // routing overlaps the next window's neuron kernel, whose blocks must
     // still find registers on every SM
-    k_route<<<152 * 2, 256, 0, st>>>(RP, L.step + parity * L.cap, L.idx + parity * L.cap, L.counter + parity, 0,
-                                     L.cap);
+    const size_t smem = RP.in_rec && RP.pull_min >= 0 ? pull_smem_bytes(RP.N, RP.pull_w) : 0;
+    k_route<<<152 * 2, 32 * kPullWarps, smem, st>>>(RP, L.step + parity * L.cap, L.idx + parity * L.cap,
+                                                   L.counter + parity, 0, L.cap, t0, W, parity);
     return cudaGetLastError();
 }
 
@@ -257,7 +294,7 @@ cudaError_t launch_route_list(const RouteParams& RP, const int32_t* step, const 
 {
     if (n <= 0)
         return cudaSuccess;
-    k_route<<<152 * 8, 256, 0, st>>>(RP, step, idx, nullptr, n, n);
+    k_route<<<152 * 8, 256, 0, st>>>(RP, step, idx, nullptr, n, n, 0, 0, 0);
     return cudaGetLastError();
 }
 
@@ -283,6 +320,14 @@ cudaError_t launch_fill_out(const int64_t* row_ptr, const int32_t* col, const fl
                             cudaStream_t st)
 {
     k_fill_out<<<152 * 8, 256, 0, st>>>(row_ptr, col, w, N, cursor, out_post, out_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pull_records(const int32_t* col, const float* w, int64_t S, uint2* out, cudaStream_t st)
+{
+    if (S <= 0)
+        return cudaSuccess;
+    k_pull_records<<<152 * 8, 256, 0, st>>>(col, w, S, out);
     return cudaGetLastError();
 }
 

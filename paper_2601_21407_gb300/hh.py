@@ -149,7 +149,7 @@ EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
            "hh_layer_forward", "hh_backward", "hh_backward_from", "hh_layer_readout", "hh_layer_destroy",
            "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks", "hh_set_wait_limits",
-           "hh_poly_fit"]
+           "hh_poly_fit", "hh_set_route_pull"]
 
 
 def lib_path() -> str:
@@ -213,6 +213,8 @@ def lib():
             L.hh_measure_peaks.argtypes = [P(hh_peaks), vp]
             L.hh_set_wait_limits.restype = C.c_int
             L.hh_set_wait_limits.argtypes = [C.c_int64, C.c_int64]
+            L.hh_set_route_pull.restype = C.c_int
+            L.hh_set_route_pull.argtypes = [vp, C.c_int64]
             L.hh_poly_fit.restype = C.c_int
             L.hh_poly_fit.argtypes = [P(hh_model_desc), C.c_double, vp, vp, vp, C.c_int64, vp]
             _lib = L
@@ -475,6 +477,11 @@ class Network:
 
     def profile(self, enable: bool):
         hh_profile(self.handle, enable)
+
+    def set_route_pull(self, min_spikes: int):
+        """Windows with at least min_spikes spikes are routed by a pull over
+        the in-CSR (0: every window, < 0: never); hh_set_route_pull."""
+        _check(lib().hh_set_route_pull(self.handle, int(min_spikes)))
 
     def kernel_times(self):
         """{"neuron": (launches, total_ms), "route": (...)} since profile(True)."""
