@@ -361,6 +361,66 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps,
  * delay line and the status word.  Asynchronous. */
 hh_status hh_reset(hh_net* net, const float* V0);
 
+/* Checkpoint and resume of the whole dynamic state of the integrator of
+ * Methods, Eq. hh_eq_full after a completed step (the paper describes no
+ * checkpoint format; this one is the library's own): the step index, V,
+ * every gate, Ca, g_E and g_I, the
+ * compensated low parts (HH_PREC_COMPENSATED), the delay line with the
+ * spikes still in flight, and the status word.  The background and the
+ * sinusoidal drive are functions of (seed, step, neuron), so a network
+ * restored at step t continues bit for bit as the saved one did, provided
+ * it was created from the same descriptor and given the same channels.
+ * The model tables, maximal conductances and currents are parameters, not
+ * state, and are not saved.
+ *
+ * The image is a 256-byte header followed by the arrays, each starting on
+ * a 256-byte boundary.  hh_state_size gives its size in bytes. */
+hh_status hh_state_size(const hh_net* net, size_t* bytes);
+
+/* Write the state image into dst (any memory the device can address:
+ * device, pinned or pageable host; cap bytes).  Synchronous: it returns
+ * once the image is complete.  Errors: HH_EINVAL (NULL, cap too small),
+ * HH_ECUDA. */
+hh_status hh_save_state(hh_net* net, void* dst, size_t cap);
+
+/* Replace the network's state by an image written by hh_save_state (any
+ * memory, n bytes).  The image must come from a network with the same
+ * neuron count, delay slots, precision and synapse / background layout
+ * (HH_EINVAL otherwise, with the mismatch in hh_last_error()).  The copy is
+ * asynchronous on the network's stream; src must stay valid until the
+ * stream reaches it.  Errors: HH_EINVAL, HH_ECUDA. */
+hh_status hh_load_state(hh_net* net, const void* src, size_t n);
+
+/* Launch shape of the specialised window schedule: threads per block of the
+ * neuron-window kernel (32, 64 or 128; 0 = the library's choice from N) and
+ * blocks per routing launch (1 .. 4,096; 0 = the default 304).  Results do
+ * not depend on it (delivery is order independent), only the speed.
+ * Errors: HH_EINVAL. */
+hh_status hh_set_launch_shape(hh_net* net, int32_t neuron_block, int32_t route_blocks);
+
+/* Autotuning of the launch shape for this network's size and activity (no
+ * counterpart in the paper, whose batched simulations run on its own
+ * operators; Results, large-scale and batched simulation): each
+ * candidate -- the library's default shape, reported as (0, 0), then
+ * neuron blocks 32, 64, 128 x routing grids of 152, 304, 608 blocks (one
+ * grid when the network has no synapses) -- advances the network by
+ * trial_steps from its current state twice (the first run compiles and
+ * captures, the second is timed with CUDA events), the state is restored
+ * after every run, and the fastest shape is installed if it beats the
+ * default by at least 2 % (else the default stays).  On return the
+ * network's state is the one it had on entry.
+ * Needs a network with synapses or background on the specialised kernels
+ * (HH_EUNSUPPORTED otherwise).  Synchronous.  rep may be NULL. */
+#define HH_TUNE_MAX 16
+typedef struct {
+    int32_t n;                          /* candidates tried */
+    int32_t best;                       /* index of the installed one */
+    int32_t neuron_block[HH_TUNE_MAX];
+    int32_t route_blocks[HH_TUNE_MAX];
+    float ms[HH_TUNE_MAX];              /* timed run of trial_steps steps */
+} hh_tune_report;
+hh_status hh_autotune(hh_net* net, int32_t trial_steps, hh_tune_report* rep);
+
 /* Open-loop spike routing (Methods, "Cerebral cortex network": synaptic
  * delays and E/IPSP filters; the spike-delivery step of the network):
  * for every spike (step s, neuron j) of the given list and every synapse

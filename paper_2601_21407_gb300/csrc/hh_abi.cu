@@ -138,6 +138,9 @@ struct hh_net {
     cudaStream_t st_own = nullptr;  // capture stream when the caller's is the legacy default stream
     cudaEvent_t ev_enter = nullptr, ev_leave = nullptr;
     int persistent_cap = -1;      // co-resident blocks of the persistent kernel (-1: not queried)
+    // launch shape of the specialised window schedule (hh_set_launch_shape,
+    // hh_autotune): neuron-window block size and routing grid, 0 = default
+    int32_t shape_block = 0, shape_route = 0;
 
     // learned surrogate
     hh::Surrogate* sur = nullptr;
@@ -1267,7 +1270,7 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
                     // depend only on routing launches the stream waited for
                     if (spec)
                         return hh::jit_launch_window(net->jit, p, net->t + w0, W, slot, Iw, Rw, net->list,
-                                                     pipe && net->has_syn ? 1 : 0, net->st);
+                                                     pipe && net->has_syn ? 1 : 0, net->shape_block, net->st);
                     return hh::launch_net_window(net->models, p, net->precision, net->t + w0, W, slot, Iw, Rw,
                                                  net->list, net->st);
                 });
@@ -1277,14 +1280,16 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
                     if ((e = cudaEventRecord(net->ev_neuron[slot], net->st)) != cudaSuccess ||
                         (e = cudaStreamWaitEvent(net->st_route, net->ev_neuron[slot], 0)) != cudaSuccess ||
                         (e = timed_on(net->st_route, HH_KERNEL_ROUTE, [&] {
-                             return hh::launch_route_window(rp, net->list, slot, net->t + w0, W, net->st_route);
+                             return hh::launch_route_window(rp, net->list, slot, net->t + w0, W, net->shape_route,
+                                                            net->st_route);
                          })) != cudaSuccess ||
                         (e = cudaEventRecord(net->ev_route[slot], net->st_route)) != cudaSuccess)
                         return e;
                     last_route = gw;
                 } else if (net->has_syn) {
                     e = timed(HH_KERNEL_ROUTE, [&] {
-                        return hh::launch_route_window(rp, net->list, slot, net->t + w0, W, net->st);
+                        return hh::launch_route_window(rp, net->list, slot, net->t + w0, W, net->shape_route,
+                                                       net->st);
                     });
                 } else {
                     e = cudaMemsetAsync(net->list.counter + slot, 0, sizeof(int32_t), net->st);
@@ -1330,6 +1335,8 @@ hh_status hh_step_n(hh_net* net, int32_t n_steps, const float* I_steps, const hh
             put(&cs, sizeof cs);
             put(&net->precision, sizeof net->precision);
             put(&net->models, sizeof net->models);
+            put(&net->shape_block, sizeof net->shape_block);
+            put(&net->shape_route, sizeof net->shape_route);
             cudaError_t e = cudaSuccess;
             if (!net->relaunch_graph(sig, net->st, &e)) {
                 e = cudaStreamBeginCapture(net->st, cudaStreamCaptureModeThreadLocal);
@@ -1391,6 +1398,239 @@ hh_status hh_reset(hh_net* net, const float* V0)
     net->t = 0;
     net->window_index = 0;
     return HH_OK;
+}
+
+namespace {
+
+// The state image: a 256-byte header, then the arrays in the order of
+// state_arrays(), each at a 256-byte boundary.
+constexpr uint64_t kStateMagic = 0x3145544154534848ull;  // "HHSTATE1"
+struct StateHeader {
+    uint64_t magic;
+    uint64_t bytes;
+    int64_t N, t, window_index;
+    int32_t R, max_gates, precision, has_lo, has_ring, has_syn;
+    uint8_t pad[256 - 8 * 5 - 4 * 6];
+};
+static_assert(sizeof(StateHeader) == 256, "state header");
+
+struct StateArray {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<StateArray> state_arrays(const hh_net* n)
+{
+    const size_t N = (size_t)n->N, G = (size_t)hh::kMaxGates;
+    std::vector<StateArray> a = {{n->V, N * 4}, {n->Ca, N * 4}, {n->gE, N * 4}, {n->gI, N * 4},
+                                 {n->P, G * N * 4}, {n->status, 4}};
+    if (n->Vlo) {
+        a.push_back({n->Vlo, N * 4});
+        a.push_back({n->Plo, G * N * 4});
+    }
+    if (n->ring) {
+        a.push_back({n->ring, (size_t)n->R * N * 2 * sizeof(int64_t)});
+        a.push_back({n->list.counter, hh::kListSlots * sizeof(int32_t)});
+    }
+    return a;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t state_bytes(const hh_net* n)
+{
+    size_t b = sizeof(StateHeader);
+    for (const StateArray& x : state_arrays(n))
+        b += round256(x.bytes);
+    return b;
+}
+
+StateHeader state_header(const hh_net* n)
+{
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.bytes = state_bytes(n);
+    h.N = n->N;
+    h.t = n->t;
+    h.window_index = n->window_index;
+    h.R = n->ring ? n->R : 0;
+    h.max_gates = hh::kMaxGates;
+    h.precision = n->precision;
+    h.has_lo = n->Vlo != nullptr;
+    h.has_ring = n->ring != nullptr;
+    h.has_syn = n->has_syn;
+    return h;
+}
+
+}  // namespace
+
+hh_status hh_state_size(const hh_net* net, size_t* bytes)
+{
+    if (!net || !bytes)
+        return fail(HH_EINVAL, "net and bytes must not be NULL");
+    *bytes = state_bytes(net);
+    return HH_OK;
+}
+
+hh_status hh_save_state(hh_net* net, void* dst, size_t cap)
+{
+    if (!net || !dst)
+        return fail(HH_EINVAL, "net and dst must not be NULL");
+    const StateHeader h = state_header(net);
+    if (cap < h.bytes)
+        return fail(HH_EINVAL, "the state image needs %zu bytes, cap is %zu", (size_t)h.bytes, cap);
+    uint8_t* out = static_cast<uint8_t*>(dst);
+    HH_CUDA(cudaMemcpyAsync(out, &h, sizeof h, cudaMemcpyDefault, net->st));
+    size_t off = sizeof h;
+    for (const StateArray& x : state_arrays(net)) {
+        HH_CUDA(cudaMemcpyAsync(out + off, x.dev, x.bytes, cudaMemcpyDefault, net->st));
+        off += round256(x.bytes);
+    }
+    // h lives on this stack frame: the copies complete before returning
+    HH_CUDA(cudaStreamSynchronize(net->st));
+    return HH_OK;
+}
+
+hh_status hh_load_state(hh_net* net, const void* src, size_t n)
+{
+    if (!net || !src)
+        return fail(HH_EINVAL, "net and src must not be NULL");
+    if (n < sizeof(StateHeader))
+        return fail(HH_EINVAL, "a state image has at least %zu bytes", sizeof(StateHeader));
+    StateHeader h{};
+    HH_CUDA(cudaMemcpyAsync(&h, src, sizeof h, cudaMemcpyDefault, net->st));
+    HH_CUDA(cudaStreamSynchronize(net->st));
+    const StateHeader mine = state_header(net);
+    if (h.magic != kStateMagic)
+        return fail(HH_EINVAL, "not a state image of this library");
+    if (h.bytes > n)
+        return fail(HH_EINVAL, "the image has %zu bytes, %zu given", (size_t)h.bytes, n);
+    if (h.N != mine.N || h.R != mine.R || h.max_gates != mine.max_gates || h.precision != mine.precision ||
+        h.has_lo != mine.has_lo || h.has_ring != mine.has_ring || h.has_syn != mine.has_syn ||
+        h.bytes != mine.bytes)
+        return fail(HH_EINVAL,
+                    "the image does not fit this network: N %lld vs %lld, delay slots %d vs %d, precision %d vs "
+                    "%d, synapses %d vs %d",
+                    (long long)h.N, (long long)mine.N, h.R, mine.R, h.precision, mine.precision, h.has_syn,
+                    mine.has_syn);
+    if (h.t < 0 || h.t > (int64_t)INT32_MAX || h.window_index < 0)
+        return fail(HH_EINVAL, "the image's step index is out of range");
+    const uint8_t* in = static_cast<const uint8_t*>(src);
+    size_t off = sizeof h;
+    for (const StateArray& x : state_arrays(net)) {
+        HH_CUDA(cudaMemcpyAsync(x.dev, in + off, x.bytes, cudaMemcpyDefault, net->st));
+        off += round256(x.bytes);
+    }
+    net->t = h.t;
+    net->window_index = h.window_index;
+    return HH_OK;
+}
+
+hh_status hh_set_launch_shape(hh_net* net, int32_t neuron_block, int32_t route_blocks)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (neuron_block != 0 && neuron_block != 32 && neuron_block != 64 && neuron_block != 128)
+        return fail(HH_EINVAL, "neuron_block must be 0, 32, 64 or 128");
+    if (route_blocks < 0 || route_blocks > 4096)
+        return fail(HH_EINVAL, "route_blocks must be in 0 .. 4096");
+    if (net->morph.n_dendrites > 0 && neuron_block != 0 && neuron_block < 32)
+        return fail(HH_EINVAL, "multi-compartment cells need whole warps");
+    net->shape_block = neuron_block;
+    net->shape_route = route_blocks;
+    return HH_OK;
+}
+
+hh_status hh_autotune(hh_net* net, int32_t trial_steps, hh_tune_report* rep)
+{
+    if (!net)
+        return fail(HH_EINVAL, "net is NULL");
+    if (trial_steps < 1 || trial_steps > 1000000)
+        return fail(HH_EINVAL, "trial_steps must be in 1 .. 1e6");
+    if (net->kernels != HH_KERNELS_SPECIALISED || !(net->has_syn || net->has_bg) || net->sur_on)
+        return fail(HH_EUNSUPPORTED,
+                    "autotuning covers the specialised window schedule (a network with synapses or background)");
+    if (net->t + 2 * (int64_t)trial_steps > (int64_t)INT32_MAX)
+        return fail(HH_EINVAL, "step index would exceed 2^31-1");
+    const int32_t blocks[] = {32, 64, 128};
+    const int32_t routes[] = {152, 304, 608};
+    static_assert(1 + 3 * 3 <= HH_TUNE_MAX, "tune report size");
+    const size_t bytes = state_bytes(net);
+    void* saved = nullptr;
+    if (cudaMalloc(&saved, bytes) != cudaSuccess)
+        return fail(HH_ENOMEM, "autotune: %zu bytes for the saved state", bytes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    hh_tune_report r{};
+    hh_status s = HH_OK;
+    const int32_t old_block = net->shape_block, old_route = net->shape_route;
+    auto run = [&](float* ms) -> hh_status {
+        hh_status q = hh_load_state(net, saved, bytes);
+        if (q != HH_OK)
+            return q;
+        if (ms && cudaEventRecord(e0, net->st) != cudaSuccess)
+            return fail(HH_ECUDA, "autotune: event record failed");
+        if ((q = hh_step_n(net, trial_steps, nullptr, nullptr)) != HH_OK)
+            return q;
+        if (ms) {
+            if (cudaEventRecord(e1, net->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+                return fail(HH_ECUDA, "autotune: timing failed");
+        }
+        return HH_OK;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        s = fail(HH_ECUDA, "autotune: event creation failed");
+    if (s == HH_OK)
+        s = hh_save_state(net, saved, bytes);
+    // candidate 0 is the library's default shape (0, 0); another one is
+    // installed only when it beats the default by at least 2 %, so that
+    // timing noise between near-equal shapes does not move the choice
+    std::vector<std::pair<int32_t, int32_t>> cand = {{0, 0}};
+    for (int32_t b : blocks)
+        for (int32_t g : routes)
+            if (net->has_syn || g == routes[1])  // no routing launches: the grid does not matter
+                cand.push_back({b, g});
+    for (const auto& c : cand) {
+        if (s != HH_OK)
+            break;
+        if ((s = hh_set_launch_shape(net, c.first, c.second)) != HH_OK || (s = run(nullptr)) != HH_OK)
+            break;
+        float ms = 0.0f;
+        if ((s = run(&ms)) != HH_OK)
+            break;
+        r.neuron_block[r.n] = c.first;
+        r.route_blocks[r.n] = c.second;
+        r.ms[r.n] = ms;
+        ++r.n;
+    }
+    r.best = -1;
+    if (s == HH_OK && r.n > 0) {
+        int32_t k = 0;
+        for (int32_t j = 1; j < r.n; ++j)
+            if (r.ms[j] < r.ms[k])
+                k = j;
+        r.best = r.ms[k] <= 0.98f * r.ms[0] ? k : 0;
+    }
+    if (s == HH_OK && r.best >= 0) {
+        s = hh_set_launch_shape(net, r.neuron_block[r.best], r.route_blocks[r.best]);
+    } else {
+        net->shape_block = old_block;
+        net->shape_route = old_route;
+    }
+    // the network leaves with the state it came in with
+    const hh_status s_restore = hh_load_state(net, saved, bytes);
+    if (s == HH_OK)
+        s = s_restore;
+    if (cudaStreamSynchronize(net->st) != cudaSuccess && s == HH_OK)
+        s = fail(HH_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(saved);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (s == HH_OK && rep)
+        *rep = r;
+    return s;
 }
 
 hh_status hh_route_spikes(hh_net* net, const int32_t* spk_step, const int32_t* spk_idx, int64_t n_spk,

@@ -35,7 +35,7 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
                               const float* I_steps, const RecordParams& R,
                               const SpikeList& L, cudaStream_t st);
 cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity, int64_t t0,
-                                int32_t W, cudaStream_t st);
+                                int32_t W, int32_t blocks, cudaStream_t st);
 cudaError_t route_pull_prepare();
 cudaError_t launch_route_list(const RouteParams& RP, const int32_t* step, const int32_t* idx,
                               int64_t n, cudaStream_t st);
@@ -126,6 +126,6 @@ cudaError_t jit_launch_indexed(const JitKernels& K, const NeuronParams& P, const
                                const RecordParams& R, cudaStream_t st);
 cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_t t0, int32_t W,
                               int32_t parity, const float* I_steps, const RecordParams& R,
-                              const SpikeList& L, int32_t early, cudaStream_t st);
+                              const SpikeList& L, int32_t early, int32_t block, cudaStream_t st);
 
 }  // namespace hh

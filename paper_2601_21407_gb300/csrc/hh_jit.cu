@@ -410,9 +410,9 @@ cudaError_t jit_launch_independent(const JitKernels& K, const NeuronParams& P, i
 
 cudaError_t jit_launch_window(const JitKernels& K, const NeuronParams& P, int64_t t0, int32_t W,
                               int32_t parity, const float* I_steps, const RecordParams& R,
-                              const SpikeList& L, int32_t early, cudaStream_t st)
+                              const SpikeList& L, int32_t early, int32_t block_size, cudaStream_t st)
 {
-    const int bs = block_for(P.N);
+    const int bs = block_size > 0 ? block_size : block_for(P.N);
     const dim3 grid((unsigned)((P.N + bs - 1) / bs)), block(bs);
     long long t = t0;
     int w = W, par = parity, ea = early;

@@ -278,13 +278,13 @@ cudaError_t route_pull_prepare()
 }
 
 cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity, int64_t t0,
-                                int32_t W, cudaStream_t st)
+                                int32_t W, int32_t blocks, cudaStream_t st)
 {
-    // two resident blocks per SM whose warps loop over the window's spikes:
-    // routing overlaps the next window's neuron kernel, whose blocks must
-    // still find registers on every SM
+    // by default two resident blocks per SM whose warps loop over the
+    // window's spikes: routing overlaps the next window's neuron kernel,
+    // whose blocks must still find registers on every SM
     const size_t smem = RP.in_rec && RP.pull_min >= 0 ? pull_smem_bytes(RP.N, RP.pull_w) : 0;
-    k_route<<<152 * 2, 32 * kPullWarps, smem, st>>>(RP, L.step + parity * L.cap, L.idx + parity * L.cap,
+    k_route<<<blocks > 0 ? blocks : 152 * 2, 32 * kPullWarps, smem, st>>>(RP, L.step + parity * L.cap, L.idx + parity * L.cap,
                                                    L.counter + parity, 0, L.cap, t0, W, parity);
     return cudaGetLastError();
 }

@@ -138,6 +138,14 @@ class hh_peaks(C.Structure):
     _fields_ = [("ffma_per_s", C.c_double), ("ex2_per_s", C.c_double), ("rcp_per_s", C.c_double)]
 
 
+HH_TUNE_MAX = 16
+
+
+class hh_tune_report(C.Structure):
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("neuron_block", C.c_int32 * HH_TUNE_MAX),
+                ("route_blocks", C.c_int32 * HH_TUNE_MAX), ("ms", C.c_float * HH_TUNE_MAX)]
+
+
 class hh_record(C.Structure):
     _fields_ = [("V_trace", C.c_void_p), ("trace_idx", C.c_void_p), ("n_trace", C.c_int32),
                 ("spikes", C.c_void_p), ("spike_cap", C.c_int64), ("n_spikes", C.c_void_p),
@@ -149,7 +157,8 @@ EXPORTS = ["hh_create_network", "hh_set_channels", "hh_step_n", "hh_reset", "hh_
            "hh_last_error", "hh_version", "hh_layer_create", "hh_layer_set_weights",
            "hh_layer_forward", "hh_backward", "hh_backward_from", "hh_layer_readout", "hh_layer_destroy",
            "hh_surrogate_train", "hh_surrogate_enable", "hh_measure_peaks", "hh_set_wait_limits",
-           "hh_poly_fit", "hh_set_route_pull"]
+           "hh_poly_fit", "hh_set_route_pull", "hh_state_size", "hh_save_state", "hh_load_state",
+           "hh_set_launch_shape", "hh_autotune"]
 
 
 def lib_path() -> str:
@@ -217,6 +226,16 @@ def lib():
             L.hh_set_route_pull.argtypes = [vp, C.c_int64]
             L.hh_poly_fit.restype = C.c_int
             L.hh_poly_fit.argtypes = [P(hh_model_desc), C.c_double, vp, vp, vp, C.c_int64, vp]
+            L.hh_state_size.restype = C.c_int
+            L.hh_state_size.argtypes = [vp, P(C.c_size_t)]
+            L.hh_save_state.restype = C.c_int
+            L.hh_save_state.argtypes = [vp, vp, C.c_size_t]
+            L.hh_load_state.restype = C.c_int
+            L.hh_load_state.argtypes = [vp, vp, C.c_size_t]
+            L.hh_set_launch_shape.restype = C.c_int
+            L.hh_set_launch_shape.argtypes = [vp, C.c_int32, C.c_int32]
+            L.hh_autotune.restype = C.c_int
+            L.hh_autotune.argtypes = [vp, C.c_int32, P(hh_tune_report)]
             _lib = L
     return _lib
 
@@ -442,6 +461,37 @@ class Network:
         v = None if V0 is None else self._f32(V0)
         hh_reset(self.handle, _ptr(v))
         self._keep.append(v)
+
+    def state_size(self) -> int:
+        n = C.c_size_t(0)
+        _check(lib().hh_state_size(self.handle, C.byref(n)))
+        return int(n.value)
+
+    def save_state(self, out=None):
+        """The full dynamic state (hh_save_state) into `out` (a torch uint8
+        tensor on any device, or a numpy uint8 array), or into a new numpy
+        array; returns it."""
+        n = self.state_size()
+        if out is None:
+            out = np.zeros(n, dtype=np.uint8)
+        nbytes = out.nbytes if hasattr(out, "nbytes") else out.numel() * out.element_size()
+        _check(lib().hh_save_state(self.handle, _ptr(out), nbytes))
+        return out
+
+    def load_state(self, image):
+        nbytes = image.nbytes if hasattr(image, "nbytes") else image.numel() * image.element_size()
+        _check(lib().hh_load_state(self.handle, _ptr(image), nbytes))
+        self._keep.append(image)
+
+    def set_launch_shape(self, neuron_block=0, route_blocks=0):
+        _check(lib().hh_set_launch_shape(self.handle, int(neuron_block), int(route_blocks)))
+
+    def autotune(self, trial_steps=400):
+        """hh_autotune: returns {"candidates": [(block, route_blocks, ms)], "best": i}."""
+        r = hh_tune_report()
+        _check(lib().hh_autotune(self.handle, int(trial_steps), C.byref(r)))
+        return {"candidates": [(r.neuron_block[k], r.route_blocks[k], float(r.ms[k])) for k in range(r.n)],
+                "best": int(r.best)}
 
     def route_spikes(self, step, idx, n_window, sumE, sumI):
         hh_route_spikes(self.handle, _ptr(step), _ptr(idx), int(step.numel()), n_window,
