@@ -273,6 +273,52 @@ def test_batched_networks_mixed_models():
     net.close()
 
 
+def test_batched_networks_config5_shape():
+    """Batched heterogeneous networks with the shape of the 64-network
+    workload -- sizes log-uniform, in-degree uniform in 100..1,000, half the
+    networks classic HH and half multi-channel, background 600 sources x 5 Hz
+    x 1.2 nS, 200 ms -- scaled to 16 networks of 1,000-6,000 neurons so the
+    oracle runs in seconds.  Closed-loop parity per horizon (as for the
+    single large network): counts within +-1 for every neuron at 50 ms and
+    100 ms, for >= 99.9 % at 200 ms; total spikes within 0.5 % and every
+    network's total within 2 % (+3 spikes)."""
+    torch = _torch()
+    bn = inp.batched_networks(n_nets=16, n_min=1000, n_max=6000, k_min=100, k_max=1000, seed=7)
+    N = int(bn["offsets"][-1])
+    bg = {"rate_hz": 5.0, "K": 600, "w": 1.2}
+    T = 8000
+    models = [inp.CLASSIC_HH, inp.MULTI_CHANNEL]
+    ref = oracle.simulate_network(models, bn, T, 0.025, 40, SYN, bg=bg, seed=3, model_id=bn["model_id"],
+                                  spk_cap=128)
+    net = make_net(bn, bg=bg, seed=3, models=tuple(models), model_id=bn["model_id"])
+    rec, b = hh.make_record(N, T, spike_cap=4_000_000)
+    net.step(T, rec=rec)
+    torch.cuda.synchronize()
+    assert int(net.readout(hh.HH_READ_STATUS)[0]) == 0
+    st, ix, _ = hh.spikes_to_numpy(b)
+    net.close()
+    assert (ref["counts"] <= ref["spk_step"].shape[1]).all()
+    off = bn["offsets"]
+    stats = {}
+    for t_ms in (50, 100, 200):
+        s_end = int(round(t_ms / 0.025))
+        cg = np.bincount(ix[st < s_end], minlength=N)
+        ss = ref["spk_step"]
+        cr = ((ss >= 0) & (ss < s_end)).sum(1)
+        d = np.abs(cg - cr)
+        per_net = [(int(cg[off[k]:off[k + 1]].sum()), int(cr[off[k]:off[k + 1]].sum())) for k in range(16)]
+        stats[t_ms] = ((d == 0).mean(), (d <= 1).mean(), int(d.max()), int(cg.sum()), int(cr.sum()), per_net)
+        print(f"{t_ms} ms: equal {stats[t_ms][0]:.5f}, within 1 {stats[t_ms][1]:.5f}, max {d.max()}, "
+              f"spikes {cg.sum()} vs {cr.sum()}")
+    print("N", N, "synapses", bn["col"].size, "per-network totals at 200 ms", stats[200][5])
+    assert stats[200][4] > 5000
+    assert stats[50][2] <= 1 and stats[100][2] <= 1
+    assert stats[200][1] >= 0.999
+    assert abs(stats[200][3] - stats[200][4]) <= 0.005 * stats[200][4]
+    for g_tot, r_tot in stats[200][5]:
+        assert abs(g_tot - r_tot) <= 0.02 * r_tot + 3
+
+
 def test_deterministic_and_resumable():
     """Two runs from the same state give bit-identical rasters (fixed-point
     delivery is order independent), splitting a run across calls at points
