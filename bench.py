@@ -545,62 +545,66 @@ def extra_surrogate(dev, timed):
     """Config 4 with the learned gating surrogate: 1e6 multi-channel neurons,
     500 ms, the MLP (3 layers of width 64, bf16 on the tensor cores, 10-step
     windows) trained on 1e6 windows of the plain integrator (training not
-    timed), against the plain FP32 path on the same GPU: speed-up, share of
-    neuron-windows taken from the MLP, spike-count and spike-time errors
-    against the plain path, and counts against the FP64 oracle on 256
-    sampled neurons."""
+    timed), against the plain FP32 path on the same GPU, at three settings of
+    the per-neuron error estimate (off, and MLP-vs-coarse-step tolerances of
+    0.1 mV / 0.004 and 0.01 mV / 0.0005): speed-up, share of neuron-windows
+    taken from the MLP, spike-count and spike-time errors against the plain
+    path, and counts against the FP64 oracle on 256 sampled neurons."""
     import oracle
     from paper_2601_21407_gb300 import hh
     N, T, dt = 1_000_000, 20_000, 0.025
     y = inp.multi_channel_neurons(N, seed=0)
-    res = {}
-    runs = {}
-    for name in ("plain", "surrogate"):
+
+    def one(err=None):
         net = hh.Network(y["V0"], dt, I_const=y["I"], precision=hh.HH_PREC_FAST)
         net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
-        if name == "surrogate":
+        rep = None
+        if err is not None:
             rep = net.train_surrogate(v_envelope=-55.0, train_neurons=16384, train_windows=1_000_000,
-                                      epochs=30, batch=8192)
+                                      epochs=30, batch=8192, err_V=err[0], err_p=err[1])
             net.enable_surrogate(True)
-            res["val_loss"] = rep["val_loss"]
         rec, b = hh.make_record(N, T, spike_cap=40 * N)
         net.step(10)
         b["counts"].zero_()
         b["n_spikes"].zero_()
         net.reset()
-        if name == "surrogate":
-            net.enable_surrogate(True)
         ms = timed(lambda: net.step(T, rec=rec))
-        runs[name] = (b["counts"].cpu().numpy(), hh.spikes_to_numpy(b))
-        res[f"{name}_ms"] = ms
-        if name == "surrogate":
-            acc, dec = net.surrogate_stats()
-            res["accepted_frac"] = acc / max(1, acc + dec)
+        acc, dec = net.surrogate_stats() if err is not None else (0, 0)
+        out = (b["counts"].cpu().numpy(), hh.spikes_to_numpy(b), ms, acc / max(1, acc + dec), rep)
         net.close()
-    cp, cs = runs["plain"][0], runs["surrogate"][0]
-    d = np.abs(cs.astype(np.int64) - cp)
-    res["speedup_vs_plain"] = res["plain_ms"] / res["surrogate_ms"]
-    res["neuron_steps_per_s"] = N * T / (res["surrogate_ms"] * 1e-3)
-    res["count_equal_vs_plain"] = float((d == 0).mean())
-    res["count_within_1_vs_plain"] = float((d <= 1).mean())
-    # spike times of the neurons whose counts agree
-    (sp, ip, fp), (ss, is_, fs) = runs["plain"][1], runs["surrogate"][1]
-    eq = np.nonzero(d == 0)[0]
-    sel = np.random.default_rng(0).choice(eq, min(20_000, eq.size), replace=False) if eq.size else eq
-    mp, ms_ = np.isin(ip, sel), np.isin(is_, sel)
-    tp = np.lexsort(((sp[mp] + fp[mp]), ip[mp]))
-    ts = np.lexsort(((ss[ms_] + fs[ms_]), is_[ms_]))
-    dtv = np.abs((sp[mp] + fp[mp])[tp] - (ss[ms_] + fs[ms_])[ts]) * dt
-    worst = np.zeros(N)
-    np.maximum.at(worst, ip[mp][tp], dtv)
-    res["spike_times_within_0.05ms_of_plain"] = float((worst[sel] <= 0.05).mean()) if sel.size else None
+        return out
+
+    cp, spk_p, plain_ms, _, _ = one()
     idx = np.random.default_rng(1).choice(N, 256, replace=False)
     ref = oracle.simulate(inp.MULTI_CHANNEL, y["I"][idx], y["V0"][idx], T, dt, gbar=y["gbar"][:, idx],
                           trace=False, spk_cap=4)
-    res["count_within_1_vs_oracle"] = float((np.abs(cs[idx] - ref["counts"]) <= 1).mean())
-    res["plain_count_within_1_vs_oracle"] = float((np.abs(cp[idx] - ref["counts"]) <= 1).mean())
-    res["note"] = ("the surrogate misses its +-1 count / 0.05 ms target and runs slower than the plain "
-                   "path; reported as measured")
+    res = {"plain_ms": plain_ms,
+           "plain_count_within_1_vs_oracle": float((np.abs(cp[idx] - ref["counts"]) <= 1).mean()),
+           "settings": []}
+    (sp, ip, fp) = spk_p
+    for err in ((0.0, 0.0), (0.1, 0.004), (0.01, 0.0005)):
+        cs, (ss, is_, fs), ms, acc_frac, rep = one(err)
+        d = np.abs(cs.astype(np.int64) - cp)
+        # spike times of (a sample of) the neurons whose counts agree
+        eq = np.nonzero(d == 0)[0]
+        sel = np.random.default_rng(0).choice(eq, min(20_000, eq.size), replace=False) if eq.size else eq
+        mp, ms_ = np.isin(ip, sel), np.isin(is_, sel)
+        tp = np.lexsort(((sp[mp] + fp[mp]), ip[mp]))
+        ts = np.lexsort(((ss[ms_] + fs[ms_]), is_[ms_]))
+        dtv = np.abs((sp[mp] + fp[mp])[tp] - (ss[ms_] + fs[ms_])[ts]) * dt
+        worst = np.zeros(N)
+        np.maximum.at(worst, ip[mp][tp], dtv)
+        res["settings"].append({
+            "err_V_mV": err[0], "err_p": err[1], "surrogate_ms": ms, "speedup_vs_plain": plain_ms / ms,
+            "neuron_steps_per_s": N * T / (ms * 1e-3), "accepted_frac": acc_frac,
+            "val_loss": rep["val_loss"],
+            "count_equal_vs_plain": float((d == 0).mean()), "count_within_1_vs_plain": float((d <= 1).mean()),
+            "max_count_diff_vs_plain": int(d.max()),
+            "spike_times_within_0.05ms_of_plain": float((worst[sel] <= 0.05).mean()) if sel.size else None,
+            "count_within_1_vs_oracle": float((np.abs(cs[idx] - ref["counts"]) <= 1).mean())})
+    res["note"] = ("the error estimate trades accepted windows for accuracy: off, the surrogate misses "
+                   "the +-1 count / 0.05 ms target; at 0.01 mV it meets it on few windows; no setting "
+                   "is faster than the plain path")
     return res
 
 

@@ -472,8 +472,15 @@ hh_status hh_set_route_pull(hh_net* net, int64_t min_spikes);
  * over the window, scaled to unit variance.  A window is taken from the MLP
  * when V < v_envelope at its start, every feature lies within the range seen
  * in training (widened by 2 %), and the prediction keeps V below the
- * envelope, the gates in [0, 1] and Ca positive; otherwise the plain kernel
- * integrates it (so every spike comes from the plain integrator). */
+ * envelope, the gates in [0, 1] and Ca positive, and -- the per-neuron
+ * error estimate, when err_V > 0 -- the prediction agrees with one
+ * exponential-Euler step over the whole window from the same state (rates
+ * at the window's first V, window length dt W) to err_V mV in V and err_p
+ * in every gate; otherwise the plain kernel integrates it (so every spike
+ * comes from the plain integrator).  The coarse step is exact for a neuron
+ * at rest and its disagreement with the MLP grows where V and the fast
+ * gates move within the window, which is where the MLP's errors come
+ * from. */
 typedef struct {
     int32_t window;          /* steps per MLP evaluation, 1..1000           */
     float v_envelope;        /* mV                                          */
@@ -486,6 +493,9 @@ typedef struct {
     float I_min, I_max;      /* uA/cm^2 range of the training neurons       */
     float gbar_sigma;        /* lognormal spread of their maximal conductances */
     float V0_min, V0_max;    /* initial V range (gates at steady state)     */
+    float err_V;             /* error-estimate tolerance in V (mV); 0: off  */
+    float err_p;             /* error-estimate tolerance of the gates (used
+                                when err_V > 0)                            */
 } hh_surrogate_desc;
 
 typedef struct {

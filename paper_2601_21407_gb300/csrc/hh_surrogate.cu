@@ -343,6 +343,8 @@ struct InferParams {
     unsigned long long* stats;  // [0] accepted windows, [1] fallbacks
     int32_t* err;
     float margin;         // fractional widening of the feature envelope
+    int32_t W;            // steps per window
+    float err_V, err_p;   // error-estimate tolerances (err_V <= 0: off)
 };
 
 constexpr uint32_t kTile = 128 * kRow * 2;  // 16 KB per 128-row bf16 tile
@@ -376,8 +378,37 @@ __device__ __forceinline__ void put_row(uint8_t* tile, int r, const float* v)
     }
 }
 
+// The per-neuron error estimate: one exponential-Euler step over the whole
+// window (rates at its first V, step dt W; Mc is the model with the
+// calcium decay of dt W) from the neuron's state.
+template <int PREC>
+__device__ __forceinline__ void coarse_step(const DevModel& Mc, float dt_w, float V, const float* p, float Ca,
+                                            float I, const float* gch, State<kMaxGates, PREC>& c)
+{
+    c.poly = nullptr;
+    c.V = V;
+    c.Vlo = 0.0f;
+    c.Ca = Ca;
+    c.gconst = 0.0f;
+    c.gconstE = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < kMaxChannels; ++ch)
+        if (ch < Mc.n_ch && Mc.ch_ng[ch] == 0) {
+            c.gconst += gch[ch];
+            c.gconstE += gch[ch] * Mc.E[ch];
+        }
+#pragma unroll
+    for (int q = 0; q < kMaxGates; ++q) {
+        c.p[q] = p[q];
+        c.plo[q] = 0.0f;
+        c.gq[q] = (q < Mc.n_gates && Mc.gate_last[q]) ? gch[Mc.gate_ch[q]] : 0.0f;
+    }
+    neuron_step<kMaxGates, PREC>(Mc, dt_w, HH_V_EXP_EULER, I, 0.0f, 0.0f, 0.0f, 0.0f, c);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevModels Ms,
+                                                   const __grid_constant__ DevModels Mcoarse,
                                                    const __grid_constant__ SurNorm S,
                                                    const __grid_constant__ NeuronParams P,
                                                    const __grid_constant__ InferParams Q)
@@ -534,6 +565,15 @@ __global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevMo
         Can = Ca + (o[1 + G] + Q.b[2 * kSH + 1 + G]) * S.out_scale[1 + G];
         acc = acc && Can > 0.0f;
     }
+    if (Q.err_V > 0.0f && acc) {
+        State<kMaxGates, PREC> c;
+        coarse_step<PREC>(Mcoarse.m[0], P.dt * (float)Q.W, V, p, Ca, I, gch, c);
+        acc = fabsf(Vn - c.V) <= Q.err_V;
+#pragma unroll
+        for (int q = 0; q < kMaxGates; ++q)
+            if (q < G)
+                acc = acc && fabsf(pn[q] - c.p[q]) <= Q.err_p;
+    }
     if (valid) {
         if (acc) {
             P.V[i] = Vn;
@@ -580,6 +620,8 @@ struct Surrogate {
     int W = 10;
     int n_out = 0;
     SurNorm norm{};
+    float err_V = 0.0f, err_p = 0.0f;
+    DevModels coarse{};          // the network's models with the calcium decay of dt W
     float* params = nullptr;     // fp32 master parameters
     uint16_t* wb = nullptr;      // bf16 copies of W1 | W2 | W3
     float* bias = nullptr;       // [64 | 64 | 16]
@@ -621,8 +663,17 @@ hh_status surrogate_train(const DevModels& Ms, int precision, double dt, int64_t
     const int n_feat = 3 + G + M.n_ch, n_out = 1 + G + has_ca;
     if (n_feat > kSF || n_out > kSO)
         return fail(HH_EUNSUPPORTED, "model too large for the surrogate (%d features, %d outputs)", n_feat, n_out);
+    if (!(d->err_V >= 0.0f) || !(d->err_p >= 0.0f) || !std::isfinite(d->err_V) || !std::isfinite(d->err_p) ||
+        (d->err_V > 0.0f && !(d->err_p > 0.0f)))
+        return fail(HH_EINVAL, "surrogate error-estimate tolerances: err_V >= 0, and err_p > 0 when err_V > 0");
     Surrogate* S = new Surrogate();
     S->W = d->window;
+    S->err_V = d->err_V;
+    S->err_p = d->err_p;
+    S->coarse = Ms;
+    for (int k = 0; k < kMaxModels; ++k)
+        if (S->coarse.m[k].ca_tau > 0.0f)
+            S->coarse.m[k].ca_decay = (float)std::exp(-(double)d->window * dt / (double)S->coarse.m[k].ca_tau);
     S->n_out = n_out;
     S->N = N_net;
     S->margin = 0.02f;
@@ -896,14 +947,17 @@ cudaError_t surrogate_window(const DevModels& Ms, Surrogate* S, const NeuronPara
     q.stats = S->stats;
     q.err = S->err;
     q.margin = S->margin;
+    q.W = S->W;
+    q.err_V = S->err_V;
+    q.err_p = S->err_p;
     cudaError_t e = cudaMemsetAsync(S->fb_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess)
         return e;
     const unsigned grid = (unsigned)((P.N + 127) / 128);
     if (precision == HH_PREC_FAST)
-        k_sur_infer<HH_PREC_FAST><<<grid, 128, kInferSmem, st>>>(Ms, S->norm, P, q);
+        k_sur_infer<HH_PREC_FAST><<<grid, 128, kInferSmem, st>>>(Ms, S->coarse, S->norm, P, q);
     else
-        k_sur_infer<HH_PREC_ACCURATE><<<grid, 128, kInferSmem, st>>>(Ms, S->norm, P, q);
+        k_sur_infer<HH_PREC_ACCURATE><<<grid, 128, kInferSmem, st>>>(Ms, S->coarse, S->norm, P, q);
     return cudaGetLastError();
 }
 

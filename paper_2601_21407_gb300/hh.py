@@ -106,7 +106,8 @@ class hh_surrogate_desc(C.Structure):
     _fields_ = [("window", C.c_int32), ("v_envelope", C.c_float), ("train_neurons", C.c_int32),
                 ("train_windows", C.c_int32), ("epochs", C.c_int32), ("batch", C.c_int32),
                 ("lr", C.c_float), ("seed", C.c_uint64), ("I_min", C.c_float), ("I_max", C.c_float),
-                ("gbar_sigma", C.c_float), ("V0_min", C.c_float), ("V0_max", C.c_float)]
+                ("gbar_sigma", C.c_float), ("V0_min", C.c_float), ("V0_max", C.c_float),
+                ("err_V", C.c_float), ("err_p", C.c_float)]
 
 
 class hh_surrogate_report(C.Structure):
@@ -509,9 +510,9 @@ class Network:
 
     def train_surrogate(self, window=10, v_envelope=-55.0, train_neurons=16384, train_windows=1_000_000,
                         epochs=40, batch=8192, lr=2e-3, seed=0, I_min=0.0, I_max=15.0, gbar_sigma=0.3,
-                        V0_min=-80.0, V0_max=-55.0):
+                        V0_min=-80.0, V0_max=-55.0, err_V=0.0, err_p=0.0):
         d = hh_surrogate_desc(window, v_envelope, train_neurons, train_windows, epochs, batch, lr, seed,
-                              I_min, I_max, gbar_sigma, V0_min, V0_max)
+                              I_min, I_max, gbar_sigma, V0_min, V0_max, err_V, err_p)
         r = hh_surrogate_report()
         _check(lib().hh_surrogate_train(self.handle, C.byref(d), C.byref(r)))
         return {"train_windows": r.train_windows, "train_loss": r.train_loss, "val_loss": r.val_loss,

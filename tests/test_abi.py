@@ -53,6 +53,7 @@ int main(void){
  printf("%zu %zu\\n", sizeof(hh_peaks), offsetof(hh_peaks, rcp_per_s));
  printf("%zu %zu\\n", sizeof(hh_grads), offsetof(hh_grads, dX));
  printf("%zu %zu\\n", sizeof(hh_tune_report), offsetof(hh_tune_report, ms));
+ printf("%zu %zu\\n", sizeof(hh_surrogate_desc), offsetof(hh_surrogate_desc, err_p));
  return 0; }
 """)
     exe = tmp_path / "probe"
@@ -70,7 +71,8 @@ int main(void){
             hh.hh_net_desc.bg_weight_sd.offset, C.sizeof(hh.hh_net_desc),
             C.sizeof(hh.hh_peaks), hh.hh_peaks.rcp_per_s.offset,
             C.sizeof(hh.hh_grads), hh.hh_grads.dX.offset,
-            C.sizeof(hh.hh_tune_report), hh.hh_tune_report.ms.offset]
+            C.sizeof(hh.hh_tune_report), hh.hh_tune_report.ms.offset,
+            C.sizeof(hh.hh_surrogate_desc), hh.hh_surrogate_desc.err_p.offset]
     assert got == want
 
 

@@ -3,9 +3,10 @@ via the C ABI): training converges on windows from the plain integrator,
 windows outside the trained envelope are integrated by the plain kernel
 (with every window declined the run is bit-identical to the plain path), and
 the error against the plain path and the FP64 oracle is measured and
-reported (the accuracy target -- spike counts within +-1 and spike times
-within 0.05 ms for every neuron -- is not met by this surrogate; the test
-records the achieved figures)."""
+reported.  Without its per-neuron error estimate the surrogate misses the
+accuracy target (spike counts within +-1 and spike times within 0.05 ms for
+every neuron); with a tight estimate it meets it, on few windows.  The tests
+record the achieved figures."""
 import json
 
 import numpy as np
@@ -144,3 +145,53 @@ def test_surrogate_error_is_measured():
     assert report["count_within_1_vs_plain"] >= 0.55
     assert report["count_within_1_vs_oracle"] >= 0.5
     assert report["spike_times_within_0.05ms_of_plain"] >= 0.2
+
+
+def test_error_estimate_controls_accuracy():
+    """The per-neuron error estimate (the MLP's 10-step prediction against one
+    exponential-Euler step over the whole window, hh_surrogate_desc.err_V /
+    err_p) hands every window where the two disagree to the plain kernel.
+    Tightening it trades accepted windows for accuracy (4,096 multi-channel
+    neurons, 500 ms; measured: at 0.1 mV / 0.004, 34 % of windows accepted
+    and counts within +-1 of the plain path for 99.5 % of neurons; at 0.01 mV
+    / 0.0005, 4 % accepted, counts within +-1 for every neuron and spike
+    times within 0.05 ms for 99.8 % of the count-equal neurons -- the
+    accuracy target, met on few windows).  The training windows are appended
+    by atomics, so their order, and the trained weights, vary slightly from
+    run to run: the bars sit below the measured levels (>= 99.9 % within
+    +-1 and >= 98 % of spike times at the tight setting)."""
+    y = inp.multi_channel_neurons(4096, seed=7)
+    T = 20_000
+    plain = run(y, T)
+    idx = np.random.default_rng(0).choice(4096, 256, replace=False)
+    ref = oracle.simulate(inp.MULTI_CHANNEL, y["I"][idx], y["V0"][idx], T, DT, gbar=y["gbar"][:, idx],
+                          trace=False, spk_cap=4)
+    base = dict(v_envelope=-55.0, train_neurons=16384, train_windows=1_000_000, epochs=30, batch=8192)
+    out = {}
+    for key, (eV, ep) in {"mid": (0.1, 0.004), "tight": (0.01, 0.0005)}.items():
+        sur = run(y, T, surrogate=dict(base, err_V=eV, err_p=ep))
+        acc, dec = sur["stats"]
+        dc = np.abs(sur["counts"] - plain["counts"])
+        out[key] = {"accepted_frac": acc / (acc + dec), "within_1": float((dc <= 1).mean()),
+                    "max_diff": int(dc.max()),
+                    "within_1_oracle": float((np.abs(sur["counts"][idx] - ref["counts"]) <= 1).mean()),
+                    "times": _spike_time_agreement(sur, plain, 4096)}
+        assert sur["status"] == 0
+    print(json.dumps(out))
+    assert out["mid"]["accepted_frac"] >= 0.25 and out["mid"]["within_1"] >= 0.99
+    assert out["tight"]["accepted_frac"] >= 0.02
+    assert out["tight"]["within_1"] >= 0.999 and out["tight"]["within_1_oracle"] >= 0.99
+    assert out["tight"]["times"] >= 0.98
+    # looser tolerance, more windows from the MLP
+    assert out["mid"]["accepted_frac"] > out["tight"]["accepted_frac"]
+
+
+def test_error_estimate_tolerances_are_checked():
+    y = inp.multi_channel_neurons(256, seed=8)
+    net = hh.Network(y["V0"], DT, I_const=y["I"], precision=hh.HH_PREC_FAST)
+    net.set_channels(0, inp.MULTI_CHANNEL, gbar=y["gbar"])
+    for eV, ep in ((-1.0, 0.01), (0.1, 0.0), (float("nan"), 0.01)):
+        with pytest.raises(hh.HHError) as e:
+            net.train_surrogate(v_envelope=-55.0, err_V=eV, err_p=ep, **SMALL_TRAIN)
+        assert e.value.status == hh.HH_EINVAL
+    net.close()
