@@ -227,8 +227,9 @@ def run_gpu(args):
         net.step(STEPS_PER_SIM, rec=rec)
 
     # launch shape autotuned for this network: each candidate runs one
-    # benchmark step (1 s from reset) twice, the second timed; the state is
-    # restored afterwards.  Before the warm-up, outside the timed region.
+    # benchmark step (1 s from reset) four times, the median of the last
+    # three timed; the state is restored afterwards.  Before the warm-up,
+    # outside the timed region.
     net.reset(V0_dev)
     tune = net.autotune(trial_steps=STEPS_PER_SIM)
     for _ in range(args.warmup):
@@ -434,7 +435,7 @@ def run_gpu(args):
                              "route_blocks": tune["candidates"][tune["best"]][1],
                              "source": "hh_autotune over one benchmark step (40,000 steps from reset), before "
                                        "the warm-up; (0, 0) is the library's default shape, kept unless another "
-                                       "is 2 % faster",
+                                       "is 3 % faster (median of three timed runs each)",
                              "sweep_ms_per_step": [list(c) for c in tune["candidates"]]},
         }
         if cpu is not None:

@@ -404,10 +404,11 @@ hh_status hh_set_launch_shape(hh_net* net, int32_t neuron_block, int32_t route_b
  * candidate -- the library's default shape, reported as (0, 0), then
  * neuron blocks 32, 64, 128 x routing grids of 152, 304, 608 blocks (one
  * grid when the network has no synapses) -- advances the network by
- * trial_steps from its current state twice (the first run compiles and
- * captures, the second is timed with CUDA events), the state is restored
- * after every run, and the fastest shape is installed if it beats the
- * default by at least 2 % (else the default stays).  On return the
+ * trial_steps from its current state four times (the first run compiles
+ * and captures, the other three are timed with CUDA events and their
+ * median kept), the state is restored before every run, and the fastest
+ * shape is installed if it beats the default by at least 3 % (else the
+ * default stays).  On return the
  * network's state is the one it had on entry.
  * Needs a network with synapses or background on the specialised kernels
  * (HH_EUNSUPPORTED otherwise).  Synchronous.  rep may be NULL. */
@@ -417,7 +418,7 @@ typedef struct {
     int32_t best;                       /* index of the installed one */
     int32_t neuron_block[HH_TUNE_MAX];
     int32_t route_blocks[HH_TUNE_MAX];
-    float ms[HH_TUNE_MAX];              /* timed run of trial_steps steps */
+    float ms[HH_TUNE_MAX];              /* median timed run of trial_steps steps */
 } hh_tune_report;
 hh_status hh_autotune(hh_net* net, int32_t trial_steps, hh_tune_report* rep);
 

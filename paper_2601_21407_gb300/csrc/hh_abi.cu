@@ -1,5 +1,6 @@
 // C ABI of libhh (see include/hh.h): argument validation, ownership of the
 // network's device memory, model preparation and the launch schedule.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -1583,8 +1584,9 @@ hh_status hh_autotune(hh_net* net, int32_t trial_steps, hh_tune_report* rep)
     if (s == HH_OK)
         s = hh_save_state(net, saved, bytes);
     // candidate 0 is the library's default shape (0, 0); another one is
-    // installed only when it beats the default by at least 2 %, so that
-    // timing noise between near-equal shapes does not move the choice
+    // installed only when the median of its three timed runs beats the
+    // default's by at least 3 %, so that timing noise between near-equal
+    // shapes does not move the choice
     std::vector<std::pair<int32_t, int32_t>> cand = {{0, 0}};
     for (int32_t b : blocks)
         for (int32_t g : routes)
@@ -1595,12 +1597,15 @@ hh_status hh_autotune(hh_net* net, int32_t trial_steps, hh_tune_report* rep)
             break;
         if ((s = hh_set_launch_shape(net, c.first, c.second)) != HH_OK || (s = run(nullptr)) != HH_OK)
             break;
-        float ms = 0.0f;
-        if ((s = run(&ms)) != HH_OK)
+        float t[3] = {0.0f, 0.0f, 0.0f};
+        for (int k = 0; k < 3 && s == HH_OK; ++k)
+            s = run(&t[k]);
+        if (s != HH_OK)
             break;
+        std::sort(t, t + 3);
         r.neuron_block[r.n] = c.first;
         r.route_blocks[r.n] = c.second;
-        r.ms[r.n] = ms;
+        r.ms[r.n] = t[1];  // median of three timed runs
         ++r.n;
     }
     r.best = -1;
@@ -1609,7 +1614,7 @@ hh_status hh_autotune(hh_net* net, int32_t trial_steps, hh_tune_report* rep)
         for (int32_t j = 1; j < r.n; ++j)
             if (r.ms[j] < r.ms[k])
                 k = j;
-        r.best = r.ms[k] <= 0.98f * r.ms[0] ? k : 0;
+        r.best = r.ms[k] <= 0.97f * r.ms[0] ? k : 0;
     }
     if (s == HH_OK && r.best >= 0) {
         s = hh_set_launch_shape(net, r.neuron_block[r.best], r.route_blocks[r.best]);

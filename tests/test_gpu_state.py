@@ -136,7 +136,7 @@ def test_autotune_restores_state_and_keeps_results():
     assert rep["candidates"][0][:2] == (0, 0)
     assert all(ms > 0 for _, _, ms in rep["candidates"])
     best = rep["candidates"][rep["best"]][2]
-    assert rep["best"] == 0 or best <= 0.98 * rep["candidates"][0][2]
+    assert rep["best"] == 0 or best <= 0.97 * rep["candidates"][0][2]
     assert np.array_equal(a.save_state(), before)
     ra, rb = _run(a, 4000, 600), _run(b, 4000, 600)
     _same(ra, rb)
