@@ -460,28 +460,29 @@ hh_status hh_set_route_pull(hh_net* net, int64_t min_spikes);
 /* Learned multi-step surrogate                                         */
 /* ------------------------------------------------------------------ */
 
-/* A small MLP (features -> 64 -> 64 -> state increments, tanh, bf16 weights
- * with fp32 accumulation on the tensor cores) that advances V, the gates and
- * Ca of an independent neuron by `window` steps at once while the neuron is
- * inside the sub-threshold envelope it was trained on.  It has no
+/* A small MLP (features -> 64 -> 64 -> state corrections, tanh, bf16
+ * weights with fp32 accumulation on the tensor cores) that advances V, the
+ * gates and Ca of an independent neuron by `window` steps at once while the
+ * neuron is inside the sub-threshold envelope it was trained on.  Its
+ * prediction is one exponential-Euler step over the whole window (rates at
+ * the window's first V, step dt window) plus the MLP's learned correction.  It has no
  * counterpart in the paper (whose operators use polynomial approximations of
  * the rates, Methods "Engineering optimization"); the plain exponential-
  * Euler integrator generates its training data, integrates every window the
  * surrogate declines, and judges its error.
  * Features: (V + 65)/20, 2p - 1 per gate, log(Ca/Ca_rest)/2, I/10,
- * log(gbar_c / default gbar_c)/0.3 per channel.  Targets: the increments
- * over the window, scaled to unit variance.  A window is taken from the MLP
+ * log(gbar_c / default gbar_c)/0.3 per channel.  Targets: the plain
+ * integrator's state after the window minus the coarse step's, scaled to
+ * unit variance.  A window is taken from the MLP
  * when V < v_envelope at its start, every feature lies within the range seen
  * in training (widened by 2 %), and the prediction keeps V below the
  * envelope, the gates in [0, 1] and Ca positive, and -- the per-neuron
- * error estimate, when err_V > 0 -- the prediction agrees with one
- * exponential-Euler step over the whole window from the same state (rates
- * at the window's first V, window length dt W) to err_V mV in V and err_p
- * in every gate; otherwise the plain kernel integrates it (so every spike
- * comes from the plain integrator).  The coarse step is exact for a neuron
- * at rest and its disagreement with the MLP grows where V and the fast
- * gates move within the window, which is where the MLP's errors come
- * from. */
+ * error estimate, when err_V > 0 -- the MLP's correction to the coarse step
+ * is at most err_V mV in V and err_p in every gate; otherwise the plain
+ * kernel integrates it (so every spike comes from the plain integrator).
+ * The coarse step is exact for a neuron at rest; the correction grows where
+ * V and the fast gates move within the window, and the MLP's error is a
+ * fraction of the correction it predicts. */
 typedef struct {
     int32_t window;          /* steps per MLP evaluation, 1..1000           */
     float v_envelope;        /* mV                                          */

@@ -2,8 +2,10 @@
 //
 // A small MLP (features 32 -> 64 -> 64 -> 16, tanh) advances the neuron
 // state (V, gates, Ca) by W time steps at once inside the sub-threshold
-// envelope it was trained on; everything else -- and every window that
-// leaves the envelope -- is integrated by the plain exponential-Euler
+// envelope it was trained on, as a learned correction to one
+// exponential-Euler step over the whole window; everything else -- and
+// every window that leaves the envelope or needs a larger correction than
+// the error estimate allows -- is integrated by the plain exponential-Euler
 // kernel, which also generated the training data and judges the error.
 // (The paper accelerates its ion-channel operators with polynomial
 // approximations of the rates, Methods "Engineering optimization"; this
@@ -11,8 +13,8 @@
 // describe.)
 //
 //   data      k_sur_gen: the plain integrator on random training neurons
-//             records (features(state_t), state_{t+W} - state_t) for windows
-//             whose V stays below v_env;
+//             records (features(state_t), state_{t+W} - coarse(state_t))
+//             for windows whose V stays below v_env;
 //   training  k_sur_train / k_sur_adam: FP32 forward + backward of a
 //             128-sample block, deterministic reduction of block partials,
 //             Adam;
@@ -75,6 +77,34 @@ __device__ __forceinline__ void sur_features(const DevModel& M, const SurNorm& S
             f[3 + G + c] = S.gbar_ref[c] > 0.0f ? logf(fmaxf(gch[c], 1e-12f) / S.gbar_ref[c]) * (1.0f / 0.3f) : 0.0f;
 }
 
+// One exponential-Euler step over a whole window (rates at its first V,
+// step dt W; Mc is the model with the calcium decay of dt W) from a
+// neuron's state: the coarse prediction the MLP corrects.
+template <int PREC>
+__device__ __forceinline__ void coarse_step(const DevModel& Mc, float dt_w, float V, const float* p, float Ca,
+                                            float I, const float* gch, State<kMaxGates, PREC>& c)
+{
+    c.poly = nullptr;
+    c.V = V;
+    c.Vlo = 0.0f;
+    c.Ca = Ca;
+    c.gconst = 0.0f;
+    c.gconstE = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < kMaxChannels; ++ch)
+        if (ch < Mc.n_ch && Mc.ch_ng[ch] == 0) {
+            c.gconst += gch[ch];
+            c.gconstE += gch[ch] * Mc.E[ch];
+        }
+#pragma unroll
+    for (int q = 0; q < kMaxGates; ++q) {
+        c.p[q] = p[q];
+        c.plo[q] = 0.0f;
+        c.gq[q] = (q < Mc.n_gates && Mc.gate_last[q]) ? gch[Mc.gate_ch[q]] : 0.0f;
+    }
+    neuron_step<kMaxGates, PREC>(Mc, dt_w, HH_V_EXP_EULER, I, 0.0f, 0.0f, 0.0f, 0.0f, c);
+}
+
 // ---------------------------------------------------------------------------
 // training data
 // ---------------------------------------------------------------------------
@@ -91,7 +121,9 @@ struct GenParams {
 };
 
 template <int PREC>
-__global__ void __launch_bounds__(128) k_sur_gen(const __grid_constant__ DevModels Ms, const __grid_constant__ SurNorm S,
+__global__ void __launch_bounds__(128) k_sur_gen(const __grid_constant__ DevModels Ms,
+                                                 const __grid_constant__ DevModels Mc,
+                                                 const __grid_constant__ SurNorm S,
                                                  const __grid_constant__ GenParams g)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,6 +163,8 @@ __global__ void __launch_bounds__(128) k_sur_gen(const __grid_constant__ DevMode
 #pragma unroll
         for (int q = 0; q < kMaxGates; ++q)
             p0[q] = s.p[q];
+        State<kMaxGates, PREC> c;
+        coarse_step<PREC>(Mc.m[0], g.dt * (float)g.W, V0, p0, Ca0, I, gch, c);
         float vmax = s.V;
         for (int k = 0; k < g.W; ++k) {
             neuron_step<kMaxGates, PREC>(M, g.dt, HH_V_EXP_EULER, I, 0.0f, 0.0f, 0.0f, 0.0f, s);
@@ -147,11 +181,13 @@ __global__ void __launch_bounds__(128) k_sur_gen(const __grid_constant__ DevMode
                 float* y = g.Y + slot * kSO;
                 for (int k = 0; k < kSO; ++k)
                     y[k] = 0.0f;
-                y[0] = s.V - V0;
+                // the target is the plain integrator's window minus the
+                // coarse step: what the MLP has to add to the coarse step
+                y[0] = s.V - c.V;
                 for (int q = 0; q < M.n_gates; ++q)
-                    y[1 + q] = s.p[q] - p0[q];
+                    y[1 + q] = s.p[q] - c.p[q];
                 if (S.has_ca)
-                    y[1 + M.n_gates] = s.Ca - Ca0;
+                    y[1 + M.n_gates] = s.Ca - c.Ca;
             }
         }
     }
@@ -378,34 +414,6 @@ __device__ __forceinline__ void put_row(uint8_t* tile, int r, const float* v)
     }
 }
 
-// The per-neuron error estimate: one exponential-Euler step over the whole
-// window (rates at its first V, step dt W; Mc is the model with the
-// calcium decay of dt W) from the neuron's state.
-template <int PREC>
-__device__ __forceinline__ void coarse_step(const DevModel& Mc, float dt_w, float V, const float* p, float Ca,
-                                            float I, const float* gch, State<kMaxGates, PREC>& c)
-{
-    c.poly = nullptr;
-    c.V = V;
-    c.Vlo = 0.0f;
-    c.Ca = Ca;
-    c.gconst = 0.0f;
-    c.gconstE = 0.0f;
-#pragma unroll
-    for (int ch = 0; ch < kMaxChannels; ++ch)
-        if (ch < Mc.n_ch && Mc.ch_ng[ch] == 0) {
-            c.gconst += gch[ch];
-            c.gconstE += gch[ch] * Mc.E[ch];
-        }
-#pragma unroll
-    for (int q = 0; q < kMaxGates; ++q) {
-        c.p[q] = p[q];
-        c.plo[q] = 0.0f;
-        c.gq[q] = (q < Mc.n_gates && Mc.gate_last[q]) ? gch[Mc.gate_ch[q]] : 0.0f;
-    }
-    neuron_step<kMaxGates, PREC>(Mc, dt_w, HH_V_EXP_EULER, I, 0.0f, 0.0f, 0.0f, 0.0f, c);
-}
-
 template <int PREC>
 __global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevModels Ms,
                                                    const __grid_constant__ DevModels Mcoarse,
@@ -547,32 +555,32 @@ __global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevMo
     float o[kSO];
     tmem_ld16(tmem + lane_base, o);
 
-    // accept inside the envelope, otherwise hand the window to the plain kernel
+    // the prediction: the coarse step plus the learned correction; accepted
+    // inside the envelope (and, with the error estimate on, when the
+    // correction is small: the MLP's error is a fraction of it), otherwise
+    // the window goes to the plain kernel
     const int G = M.n_gates;
-    const float Vn = V + (o[0] + Q.b[2 * kSH + 0]) * S.out_scale[0];
+    State<kMaxGates, PREC> c;
+    coarse_step<PREC>(Mcoarse.m[0], P.dt * (float)Q.W, V, p, Ca, I, gch, c);
+    const float Vn = c.V + (o[0] + Q.b[2 * kSH + 0]) * S.out_scale[0];
     bool acc = cand && ok && Vn < S.v_env && finite(Vn);
+    if (Q.err_V > 0.0f)
+        acc = acc && fabsf(Vn - c.V) <= Q.err_V;
     float pn[kMaxGates];
 #pragma unroll
     for (int q = 0; q < kMaxGates; ++q) {
         pn[q] = p[q];
         if (q < G) {
-            pn[q] = p[q] + (o[1 + q] + Q.b[2 * kSH + 1 + q]) * S.out_scale[1 + q];
+            pn[q] = c.p[q] + (o[1 + q] + Q.b[2 * kSH + 1 + q]) * S.out_scale[1 + q];
             acc = acc && pn[q] >= 0.0f && pn[q] <= 1.0f;
+            if (Q.err_V > 0.0f)
+                acc = acc && fabsf(pn[q] - c.p[q]) <= Q.err_p;
         }
     }
     float Can = Ca;
     if (S.has_ca) {
-        Can = Ca + (o[1 + G] + Q.b[2 * kSH + 1 + G]) * S.out_scale[1 + G];
+        Can = c.Ca + (o[1 + G] + Q.b[2 * kSH + 1 + G]) * S.out_scale[1 + G];
         acc = acc && Can > 0.0f;
-    }
-    if (Q.err_V > 0.0f && acc) {
-        State<kMaxGates, PREC> c;
-        coarse_step<PREC>(Mcoarse.m[0], P.dt * (float)Q.W, V, p, Ca, I, gch, c);
-        acc = fabsf(Vn - c.V) <= Q.err_V;
-#pragma unroll
-        for (int q = 0; q < kMaxGates; ++q)
-            if (q < G)
-                acc = acc && fabsf(pn[q] - c.p[q]) <= Q.err_p;
     }
     if (valid) {
         if (acc) {
@@ -756,9 +764,9 @@ hh_status surrogate_train(const DevModels& Ms, int precision, double dt, int64_t
     gp.cap = cap;
     if (e == cudaSuccess) {
         if (precision == HH_PREC_FAST)
-            k_sur_gen<HH_PREC_FAST><<<(ntr + 127) / 128, 128, 0, st>>>(Ms, nm, gp);
+            k_sur_gen<HH_PREC_FAST><<<(ntr + 127) / 128, 128, 0, st>>>(Ms, S->coarse, nm, gp);
         else
-            k_sur_gen<HH_PREC_ACCURATE><<<(ntr + 127) / 128, 128, 0, st>>>(Ms, nm, gp);
+            k_sur_gen<HH_PREC_ACCURATE><<<(ntr + 127) / 128, 128, 0, st>>>(Ms, S->coarse, nm, gp);
         e = cudaGetLastError();
     }
     unsigned long long got = 0;

@@ -3,10 +3,12 @@ via the C ABI): training converges on windows from the plain integrator,
 windows outside the trained envelope are integrated by the plain kernel
 (with every window declined the run is bit-identical to the plain path), and
 the error against the plain path and the FP64 oracle is measured and
-reported.  Without its per-neuron error estimate the surrogate misses the
-accuracy target (spike counts within +-1 and spike times within 0.05 ms for
-every neuron); with a tight estimate it meets it, on few windows.  The tests
-record the achieved figures."""
+reported.  The MLP learns the correction to one exponential-Euler step over
+the whole window.  Without its per-neuron error estimate the surrogate
+misses the spike-time part of the accuracy target (spike counts within +-1
+and spike times within 0.05 ms for every neuron); with a tight estimate it
+meets it on about half of the windows.  The tests record the achieved
+figures."""
 import json
 
 import numpy as np
@@ -109,13 +111,15 @@ def _spike_time_agreement(a, b, N, tol_ms=0.05):
 
 
 def test_surrogate_error_is_measured():
-    """Surrogate run of 4,096 multi-channel neurons for 500 ms: the share of
-    neuron-windows taken from the MLP and the spike-count and spike-time
-    errors against the plain FP32 path and the FP64 oracle, asserted at the
-    levels this surrogate reaches (measured: 63 % of windows accepted, counts
-    within +-1 of the plain path for 62 % of neurons and of the oracle for
-    58 %).  The +-1 / 0.05 ms target is not met; the plain path itself meets
-    it against the oracle."""
+    """Surrogate run of 4,096 multi-channel neurons for 500 ms without the
+    error estimate: the share of neuron-windows taken from the MLP and the
+    spike-count and spike-time errors against the plain FP32 path and the
+    FP64 oracle, asserted at the levels this surrogate reaches (measured: 85 %
+    of windows accepted, counts within +-1 of the plain path for 99.0-99.2 %
+    of neurons and of the oracle for 99.6 %, spike times within 0.05 ms for
+    62-64 % of the count-equal neurons).  The +-1 / 0.05 ms target is not met
+    without the estimate; the plain path itself meets it against the
+    oracle."""
     y = inp.multi_channel_neurons(4096, seed=7)
     T = 20_000
     plain = run(y, T)
@@ -141,25 +145,24 @@ def test_surrogate_error_is_measured():
     # the plain path itself meets the count target against the oracle
     assert report["plain_count_within_1_vs_oracle"] == 1.0
     # the levels the surrogate reaches
-    assert report["accepted_frac"] >= 0.55
-    assert report["count_within_1_vs_plain"] >= 0.55
-    assert report["count_within_1_vs_oracle"] >= 0.5
-    assert report["spike_times_within_0.05ms_of_plain"] >= 0.2
+    assert report["accepted_frac"] >= 0.75
+    assert report["count_within_1_vs_plain"] >= 0.97
+    assert report["count_within_1_vs_oracle"] >= 0.97
+    assert report["spike_times_within_0.05ms_of_plain"] >= 0.5
 
 
 def test_error_estimate_controls_accuracy():
-    """The per-neuron error estimate (the MLP's 10-step prediction against one
+    """The per-neuron error estimate (the size of the MLP's correction to one
     exponential-Euler step over the whole window, hh_surrogate_desc.err_V /
-    err_p) hands every window where the two disagree to the plain kernel.
-    Tightening it trades accepted windows for accuracy (4,096 multi-channel
-    neurons, 500 ms; measured: at 0.1 mV / 0.004, 34 % of windows accepted
-    and counts within +-1 of the plain path for 99.5 % of neurons; at 0.01 mV
-    / 0.0005, 4 % accepted, counts within +-1 for every neuron and spike
-    times within 0.05 ms for 99.8 % of the count-equal neurons -- the
-    accuracy target, met on few windows).  The training windows are appended
-    by atomics, so their order, and the trained weights, vary slightly from
-    run to run: the bars sit below the measured levels (>= 99.9 % within
-    +-1 and >= 98 % of spike times at the tight setting)."""
+    err_p) hands every window that needs a larger correction to the plain
+    kernel.  Tightening it trades accepted windows for accuracy (4,096
+    multi-channel neurons, 500 ms; measured: at 0.1 mV / 0.004, 79 % of
+    windows accepted and counts within +-1 of the plain path for 99.0-99.1 %
+    of neurons; at 0.01 mV / 0.0005, 54 % accepted, every neuron's count
+    equal to the plain path's and spike times within 0.05 ms for 99.7-99.8 %
+    of them -- the accuracy target).  The training windows are appended by
+    atomics, so their order, and the trained weights, vary slightly from run
+    to run: the bars sit below the measured levels."""
     y = inp.multi_channel_neurons(4096, seed=7)
     T = 20_000
     plain = run(y, T)
@@ -178,8 +181,8 @@ def test_error_estimate_controls_accuracy():
                     "times": _spike_time_agreement(sur, plain, 4096)}
         assert sur["status"] == 0
     print(json.dumps(out))
-    assert out["mid"]["accepted_frac"] >= 0.25 and out["mid"]["within_1"] >= 0.99
-    assert out["tight"]["accepted_frac"] >= 0.02
+    assert out["mid"]["accepted_frac"] >= 0.6 and out["mid"]["within_1"] >= 0.97
+    assert out["tight"]["accepted_frac"] >= 0.4
     assert out["tight"]["within_1"] >= 0.999 and out["tight"]["within_1_oracle"] >= 0.99
     assert out["tight"]["times"] >= 0.98
     # looser tolerance, more windows from the MLP
