@@ -384,7 +384,11 @@ struct InferParams {
 };
 
 constexpr uint32_t kTile = 128 * kRow * 2;  // 16 KB per 128-row bf16 tile
-constexpr size_t kInferSmem = 1024 + 3 * kTile + (kSH + kSH + kSO) * kRow * 2 + 64;
+// one activation tile (features, then each hidden layer's output in turn),
+// the three weight tiles and the biases: five CTAs per SM
+constexpr size_t kInferSmem = 1024 + kTile + (kSH + kSH + kSO) * kRow * 2 + (2 * kSH + kSO) * 4 + 64;
+constexpr int kInferCtasPerSm = 5;
+constexpr uint32_t kInferTmemCols = 64;
 
 __device__ __forceinline__ uint16_t bf16_rn(float x)
 {
@@ -414,27 +418,50 @@ __device__ __forceinline__ void put_row(uint8_t* tile, int r, const float* v)
     }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevModels Ms,
-                                                   const __grid_constant__ DevModels Mcoarse,
-                                                   const __grid_constant__ SurNorm S,
-                                                   const __grid_constant__ NeuronParams P,
-                                                   const __grid_constant__ InferParams Q)
+// columns 32 h .. 32 h + 31 of a row (chunks 4 h .. 4 h + 3); v == nullptr
+// writes zeros
+__device__ __forceinline__ void put_half(uint8_t* tile, int r, int h, const float* v)
 {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        uint4 c = make_uint4(0u, 0u, 0u, 0u);
+        if (v) {
+            c.x = (uint32_t)bf16_rn(v[8 * jj + 0]) | ((uint32_t)bf16_rn(v[8 * jj + 1]) << 16);
+            c.y = (uint32_t)bf16_rn(v[8 * jj + 2]) | ((uint32_t)bf16_rn(v[8 * jj + 3]) << 16);
+            c.z = (uint32_t)bf16_rn(v[8 * jj + 4]) | ((uint32_t)bf16_rn(v[8 * jj + 5]) << 16);
+            c.w = (uint32_t)bf16_rn(v[8 * jj + 6]) | ((uint32_t)bf16_rn(v[8 * jj + 7]) << 16);
+        }
+        const int j = 4 * h + jj;
+        *reinterpret_cast<uint4*>(tile + r * 128 + ((j ^ (r & 7)) << 4)) = c;
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128, kInferCtasPerSm) k_sur_infer(const __grid_constant__ DevModels Ms,
+                                                                    const __grid_constant__ DevModels Mcoarse,
+                                                                    const __grid_constant__ SurNorm S,
+                                                                    const __grid_constant__ NeuronParams P,
+                                                                    const __grid_constant__ InferParams Q)
+{
+    // Persistent: each CTA stages the weights and biases once, allocates its
+    // TMEM columns once and takes 128-neuron tiles tile = blockIdx.x,
+    // blockIdx.x + gridDim.x, ...  Per tile: features -> A; three
+    // tcgen05.mma layers, each epilogue reading its accumulator from TMEM
+    // (columns 0..63, reused by every layer) and writing its activations
+    // back into A once the layer's MMA has completed.
     extern __shared__ uint8_t raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t* A0 = sm;
-    uint8_t* A1 = A0 + kTile;
-    uint8_t* A2 = A1 + kTile;
-    uint8_t* B1 = A2 + kTile;
+    uint8_t* A = sm;
+    uint8_t* B1 = A + kTile;
     uint8_t* B2 = B1 + kSH * 128;
     uint8_t* B3 = B2 + kSH * 128;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(B3 + kSO * 128);
+    float* sb = reinterpret_cast<float*>(B3 + kSO * 128);   // [64 | 64 | 16]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sb + 2 * kSH + kSO);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const DevModel& M = Ms.m[0];
 
-    // weights -> swizzled tiles (row r chunk j at j ^ (r & 7))
+    // weights -> swizzled tiles (row r chunk j at j ^ (r & 7)); biases
     for (int c = t; c < (kSH + kSH + kSO) * 8; c += 128) {
         const int r = c >> 3, j = c & 7;
         const uint16_t* src;
@@ -450,46 +477,14 @@ __global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevMo
         *reinterpret_cast<uint4*>(dst + rr * 128 + ((j ^ (rr & 7)) << 4)) =
             *reinterpret_cast<const uint4*>(src + rr * kRow + 8 * j);
     }
+    for (int k = t; k < 2 * kSH + kSO; k += 128)
+        sb[k] = Q.b[k];
     if (t == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0)
-        tmem_alloc(tslot, 128);
-
-    // neuron state and features
-    const int64_t gi = (int64_t)blockIdx.x * 128 + t;
-    const bool valid = gi < P.N;
-    const int64_t i = valid ? gi : 0;
-    float V = P.V[i], Ca = P.Ca[i];
-    float p[kMaxGates];
-#pragma unroll
-    for (int q = 0; q < kMaxGates; ++q)
-        p[q] = P.P[(int64_t)q * P.N + i];
-    float gch[kMaxChannels];
-#pragma unroll
-    for (int c = 0; c < kMaxChannels; ++c)
-        gch[c] = c < M.n_ch ? (P.gbar ? P.gbar[(int64_t)c * P.N + i] : M.gbar[c]) : 0.0f;
-    const float I = P.I_const ? P.I_const[i] : 0.0f;
-    float f[kRow];
-    sur_features(M, S, V, p, Ca, I, gch, f);
-#pragma unroll
-    for (int k = kSF; k < kRow; ++k)
-        f[k] = 0.0f;
-    bool cand = valid && V < S.v_env && finite(V);
-#pragma unroll
-    for (int k = 0; k < kSF; ++k) {
-        if (k < S.n_feat) {
-            const float w = (S.hi[k] - S.lo[k]) * Q.margin;
-            cand = cand && f[k] >= S.lo[k] - w && f[k] <= S.hi[k] + w;
-        }
-    }
-    if (!cand) {
-#pragma unroll
-        for (int k = 0; k < kRow; ++k)
-            f[k] = 0.0f;
-    }
-    put_row(A0, t, f);
+        tmem_alloc(tslot, kInferTmemCols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -497,126 +492,146 @@ __global__ void __launch_bounds__(128) k_sur_infer(const __grid_constant__ DevMo
     const uint32_t tmem = *tslot;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     uint32_t phase = 0;
-    bool ok = true;
-    float h[kRow];
+    const int64_t n_tiles = (P.N + 127) / 128;
+    unsigned long long n_acc = 0, n_dec = 0;
 
-    // layer 1: A0 (128 x 64) x W1^T -> cols [0, 64)
-    if (t == 0) {
-        const uint64_t da = sdesc(smem_u32(A0)), db = sdesc(smem_u32(B1));
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // neuron state and features
+        const int64_t gi = tile * 128 + t;
+        const bool valid = gi < P.N;
+        const int64_t i = valid ? gi : 0;
+        const float V = P.V[i], Ca = P.Ca[i];
+        float p[kMaxGates];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc_bf16(128, kSH), k > 0 ? 1u : 0u);
-        mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase, Q.err, 16) && ok;
-    phase ^= 1u;
-    tc_fence_after();
-    tmem_ld32(tmem + lane_base, h);
-    tmem_ld32(tmem + lane_base + 32, h + 32);
+        for (int q = 0; q < kMaxGates; ++q)
+            p[q] = P.P[(int64_t)q * P.N + i];
+        float gch[kMaxChannels];
 #pragma unroll
-    for (int k = 0; k < kSH; ++k)
-        h[k] = tanh_approx(h[k] + Q.b[k]);
-    put_row(A1, t, h);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // layer 2: A1 x W2^T -> cols [64, 128)
-    if (t == 0) {
-        const uint64_t da = sdesc(smem_u32(A1)), db = sdesc(smem_u32(B2));
+        for (int c = 0; c < kMaxChannels; ++c)
+            gch[c] = c < M.n_ch ? (P.gbar ? P.gbar[(int64_t)c * P.N + i] : M.gbar[c]) : 0.0f;
+        const float I = P.I_const ? P.I_const[i] : 0.0f;
+        bool cand = valid && V < S.v_env && finite(V);
+        {
+            float f[kSF];
+            sur_features(M, S, V, p, Ca, I, gch, f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem + 64, da + 2 * k, db + 2 * k, idesc_bf16(128, kSH), k > 0 ? 1u : 0u);
-        mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase, Q.err, 16) && ok;
-    phase ^= 1u;
-    tc_fence_after();
-    tmem_ld32(tmem + lane_base + 64, h);
-    tmem_ld32(tmem + lane_base + 96, h + 32);
-#pragma unroll
-    for (int k = 0; k < kSH; ++k)
-        h[k] = tanh_approx(h[k] + Q.b[kSH + k]);
-    put_row(A2, t, h);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // layer 3: A2 x W3^T -> cols [0, 16)
-    if (t == 0) {
-        const uint64_t da = sdesc(smem_u32(A2)), db = sdesc(smem_u32(B3));
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc_bf16(128, kSO), k > 0 ? 1u : 0u);
-        mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase, Q.err, 16) && ok;
-    tc_fence_after();
-    float o[kSO];
-    tmem_ld16(tmem + lane_base, o);
-
-    // the prediction: the coarse step plus the learned correction; accepted
-    // inside the envelope (and, with the error estimate on, when the
-    // correction is small: the MLP's error is a fraction of it), otherwise
-    // the window goes to the plain kernel
-    const int G = M.n_gates;
-    State<kMaxGates, PREC> c;
-    coarse_step<PREC>(Mcoarse.m[0], P.dt * (float)Q.W, V, p, Ca, I, gch, c);
-    const float Vn = c.V + (o[0] + Q.b[2 * kSH + 0]) * S.out_scale[0];
-    bool acc = cand && ok && Vn < S.v_env && finite(Vn);
-    if (Q.err_V > 0.0f)
-        acc = acc && fabsf(Vn - c.V) <= Q.err_V;
-    float pn[kMaxGates];
-#pragma unroll
-    for (int q = 0; q < kMaxGates; ++q) {
-        pn[q] = p[q];
-        if (q < G) {
-            pn[q] = c.p[q] + (o[1 + q] + Q.b[2 * kSH + 1 + q]) * S.out_scale[1 + q];
-            acc = acc && pn[q] >= 0.0f && pn[q] <= 1.0f;
-            if (Q.err_V > 0.0f)
-                acc = acc && fabsf(pn[q] - c.p[q]) <= Q.err_p;
+            for (int k = 0; k < kSF; ++k) {
+                if (k < S.n_feat) {
+                    const float w = (S.hi[k] - S.lo[k]) * Q.margin;
+                    cand = cand && f[k] >= S.lo[k] - w && f[k] <= S.hi[k] + w;
+                }
+            }
+            put_half(A, t, 0, cand ? f : nullptr);
+            put_half(A, t, 1, nullptr);
         }
-    }
-    float Can = Ca;
-    if (S.has_ca) {
-        Can = c.Ca + (o[1 + G] + Q.b[2 * kSH + 1 + G]) * S.out_scale[1 + G];
-        acc = acc && Can > 0.0f;
-    }
-    if (valid) {
-        if (acc) {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        bool ok = true;
+        // two hidden layers: A x W^T -> TMEM columns 0..63, tanh(. + b) -> A
+#pragma unroll 1
+        for (int layer = 0; layer < 2; ++layer) {
+            if (t == 0) {
+                const uint64_t da = sdesc(smem_u32(A)), db = sdesc(smem_u32(layer == 0 ? B1 : B2));
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc_bf16(128, kSH), k > 0 ? 1u : 0u);
+                mma_commit(bar);
+            }
+            ok = mbar_wait(bar, phase, Q.err, 16) && ok;
+            phase ^= 1u;
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[32];
+                tmem_ld32(tmem + lane_base + 32 * h, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    v[k] = tanh_approx(v[k] + sb[layer * kSH + 32 * h + k]);
+                put_half(A, t, h, v);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+        // output layer: A x W3^T -> columns 0..15
+        if (t == 0) {
+            const uint64_t da = sdesc(smem_u32(A)), db = sdesc(smem_u32(B3));
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc_bf16(128, kSO), k > 0 ? 1u : 0u);
+            mma_commit(bar);
+        }
+        ok = mbar_wait(bar, phase, Q.err, 16) && ok;
+        phase ^= 1u;
+        tc_fence_after();
+        float o[kSO];
+        tmem_ld16(tmem + lane_base, o);
+
+        // the prediction: the coarse step plus the learned correction;
+        // accepted inside the envelope (and, with the error estimate on,
+        // when the correction is small: the MLP's error is a fraction of
+        // it), otherwise the window goes to the plain kernel
+        const int G = M.n_gates;
+        State<kMaxGates, PREC> c;
+        coarse_step<PREC>(Mcoarse.m[0], P.dt * (float)Q.W, V, p, Ca, I, gch, c);
+        const float Vn = c.V + (o[0] + sb[2 * kSH + 0]) * S.out_scale[0];
+        bool acc = cand && ok && Vn < S.v_env && finite(Vn);
+        if (Q.err_V > 0.0f)
+            acc = acc && fabsf(Vn - c.V) <= Q.err_V;
+        float pn[kMaxGates];
+#pragma unroll
+        for (int q = 0; q < kMaxGates; ++q) {
+            pn[q] = p[q];
+            if (q < G) {
+                pn[q] = c.p[q] + (o[1 + q] + sb[2 * kSH + 1 + q]) * S.out_scale[1 + q];
+                acc = acc && pn[q] >= 0.0f && pn[q] <= 1.0f;
+                if (Q.err_V > 0.0f)
+                    acc = acc && fabsf(pn[q] - c.p[q]) <= Q.err_p;
+            }
+        }
+        float Can = Ca;
+        if (S.has_ca) {
+            Can = c.Ca + (o[1 + G] + sb[2 * kSH + 1 + G]) * S.out_scale[1 + G];
+            acc = acc && Can > 0.0f;
+        }
+        if (valid && acc) {
             P.V[i] = Vn;
             P.Ca[i] = Can;
 #pragma unroll
             for (int q = 0; q < kMaxGates; ++q)
                 if (q < G)
                     P.P[(int64_t)q * P.N + i] = pn[q];
-        } else {
-            P.Ca[i] = Ca;
         }
-    }
-    // warp-aggregated append of the declined neurons and the counters
-    const bool fb = valid && !acc;
-    const unsigned bm = __ballot_sync(0xffffffffu, fb);
-    const unsigned am = __ballot_sync(0xffffffffu, valid && acc);
-    const int lane = t & 31;
-    if (bm) {
-        int base = 0;
-        if (lane == __ffs(bm) - 1)
-            base = atomicAdd(Q.fb_count, __popc(bm));
-        base = __shfl_sync(0xffffffffu, base, __ffs(bm) - 1);
-        if (fb)
-            Q.fb_list[base + __popc(bm & ((1u << lane) - 1u))] = (int32_t)i;
+        // warp-aggregated append of the declined neurons
+        const bool fb = valid && !acc;
+        const unsigned bm = __ballot_sync(0xffffffffu, fb);
+        const unsigned am = __ballot_sync(0xffffffffu, valid && acc);
+        if (bm) {
+            int base = 0;
+            if (lane == __ffs(bm) - 1)
+                base = atomicAdd(Q.fb_count, __popc(bm));
+            base = __shfl_sync(0xffffffffu, base, __ffs(bm) - 1);
+            if (fb)
+                Q.fb_list[base + __popc(bm & ((1u << lane) - 1u))] = (int32_t)i;
+        }
+        n_acc += __popc(am);
+        n_dec += __popc(bm);
+        // every thread's TMEM reads are complete before the next tile's
+        // first MMA (the barrier after the next features) overwrites them
     }
     if (lane == 0) {
-        if (am)
-            atomicAdd(&Q.stats[0], (unsigned long long)__popc(am));
-        if (bm)
-            atomicAdd(&Q.stats[1], (unsigned long long)__popc(bm));
+        if (n_acc)
+            atomicAdd(&Q.stats[0], n_acc);
+        if (n_dec)
+            atomicAdd(&Q.stats[1], n_dec);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        tmem_dealloc(tmem, 128);
+        tmem_dealloc(tmem, kInferTmemCols);
 }
 
 }  // namespace
@@ -961,7 +976,8 @@ cudaError_t surrogate_window(const DevModels& Ms, Surrogate* S, const NeuronPara
     cudaError_t e = cudaMemsetAsync(S->fb_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess)
         return e;
-    const unsigned grid = (unsigned)((P.N + 127) / 128);
+    const int64_t n_tiles = (P.N + 127) / 128;
+    const unsigned grid = (unsigned)std::min<int64_t>(n_tiles, (int64_t)152 * kInferCtasPerSm);
     if (precision == HH_PREC_FAST)
         k_sur_infer<HH_PREC_FAST><<<grid, 128, kInferSmem, st>>>(Ms, S->coarse, S->norm, P, q);
     else
