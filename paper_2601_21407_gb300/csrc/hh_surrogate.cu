@@ -390,10 +390,13 @@ constexpr size_t kInferSmem = 1024 + kTile + (kSH + kSH + kSO) * kRow * 2 + (2 *
 constexpr int kInferCtasPerSm = 5;
 constexpr uint32_t kInferTmemCols = 64;
 
-__device__ __forceinline__ uint16_t bf16_rn(float x)
+// two floats as a packed bf16 pair (lo in the low half), rounded to nearest
+// even by the hardware conversion
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi)
 {
-    const uint32_t u = __float_as_uint(x);
-    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 __device__ __forceinline__ float tanh_approx(float x)
@@ -403,33 +406,19 @@ __device__ __forceinline__ float tanh_approx(float x)
     return y;
 }
 
-// write one 64-wide bf16 row into a 128-byte-swizzled tile (16-byte chunk j
-// of row r at chunk j ^ (r & 7))
-__device__ __forceinline__ void put_row(uint8_t* tile, int r, const float* v)
-{
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        uint4 c;
-        c.x = (uint32_t)bf16_rn(v[8 * j + 0]) | ((uint32_t)bf16_rn(v[8 * j + 1]) << 16);
-        c.y = (uint32_t)bf16_rn(v[8 * j + 2]) | ((uint32_t)bf16_rn(v[8 * j + 3]) << 16);
-        c.z = (uint32_t)bf16_rn(v[8 * j + 4]) | ((uint32_t)bf16_rn(v[8 * j + 5]) << 16);
-        c.w = (uint32_t)bf16_rn(v[8 * j + 6]) | ((uint32_t)bf16_rn(v[8 * j + 7]) << 16);
-        *reinterpret_cast<uint4*>(tile + r * 128 + ((j ^ (r & 7)) << 4)) = c;
-    }
-}
-
-// columns 32 h .. 32 h + 31 of a row (chunks 4 h .. 4 h + 3); v == nullptr
-// writes zeros
+// columns 32 h .. 32 h + 31 of row r of a 128-byte-swizzled bf16 tile
+// (16-byte chunk j of row r at chunk j ^ (r & 7); here j = 4 h .. 4 h + 3);
+// v == nullptr writes zeros
 __device__ __forceinline__ void put_half(uint8_t* tile, int r, int h, const float* v)
 {
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
         uint4 c = make_uint4(0u, 0u, 0u, 0u);
         if (v) {
-            c.x = (uint32_t)bf16_rn(v[8 * jj + 0]) | ((uint32_t)bf16_rn(v[8 * jj + 1]) << 16);
-            c.y = (uint32_t)bf16_rn(v[8 * jj + 2]) | ((uint32_t)bf16_rn(v[8 * jj + 3]) << 16);
-            c.z = (uint32_t)bf16_rn(v[8 * jj + 4]) | ((uint32_t)bf16_rn(v[8 * jj + 5]) << 16);
-            c.w = (uint32_t)bf16_rn(v[8 * jj + 6]) | ((uint32_t)bf16_rn(v[8 * jj + 7]) << 16);
+            c.x = bf16x2_rn(v[8 * jj + 0], v[8 * jj + 1]);
+            c.y = bf16x2_rn(v[8 * jj + 2], v[8 * jj + 3]);
+            c.z = bf16x2_rn(v[8 * jj + 4], v[8 * jj + 5]);
+            c.w = bf16x2_rn(v[8 * jj + 6], v[8 * jj + 7]);
         }
         const int j = 4 * h + jj;
         *reinterpret_cast<uint4*>(tile + r * 128 + ((j ^ (r & 7)) << 4)) = c;
