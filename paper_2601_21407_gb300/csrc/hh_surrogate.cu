@@ -50,7 +50,7 @@ constexpr int oW1 = 0, ob1 = oW1 + kSH * kRow, oW2 = ob1 + kSH, ob2 = oW2 + kSH 
 
 struct SurNorm {
     float out_scale[kSO];
-    float lo[kSF], hi[kSF];   // trained envelope of the features
+    float lo[kSF], hi[kSF];   // trained envelope of the features, widened by the margin
     float v_env;
     int32_t n_feat, n_out, G, has_ca;
     float gbar_ref[kMaxChannels];
@@ -69,12 +69,16 @@ __device__ __forceinline__ void sur_features(const DevModel& M, const SurNorm& S
         if (q < M.n_gates)
             f[1 + q] = 2.0f * p[q] - 1.0f;
     const int G = M.n_gates;
-    f[1 + G] = S.has_ca ? 0.5f * logf(fmaxf(Ca, 1e-6f) / M.ca_rest) : 0.0f;
+    // (fast logarithms and divisions: the features feed a bf16 network, and
+    // training and inference evaluate them alike)
+    f[1 + G] = S.has_ca ? 0.5f * __logf(__fdividef(fmaxf(Ca, 1e-6f), M.ca_rest)) : 0.0f;
     f[2 + G] = I * 0.1f;
 #pragma unroll
     for (int c = 0; c < kMaxChannels; ++c)
         if (c < M.n_ch && 3 + G + c < kSF)
-            f[3 + G + c] = S.gbar_ref[c] > 0.0f ? logf(fmaxf(gch[c], 1e-12f) / S.gbar_ref[c]) * (1.0f / 0.3f) : 0.0f;
+            f[3 + G + c] = S.gbar_ref[c] > 0.0f
+                               ? __logf(__fdividef(fmaxf(gch[c], 1e-12f), S.gbar_ref[c])) * (1.0f / 0.3f)
+                               : 0.0f;
 }
 
 // One exponential-Euler step over a whole window (rates at its first V,
@@ -378,7 +382,6 @@ struct InferParams {
     int32_t* fb_count;
     unsigned long long* stats;  // [0] accepted windows, [1] fallbacks
     int32_t* err;
-    float margin;         // fractional widening of the feature envelope
     int32_t W;            // steps per window
     float err_V, err_p;   // error-estimate tolerances (err_V <= 0: off)
 };
@@ -505,10 +508,8 @@ __global__ void __launch_bounds__(128, kInferCtasPerSm) k_sur_infer(const __grid
             sur_features(M, S, V, p, Ca, I, gch, f);
 #pragma unroll
             for (int k = 0; k < kSF; ++k) {
-                if (k < S.n_feat) {
-                    const float w = (S.hi[k] - S.lo[k]) * Q.margin;
-                    cand = cand && f[k] >= S.lo[k] - w && f[k] <= S.hi[k] + w;
-                }
+                if (k < S.n_feat)
+                    cand = cand && f[k] >= S.lo[k] && f[k] <= S.hi[k];
             }
             put_half(A, t, 0, cand ? f : nullptr);
             put_half(A, t, 1, nullptr);
@@ -642,7 +643,7 @@ struct Surrogate {
     unsigned long long* stats = nullptr;
     int32_t* err = nullptr;
     int64_t N = 0;
-    float margin = 0.0f;
+    float margin = 0.0f;         // fractional widening of the feature envelope
     std::vector<void*> allocs;
     template <class T>
     cudaError_t alloc(T** p, size_t n)
@@ -829,8 +830,10 @@ hh_status surrogate_train(const DevModels& Ms, int precision, double dt, int64_t
                     const double mean = s / n, var = std::max(0.0, q / n - mean * mean);
                     nm.out_scale[col] = col < n_out ? (float)std::max(std::sqrt(var), 1e-7) : 1.0f;
                 } else {
-                    nm.lo[col] = col < n_feat ? mn : 0.0f;
-                    nm.hi[col] = col < n_feat ? mx : 0.0f;
+                    // the envelope widened by the margin on both sides
+                    const double w = ((double)mx - (double)mn) * S->margin;
+                    nm.lo[col] = col < n_feat ? (float)((double)mn - w) : 0.0f;
+                    nm.hi[col] = col < n_feat ? (float)((double)mx + w) : 0.0f;
                 }
             }
         }
@@ -958,7 +961,6 @@ cudaError_t surrogate_window(const DevModels& Ms, Surrogate* S, const NeuronPara
     q.fb_count = S->fb_count;
     q.stats = S->stats;
     q.err = S->err;
-    q.margin = S->margin;
     q.W = S->W;
     q.err_V = S->err_V;
     q.err_p = S->err_p;
