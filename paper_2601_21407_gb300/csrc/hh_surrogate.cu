@@ -486,6 +486,10 @@ __global__ void __launch_bounds__(128, kInferCtasPerSm) k_sur_infer(const __grid
     uint32_t phase = 0;
     const int64_t n_tiles = (P.N + 127) / 128;
     unsigned long long n_acc = 0, n_dec = 0;
+    // false once a wait of this CTA has run out (status bit set): the phase
+    // bookkeeping can no longer be trusted, so every later window of the
+    // CTA goes to the plain kernel
+    bool ok = true;
 
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         // neuron state and features
@@ -518,7 +522,6 @@ __global__ void __launch_bounds__(128, kInferCtasPerSm) k_sur_infer(const __grid
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        bool ok = true;
         // two hidden layers: A x W^T -> TMEM columns 0..63, tanh(. + b) -> A
 #pragma unroll 1
         for (int layer = 0; layer < 2; ++layer) {
