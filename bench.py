@@ -231,7 +231,10 @@ def run_gpu(args):
     # three timed; the state is restored afterwards.  Before the warm-up,
     # outside the timed region.
     net.reset(V0_dev)
-    tune = net.autotune(trial_steps=STEPS_PER_SIM)
+    if args.no_autotune:
+        tune = {"candidates": [(0, 0, 0.0)], "best": 0}
+    else:
+        tune = net.autotune(trial_steps=STEPS_PER_SIM)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -433,9 +436,10 @@ def run_gpu(args):
             "peaks_measured": {k: v / 1e9 for k, v in sfu_peaks.items()} | {"unit": "G results/s"},
             "launch_shape": {"neuron_block": tune["candidates"][tune["best"]][0],
                              "route_blocks": tune["candidates"][tune["best"]][1],
-                             "source": "hh_autotune over one benchmark step (40,000 steps from reset), before "
-                                       "the warm-up; (0, 0) is the library's default shape, kept unless another "
-                                       "is 3 % faster (median of three timed runs each)",
+                             "source": ("the library's default shape (--no-autotune)" if args.no_autotune else
+                                        "hh_autotune over one benchmark step (40,000 steps from reset), before "
+                                        "the warm-up; (0, 0) is the library's default shape, kept unless another "
+                                        "is 3 % faster (median of three timed runs each)"),
                              "sweep_ms_per_step": [list(c) for c in tune["candidates"]]},
         }
         if cpu is not None:
@@ -921,6 +925,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shape (no hh_autotune before the warm-up; the launch "
+                         "indices of the timed steps are then those of the profiles' ncu commands)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64 batched heterogeneous networks (graph generation on the host cores)")
     ap.add_argument("--no-extras", action="store_true",
