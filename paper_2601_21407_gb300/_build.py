@@ -16,8 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhh.so")
-SOURCES = ["hh_kernels.cu", "hh_abi.cu", "hh_jit.cu", "hh_gemm.cu", "hh_layer.cu", "hh_surrogate.cu",
-           "hh_peaks.cu"]
+# (source, object, extra flags): the table-interpreting kernels are compiled
+# once per precision so that their instantiations build in parallel
+UNITS = [(f, f.replace(".cu", ".o"), []) for f in
+         ("hh_kernels.cu", "hh_abi.cu", "hh_jit.cu", "hh_gemm.cu", "hh_layer.cu", "hh_surrogate.cu", "hh_peaks.cu")]
+UNITS += [("hh_table.cu", f"hh_table_{p}.o", [f"-DHH_TABLE_PREC={p}"]) for p in (0, 1, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -61,10 +64,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if ptxas_info:
         common += ["-Xptxas", "-v"]
     procs, objs = [], []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    for src, obj_name, flags in UNITS:
+        obj = os.path.join(BUILD, obj_name)
         objs.append(obj)
-        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + common
+        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + common + flags
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -34,6 +34,18 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
                               int64_t t0, int32_t W, int32_t window_parity,
                               const float* I_steps, const RecordParams& R,
                               const SpikeList& L, cudaStream_t st);
+// the table-interpreting kernels of one precision each (hh_table.cu)
+#define HH_TABLE_DECL(suffix)                                                                              \
+    cudaError_t table_independent_##suffix(const DevModels& M, const NeuronParams& P, int64_t t0,          \
+                                           int32_t n_steps, const float* I_steps, const RecordParams& R, \
+                                           int grid, int block, cudaStream_t st);                          \
+    cudaError_t table_net_window_##suffix(const DevModels& M, const NeuronParams& P, int64_t t0, int32_t W, \
+                                          int32_t parity, const float* I_steps, const RecordParams& R,    \
+                                          const SpikeList& L, int grid, int block, cudaStream_t st);
+HH_TABLE_DECL(fast)
+HH_TABLE_DECL(accurate)
+HH_TABLE_DECL(compensated)
+#undef HH_TABLE_DECL
 cudaError_t launch_route_window(const RouteParams& RP, const SpikeList& L, int32_t parity, int64_t t0,
                                 int32_t W, int32_t blocks, cudaStream_t st);
 cudaError_t route_pull_prepare();

@@ -1,12 +1,8 @@
 // CUDA kernels of the Hodgkin-Huxley hot path compiled into libhh.so (sm_103a).
 //
-//   k_independent  (table interpreter) many time steps of independent neurons
-//                  in one launch, state in registers (Methods, Eq. hh_eq_full
-//                  with exponential-Euler gates and V)
-//   k_net_window   (table interpreter) up to D steps of a network per launch:
-//                  delivery from the delay ring + Poisson background, rates,
-//                  gates, V, Ca, threshold, warp-aggregated spike compaction,
-//                  synaptic decay
+//   launchers of the table-interpreting neuron kernels (k_independent,
+//                  k_net_window in hh_table.cu, one translation unit per
+//                  precision)
 //   k_route        spike propagation over the out-CSR: one warp per
 //                  (spike, 256-synapse segment) item, or per spike for
 //                  large windows; 128-bit reads of (target, weight), 64-bit
@@ -21,46 +17,6 @@
 
 namespace hh {
 namespace {
-
-// Dynamics read from a model table in the kernel parameters.
-struct TableDyn {
-    static constexpr bool kDrive = true, kCable = true, kSynCurrent = true, kCompound = true;
-    const DevModels& Ms;
-    template <int MAXG, int PREC>
-    __device__ __forceinline__ void load(int mid, const NeuronParams& P, int64_t i,
-                                         State<MAXG, PREC>& s) const
-    {
-        load_conductances(Ms.m[mid], P.gbar, P.N, i, s);
-    }
-    template <int MAXG, int PREC>
-    __device__ __forceinline__ void step(int mid, float dt, int v_update, float I, float gsE, float EE,
-                                         float gsI, float EI, State<MAXG, PREC>& s) const
-    {
-        neuron_step<MAXG, PREC>(Ms.m[mid], dt, v_update, I, gsE, EE, gsI, EI, s);
-    }
-};
-
-template <int MAXG, int PREC>
-__global__ void __launch_bounds__(128) k_independent(const __grid_constant__ DevModels Ms,
-                                                     const __grid_constant__ NeuronParams P,
-                                                     int64_t t0, int32_t n_steps,
-                                                     const float* __restrict__ I_steps,
-                                                     const __grid_constant__ RecordParams R)
-{
-    independent_body<MAXG, PREC>(TableDyn{Ms}, P, t0, n_steps, I_steps, R);
-}
-
-template <int MAXG, int PREC>
-__global__ void __launch_bounds__(128) k_net_window(const __grid_constant__ DevModels Ms,
-                                                    const __grid_constant__ NeuronParams P,
-                                                    int64_t t0, int32_t W,
-                                                    const float* __restrict__ I_steps,
-                                                    const __grid_constant__ RecordParams R,
-                                                    const __grid_constant__ SpikeList L,
-                                                    int32_t parity)
-{
-    window_body<MAXG, PREC, 1>(TableDyn{Ms}, P, t0, W, I_steps, R, L, parity, 0);
-}
 
 // Spike routing of a list whose length is read on the device.  A window of
 // the window schedule (W > 0: steps t0 .. t0 + W - 1, list slot lslot) with
@@ -221,19 +177,6 @@ int grid_for(int64_t N, int bs)
 
 }  // namespace
 
-#define HH_DISPATCH(MAXG_, PREC_, CALL)                                            \
-    do {                                                                           \
-        if ((MAXG_) <= 4) {                                                        \
-            if ((PREC_) == HH_PREC_FAST) { constexpr int G = 4, Q = HH_PREC_FAST; CALL; }             \
-            else if ((PREC_) == HH_PREC_ACCURATE) { constexpr int G = 4, Q = HH_PREC_ACCURATE; CALL; } \
-            else { constexpr int G = 4, Q = HH_PREC_COMPENSATED; CALL; }            \
-        } else {                                                                   \
-            if ((PREC_) == HH_PREC_FAST) { constexpr int G = 8, Q = HH_PREC_FAST; CALL; }             \
-            else if ((PREC_) == HH_PREC_ACCURATE) { constexpr int G = 8, Q = HH_PREC_ACCURATE; CALL; } \
-            else { constexpr int G = 8, Q = HH_PREC_COMPENSATED; CALL; }            \
-        }                                                                          \
-    } while (0)
-
 cudaError_t launch_init_state(const DevModels& M, const NeuronParams& P, const float* V0,
                               int32_t model_index, int precision, cudaStream_t st)
 {
@@ -243,14 +186,19 @@ cudaError_t launch_init_state(const DevModels& M, const NeuronParams& P, const f
     return cudaGetLastError();
 }
 
+// The table-interpreting neuron kernels, one translation unit per
+// precision (hh_table.cu); COMPENSATED also serves any other mode.
 cudaError_t launch_independent(const DevModels& M, const NeuronParams& P, int precision, int64_t t0,
                                int32_t n_steps, const float* I_steps, const RecordParams& R,
                                cudaStream_t st)
 {
     const int bs = block_for(P.N);
-    HH_DISPATCH(M.max_gates, precision,
-                (k_independent<G, Q><<<grid_for(P.N, bs), bs, 0, st>>>(M, P, t0, n_steps, I_steps, R)));
-    return cudaGetLastError();
+    const int grid = grid_for(P.N, bs);
+    if (precision == HH_PREC_FAST)
+        return table_independent_fast(M, P, t0, n_steps, I_steps, R, grid, bs, st);
+    if (precision == HH_PREC_ACCURATE)
+        return table_independent_accurate(M, P, t0, n_steps, I_steps, R, grid, bs, st);
+    return table_independent_compensated(M, P, t0, n_steps, I_steps, R, grid, bs, st);
 }
 
 cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int precision, int64_t t0,
@@ -258,9 +206,12 @@ cudaError_t launch_net_window(const DevModels& M, const NeuronParams& P, int pre
                               const RecordParams& R, const SpikeList& L, cudaStream_t st)
 {
     const int bs = block_for(P.N);
-    HH_DISPATCH(M.max_gates, precision,
-                (k_net_window<G, Q><<<grid_for(P.N, bs), bs, 0, st>>>(M, P, t0, W, I_steps, R, L, parity)));
-    return cudaGetLastError();
+    const int grid = grid_for(P.N, bs);
+    if (precision == HH_PREC_FAST)
+        return table_net_window_fast(M, P, t0, W, parity, I_steps, R, L, grid, bs, st);
+    if (precision == HH_PREC_ACCURATE)
+        return table_net_window_accurate(M, P, t0, W, parity, I_steps, R, L, grid, bs, st);
+    return table_net_window_compensated(M, P, t0, W, parity, I_steps, R, L, grid, bs, st);
 }
 
 // the shared memory a pulling routing block may take, and the largest
