@@ -110,6 +110,22 @@ def test_null_arguments():
     L.hh_destroy(None)
 
 
+def test_null_arguments_of_state_and_launch_shape_calls():
+    """Checkpoint, launch-shape and autotuning calls reject a NULL network or
+    buffer before touching the device."""
+    L = hh.lib()
+    n = C.c_size_t(0)
+    buf = (C.c_uint8 * 512)()
+    assert L.hh_state_size(None, C.byref(n)) == hh.HH_EINVAL
+    assert L.hh_save_state(None, buf, 512) == hh.HH_EINVAL
+    assert L.hh_load_state(None, buf, 512) == hh.HH_EINVAL
+    assert L.hh_set_launch_shape(None, 0, 0) == hh.HH_EINVAL
+    assert L.hh_autotune(None, 100, None) == hh.HH_EINVAL
+    rep = hh.hh_surrogate_report()
+    assert L.hh_surrogate_train(None, None, C.byref(rep)) == hh.HH_EINVAL
+    assert hh.hh_last_error()
+
+
 def test_model_marshalling_roundtrip():
     m = hh.model_desc(inp.MULTI_CHANNEL)
     assert m.n_channels == len(inp.MULTI_CHANNEL["channels"])
